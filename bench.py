@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the MLFFT block-Toeplitz product inside GMRES on GB300.
+
+Workload (the 30 x 30 array, b = 60, N = 54,000 unknowns, synthetic Green's
+function generators with centroid seed 1, mx = my = 60): one step is one
+GMRES(50)-IR solve of the centre-element delta-gap excitation to a true
+relative residual of 1e-8 -- binary32 products inside each restart cycle,
+double-float (FP64-class) residual, Arnoldi and updates.
+
+Reported:
+  value        FFT-product throughput inside the solve: algorithmic bytes of
+               every product the step ran (spectrum planes read once + x in +
+               y out per product) / measured step time, summed over ranks.
+  roofline     the dominant kernel (the binary32 block product), measured live
+               with CUDA events on the plan's stream over the timed steps.
+  gmres        plain FP64 (double-float) GMRES time to 1e-8 vs the IR step.
+  e2e          the same step through the C ABI with host buffers (H2D of V,
+               D2H of I inside the timed region).
+  cpu_baseline the CPU oracle's O(N^2) product timed on the host cores.
+
+``--impl reference`` times the CPU oracle as it stands on this workload:
+each step is one brute-force product (a bounded sample of the solve).
+Multi-GPU (torchrun): every rank solves its own replica; no collective is on
+the data path (weak scaling); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BTTB FFT-matvec GB/s (% HBM peak); GMRES time to 1e-8 rel. residual vs FP64"
+WORKLOAD = "30x30 array, b=60, N=54000, centre-element delta gap, GMRES(50)-IR to 1e-8"
+FALLBACK_HBM = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(use_cuda: bool):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def product_bytes(nx, ny, b, mx, my, prec):
+    """Algorithmic bytes of one FFT product: spectrum planes once, x in, y out."""
+    bins, n = mx * my, nx * ny * b
+    if prec == "fp32":
+        return bins * b * b * 8 + 2 * n * 8
+    return bins * b * b * 16 + 2 * n * 16         # double-float planes or binary64 copy
+
+
+def traffic_from_profiles(kernel_key: str):
+    """ncu DRAM bytes per launch recorded in profiles/, if the kernel source is unchanged."""
+    src = os.path.join(ROOT, "paper_2506_20350_gb300", "csrc", "contract.cu")
+    digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    path = os.path.join(ROOT, "profiles", "contract_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 3 and not line.startswith("#") and f[0] == kernel_key and f[2] == digest:
+            return float(f[1])
+    return None
+
+
+def cpu_oracle_product_time(gen, n, budget_s=12.0):
+    import oracle
+    x = (np.random.default_rng(0).standard_normal(n) + 1j * np.random.default_rng(1).standard_normal(n))
+    oracle.matvec(gen, x)                 # warm (loads and builds the C oracle)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.matvec(gen, x)
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return (time.perf_counter() - t0) / reps, reps
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(False)
+    if rank != 0:
+        return
+    from workloads import arrays
+    c = arrays.CONFIGS["precision"]
+    nx, ny, b = c["nx"], c["ny"], c["b"]
+    gen = arrays.generator_blocks(nx, ny, b, c["seed"])
+    import oracle
+    n = nx * ny * b
+    x = np.random.default_rng(0).standard_normal(n) + 0j
+    for _ in range(args.warmup):
+        oracle.matvec(gen, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.matvec(gen, x)
+    dt = (time.perf_counter() - t0) / args.steps
+    mx = my = 60
+    val = product_bytes(nx, ny, b, mx, my, "fp64") / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = "one O(N^2) brute-force FP64 product of the 30x30 b=60 matrix per step (2.9e9 complex MACs)"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle: one product per step)", "nx": nx, "ny": ny, "b": b},
+            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2506_20350_gb300 as bt
+    from workloads import arrays
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU fallback)")
+    rank, world, local = dist_setup(True)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c = arrays.CONFIGS["precision"]
+    nx, ny, b, tol, restart = c["nx"], c["ny"], c["b"], c["tol"], c["restart"]
+    gen = arrays.generator_blocks(nx, ny, b, c["seed"])
+    stream = torch.cuda.Stream(device=dev)
+    all_prec = (1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_FP32) | (1 << bt.BTTB_MV_FP64_NATIVE)
+    plan = bt.Plan(nx, ny, b, max_rhs=1, prec_mask=all_prec, stream=stream)
+    plan.set_generators(gen)
+    n, mx, my = plan.n, plan.mx, plan.my
+    v_host = arrays.centre_excitation(nx, ny, b)[None, :].copy()
+    V = torch.from_numpy(v_host).to(dev)
+    I = torch.zeros_like(V)
+    b64 = product_bytes(nx, ny, b, mx, my, "fp64")
+    b32 = product_bytes(nx, ny, b, mx, my, "fp32")
+
+    def solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_NONE, Vt=V, It=I, host_io=False):
+        with torch.cuda.stream(stream):
+            if not host_io:
+                It.zero_()
+            _, rc, res = plan.solve(Vt, It, tol=tol, restart=restart, inner=inner, pc=pc, host_io=host_io)
+        if rc != bt.BTTB_OK:
+            raise RuntimeError(f"solve failed rc={rc}: {bt.bttb_last_error()}")
+        return res[0]
+
+    def step_bytes(r, inner):
+        inner_b = b32 if inner == bt.BTTB_MV_FP32 else b64
+        return r.iters * inner_b + (r.cycles + 1) * b64
+
+    for _ in range(args.warmup):
+        solve()
+    # ---------------- timed region
+    bt.bttb_profile(plan.handle, True)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    total_bytes, iters, cycles, relres = 0.0, [], [], []
+    for _ in range(args.steps):
+        r = solve()
+        total_bytes += step_bytes(r, bt.BTTB_MV_FP32)
+        iters.append(r.iters)
+        cycles.append(r.cycles)
+        relres.append(r.relres_true)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    bt.bttb_profile(plan.handle, False)
+    ms_max = max_over_ranks(ms, world)
+    st32 = bt.bttb_profile_read(plan.handle, bt.BTTB_K_BLOCK_PRODUCT_PREC + bt.BTTB_MV_FP32)
+    st64 = bt.bttb_profile_read(plan.handle, bt.BTTB_K_BLOCK_PRODUCT_PREC + bt.BTTB_MV_FP64)
+    stfft = bt.bttb_profile_read(plan.handle, bt.BTTB_K_FFT)
+    stall = bt.bttb_profile_read(plan.handle, bt.BTTB_K_ALL)
+    value = world * total_bytes / (ms_max / 1e3) / 1e9
+    ms_step = ms_max / args.steps
+
+    if rank != 0:
+        barrier(world)
+        return
+    # ---------------- comparison arms (rank 0, untimed for the headline)
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            out.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(out))
+
+    fp64_res = solve(inner=bt.BTTB_MV_FP64)
+    fp64_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP64), 3)
+    ir_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP32), 3)
+    bj_res = solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_BLOCK_JACOBI)
+    bj_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_BLOCK_JACOBI), 3)
+
+    x = torch.randn(1, n, dtype=torch.complex128, device=dev)
+    y = torch.empty_like(x)
+    x32 = x.to(torch.complex64)
+    y32 = torch.empty_like(x32)
+    mv = {}
+    for name, prec, xx, yy, dt, nb in [("fp64_doublefloat", bt.BTTB_MV_FP64, x, y, bt.BTTB_C128, b64),
+                                      ("fp32", bt.BTTB_MV_FP32, x32, y32, bt.BTTB_C64,
+                                       product_bytes(nx, ny, b, mx, my, "fp32")),
+                                      ("fp64_native", bt.BTTB_MV_FP64_NATIVE, x, y, bt.BTTB_C128, b64)]:
+        reps = 30
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                bt.bttb_matvec(plan.handle, xx, yy, 1, n, dt, prec)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                bt.bttb_matvec(plan.handle, xx, yy, 1, n, dt, prec)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        mv[name] = {"us": t * 1e3, "gbs": nb / (t / 1e3) / 1e9}
+
+    # end to end through the C ABI with host buffers
+    vh = torch.from_numpy(v_host).pin_memory()
+    ih = torch.zeros_like(vh).pin_memory()
+    solve(Vt=vh, It=ih, host_io=True)
+    e2e_bytes, t0 = 0.0, time.perf_counter()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = solve(Vt=vh, It=ih, host_io=True)
+        e2e_bytes += step_bytes(r, bt.BTTB_MV_FP32)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * e2e_bytes / e2e_s / 1e9
+
+    peak, peak_kind = measured_peaks()
+    ach32 = st32.bytes / (st32.ms / 1e3) / 1e9 if st32.ms > 0 else 0.0
+    ach64 = st64.bytes / (st64.ms / 1e3) / 1e9 if st64.ms > 0 else 0.0
+    traffic = traffic_from_profiles("contract_f32_30x30_b60")
+    roofline = {"kernel": "contract_kernel<F32> (binary32 block product, 3600 bins x 60x60)",
+                "bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s",
+                "frac": ach32 / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                "traffic": traffic, "algorithmic_bytes_per_launch": st32.bytes / max(st32.launches, 1),
+                "avg_launch_us": st32.ms * 1e3 / max(st32.launches, 1), "launches": st32.launches,
+                "share_of_step": st32.ms / ms if ms > 0 else None,
+                "doublefloat_product": {"achieved": ach64, "frac": ach64 / peak, "launches": st64.launches,
+                                        "avg_launch_us": st64.ms * 1e3 / max(st64.launches, 1)},
+                "fft_passes": {"ms_per_step": stfft.ms / args.steps, "launches": stfft.launches,
+                               "achieved_gbs": stfft.bytes / (stfft.ms / 1e3) / 1e9 if stfft.ms > 0 else 0.0}}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        t_cpu, reps = cpu_oracle_product_time(gen, n)
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        cpu = {"value": b64 / t_cpu / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"{reps} brute-force O(N^2) FP64 products of the same matrix ({t_cpu:.2f} s each); "
+                         "bytes counted as for one FFT product"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 products + df64 (double-float) residual/Arnoldi",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "b": b, "grid": [mx, my], "seed": c["seed"],
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: every product streams the 104-207 MB spectrum"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 16,
+                "ms_per_step": e2e_s * 1e3 / args.steps},
+        "gpu_launches": stall.launches,
+        "clocks": clk,
+        "gmres": {"ir_ms": ir_ms, "fp64_ms": fp64_ms, "speedup_ir_vs_fp64": fp64_ms / ir_ms,
+                  "ir_iters": iters[0], "ir_cycles": cycles[0], "fp64_iters": fp64_res.iters,
+                  "ir_relres_true": max(relres), "fp64_relres_true": fp64_res.relres_true,
+                  "block_jacobi_ir_ms": bj_ms, "block_jacobi_ir_iters": bj_res.iters,
+                  "speedup_bj_ir_vs_fp64": fp64_ms / bj_ms},
+        "matvec": mv,
+    }
+    print(json.dumps(line), flush=True)
+    barrier(world)
+    plan.close()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

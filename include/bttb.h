@@ -1,0 +1,205 @@
+/*
+ * bttb.h -- C ABI of the GB300 solver for two-level block-Toeplitz
+ * Method-of-Moments systems  Z I = V  (Akerstedt et al., "Solver Performance
+ * of Accelerated MoM for Connected Arrays", arXiv:2506.20350).
+ *
+ * The matrix (Sec. II-A, Eq. (Tblock) with L = 2) belongs to an nx x ny
+ * array of identical cells with b basis functions each, N = nx*ny*b:
+ *   Z[(m*b + p), (n*b + q)] = T[ix_m - ix_n, iy_m - iy_n][p][q],
+ *   cell m = iy_m*nx + ix_m, offsets i in [-(nx-1), nx-1], j in [-(ny-1), ny-1].
+ * Only the (2nx-1)(2ny-1) generator blocks T[i,j] (b x b) are stored
+ * (Sec. II-C).  Products use the multilevel FFT of Sec. II-C / III-A:
+ * zero-pad onto an mx x my cell grid (Eq. (xc2)), 2-D DFT over cells for every
+ * basis index (Eq. (F2), App. B), per-bin b x b block product with the
+ * spectrum of the first block column (Eq. (circL2), (multL)), inverse DFT and
+ * crop.  mx, my are the smallest 5-smooth integers >= 2nx-1, 2ny-1; any grid
+ * at least that large gives the same product (the padded slots hold zeros).
+ *
+ * Conventions for every entry point
+ *  - Complex numbers are interleaved (re, im): BTTB_C128 = 2 x double,
+ *    BTTB_C64 = 2 x float.
+ *  - A vector holds element (ix, iy, p) at (iy*nx + ix)*b + p; column c of a
+ *    multi-vector starts at c*ld elements.
+ *  - Pointers are DEVICE pointers unless an argument or option says host.
+ *    The caller owns every buffer it passes; the plan owns its spectrum copies
+ *    and workspace and frees them in bttb_plan_destroy.
+ *  - Functions never exit, abort or trap.  They return BTTB_OK (0), a soft
+ *    outcome (> 0) or an error (< 0); bttb_last_error() gives a message.
+ *    Device-side problems (a bounded wait that ran out, a non-finite norm)
+ *    set a flag in the plan that the next synchronising call returns.
+ *  - One plan per CUDA stream; a plan is not thread-safe.
+ *
+ * "FP64" below means a result within ~1e-14 relative of binary64.  On this
+ * GPU the binary64 pipe is ~30x slower than the binary32 pipes, so the FP64
+ * product and the Krylov vector work run in double-float arithmetic (an
+ * unevaluated sum hi + lo of two binary32 numbers, 48-bit significand,
+ * Dekker 1971 / Joldes-Muller-Popescu 2017) on the binary32 pipes, reading the
+ * same 8 bytes per real number as binary64.  BTTB_MV_FP64_NATIVE keeps the
+ * IEEE binary64 pipe for comparison.
+ */
+#ifndef BTTB_H
+#define BTTB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bttb_plan_s *bttb_plan;
+
+/* Storage type of a caller's vectors and generators. */
+typedef enum { BTTB_C64 = 0, BTTB_C128 = 1 } bttb_dtype;
+
+/* Arithmetic of a product.  Bit (1u << prec) of a plan's prec_mask asks the
+ * plan to keep the spectrum copy that precision reads. */
+typedef enum {
+    BTTB_MV_FP64 = 0,        /* double-float spectrum (hi+lo planes) and arithmetic  */
+    BTTB_MV_FP32 = 1,        /* binary32 spectrum (the hi plane) and arithmetic      */
+    BTTB_MV_FP64_NATIVE = 2  /* binary64 spectrum copy, binary64 (DFMA) arithmetic   */
+} bttb_mv_prec;
+
+typedef enum {
+    BTTB_PC_NONE = 0,
+    BTTB_PC_BLOCK_JACOBI = 1 /* P_K of Sec. III-B: LU of T[0,0] applied to every cell */
+} bttb_precond;
+
+enum {
+    BTTB_OK = 0,
+    BTTB_NOT_CONVERGED = 1,  /* soft: max_iters reached before tol                  */
+    BTTB_BREAKDOWN = 2,      /* soft: Krylov space exhausted without reaching tol    */
+    BTTB_ERR_INVALID_ARG = -1,
+    BTTB_ERR_CUDA = -2,
+    BTTB_ERR_OOM = -3,
+    BTTB_ERR_NO_GENERATORS = -4,
+    BTTB_ERR_TIMEOUT = -5,   /* a bounded device wait ran out (kernel returned early) */
+    BTTB_ERR_NONFINITE = -6, /* NaN/Inf seen in a norm or in the generators           */
+    BTTB_ERR_SINGULAR = -7   /* zero pivot in the block-Jacobi LU of T[0,0]            */
+};
+
+/*
+ * Create a plan for an nx x ny array with b bases per cell.
+ *   max_rhs   : largest nrhs a later call may pass (sizes the workspace).
+ *   prec_mask : OR of (1u << bttb_mv_prec) for the precisions to support;
+ *               0 means FP64 | FP32.
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream) on which every
+ *               call of this plan is ordered.
+ * Picks the FFT grid (mx, my).  Returns BTTB_ERR_INVALID_ARG for sizes < 1,
+ * nx or ny > 1024, b > 256 or max_rhs > 4096; BTTB_ERR_OOM / _CUDA on failure.
+ */
+int bttb_plan_create(bttb_plan *out, int nx, int ny, int b, int max_rhs,
+                     unsigned prec_mask, void *cuda_stream);
+
+/* FFT grid chosen by the plan (either pointer may be NULL). */
+int bttb_plan_grid(bttb_plan plan, int *mx, int *my);
+
+/*
+ * Load the generator blocks and compute their spectrum (Eq. (circL2),
+ * (multL)): T[i,j] goes to cell slot (i mod mx, j mod my) of the zero grid,
+ * and each of the b*b entries gets a 2-D DFT, in binary64 on the GPU.  The
+ * plan then keeps the copies its prec_mask asks for, scaled by 1/(mx*my).
+ *   gen        : T[i,j][p][q] at ((j+ny-1)*(2nx-1) + (i+nx-1))*b*b + p*b + q,
+ *                p the observer basis (row), q the source basis (column).
+ *   dtype      : storage type of gen.
+ *   gen_is_host: nonzero if gen is a host pointer.
+ * Synchronises the plan's stream.  The caller may free gen on return.
+ * Returns BTTB_ERR_NONFINITE if gen holds NaN/Inf.
+ */
+int bttb_set_generators(bttb_plan plan, const void *gen, bttb_dtype dtype, int gen_is_host);
+
+/*
+ * y[:, c] = Z x[:, c] for c < nrhs (Eq. (multL) with padding and crop of
+ * Eq. (xc2)).  x and y are device multi-vectors of type dtype with column
+ * stride ld >= N elements; they must not overlap.  Stream-ordered on the
+ * plan's stream; does not synchronise.  nrhs <= max_rhs.
+ */
+int bttb_matvec(bttb_plan plan, const void *x, void *y, int nrhs, long ld,
+                bttb_dtype dtype, bttb_mv_prec prec);
+
+/* GMRES options (Sec. III-C hands the product to restarted GMRES). */
+typedef struct {
+    double tol;          /* stop when ||V - Z I||_2 / ||V||_2 <= tol (per column) */
+    int restart;         /* Krylov dimension m of GMRES(m), 1..200                */
+    int max_iters;       /* total Arnoldi steps per column                         */
+    bttb_precond pc;     /* right preconditioner (the residual stays the true one) */
+    bttb_mv_prec inner;  /* precision of the products inside a restart cycle:
+                            FP64 = plain GMRES; FP32 = GMRES-IR (each cycle's
+                            starting residual is recomputed with the FP64 product,
+                            Arnoldi/Givens stay FP64)                             */
+    int use_x0;          /* nonzero: I holds the initial guess on entry            */
+    int host_io;         /* nonzero: V and I are HOST pointers (complex128); the
+                            library copies them in and out on the plan's stream  */
+    double *history;     /* optional HOST array: true relative residual of column 0
+                            at the start of each restart cycle                     */
+    int history_len;     /* capacity of history                                    */
+} bttb_gmres_opts;
+
+typedef struct {
+    int status;          /* BTTB_OK, BTTB_NOT_CONVERGED or BTTB_BREAKDOWN          */
+    int iters;           /* Arnoldi steps taken                                    */
+    int cycles;          /* restart cycles taken                                   */
+    double relres_true;  /* ||V - Z I|| / ||V|| with the FP64 product, at return   */
+} bttb_col_result;
+
+/*
+ * Solve Z I[:, c] = V[:, c] for c < nrhs with restarted GMRES(m), the product
+ * above, classical Gram-Schmidt applied twice and Givens rotations in FP64.
+ * V and I are complex128 with column stride ld (device pointers unless
+ * opts->host_io).  x0 = 0 unless use_x0.  out_host (nrhs entries, host) gets
+ * the per-column outcome.  Synchronises the plan's stream.  Returns the worst
+ * column status (an error < 0 takes precedence).
+ */
+int bttb_gmres_solve(bttb_plan plan, const void *V, void *I, int nrhs, long ld,
+                     const bttb_gmres_opts *opts, bttb_col_result *out_host);
+
+/*
+ * z[:, c] = P_K^{-1} x[:, c] (Sec. III-B): every cell's b-block is solved with
+ * one LU (partial pivoting, FP64) of the self block T[0,0].  Device
+ * multi-vectors of type dtype, stream-ordered.  Needs bttb_set_generators.
+ */
+int bttb_block_jacobi_apply(bttb_plan plan, const void *x, void *z, int nrhs, long ld,
+                            bttb_dtype dtype);
+
+/*
+ * Copy the stored spectrum of bin (ky, kx) -- the b x b block of
+ * F[2] C_1[2] / (mx*my), entry (p, q) at p*b + q -- into host memory
+ * (complex128).  Reads the binary64 copy if the plan keeps one, else the
+ * double-float planes summed in binary64.  Synchronises the stream.
+ */
+int bttb_get_spectrum_bin(bttb_plan plan, int ky, int kx, double *out_host);
+
+/*
+ * Kernel timing.  While enabled, the plan brackets every launch of the block
+ * product and of the FFT passes with CUDA events on its stream and counts
+ * every kernel it launches.  bttb_profile(plan, 1) clears and starts,
+ * bttb_profile(plan, 0) stops.  bttb_profile_read synchronises the stream and
+ * fills *out for `which`:
+ *   BTTB_K_BLOCK_PRODUCT, BTTB_K_FFT: summed event time (ms), launches, and
+ *     algorithmic bytes (the bytes the operation must move: spectrum planes
+ *     read, vectors read and written; padding zeros excluded);
+ *   BTTB_K_ALL: launches of every kernel of the library (ms, bytes = 0);
+ *   BTTB_K_BLOCK_PRODUCT_PREC + prec: the block product of one bttb_mv_prec.
+ */
+enum { BTTB_K_BLOCK_PRODUCT = 0, BTTB_K_FFT = 1, BTTB_K_ALL = 2, BTTB_K_BLOCK_PRODUCT_PREC = 16 };
+typedef struct {
+    double ms;
+    long launches;
+    double bytes;
+} bttb_kernel_stats;
+int bttb_profile(bttb_plan plan, int enable);
+int bttb_profile_read(bttb_plan plan, int which, bttb_kernel_stats *out);
+
+/* Bytes of device memory the plan holds (spectrum copies and workspace). */
+size_t bttb_plan_workspace_bytes(bttb_plan plan);
+
+/* Release everything the plan owns.  NULL is accepted. */
+int bttb_plan_destroy(bttb_plan plan);
+
+/* Message of the last error on this plan (plan may be NULL for errors of
+ * bttb_plan_create).  Thread-local; never NULL. */
+const char *bttb_last_error(bttb_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BTTB_H */

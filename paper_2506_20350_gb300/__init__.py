@@ -1,0 +1,255 @@
+"""GB300 solver for two-level block-Toeplitz MoM systems Z I = V.
+
+Python binding of ``libbttb`` (C ABI in ``include/bttb.h``).  The functions
+below carry the C names and only marshal arguments: every step of the
+product and of the solver runs in the library's CUDA kernels.  PyTorch is used
+for device memory and streams.  There is no fallback: if ``libbttb.so`` is
+missing, every entry point raises ImportError.
+
+Vector convention: a multi-vector with k columns is a C-contiguous tensor of
+shape (k, N) (column c of the paper's V is row c here), element (ix, iy, p) of
+a column at (iy*nx + ix)*b + p.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbttb.so")
+
+BTTB_C64, BTTB_C128 = 0, 1
+BTTB_MV_FP64, BTTB_MV_FP32, BTTB_MV_FP64_NATIVE = 0, 1, 2
+BTTB_PC_NONE, BTTB_PC_BLOCK_JACOBI = 0, 1
+BTTB_OK, BTTB_NOT_CONVERGED, BTTB_BREAKDOWN = 0, 1, 2
+BTTB_ERR_INVALID_ARG, BTTB_ERR_CUDA, BTTB_ERR_OOM = -1, -2, -3
+BTTB_ERR_NO_GENERATORS, BTTB_ERR_TIMEOUT, BTTB_ERR_NONFINITE, BTTB_ERR_SINGULAR = -4, -5, -6, -7
+
+BTTB_K_BLOCK_PRODUCT, BTTB_K_FFT, BTTB_K_ALL, BTTB_K_BLOCK_PRODUCT_PREC = 0, 1, 2, 16
+
+EXPORTS = ("bttb_plan_create", "bttb_plan_grid", "bttb_set_generators", "bttb_matvec",
+           "bttb_gmres_solve", "bttb_block_jacobi_apply", "bttb_get_spectrum_bin",
+           "bttb_profile", "bttb_profile_read",
+           "bttb_plan_workspace_bytes", "bttb_plan_destroy", "bttb_last_error")
+
+
+class BttbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bttb error {code}: {msg}")
+        self.code = code
+
+
+class GmresOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("pc", ctypes.c_int), ("inner", ctypes.c_int), ("use_x0", ctypes.c_int),
+                ("host_io", ctypes.c_int), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("history_len", ctypes.c_int)]
+
+
+class KernelStats(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_long), ("bytes", ctypes.c_double)]
+
+
+class ColResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("relres_true", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libbttb.so (built by ``paper_2506_20350_gb300.build``) and declare its C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2506_20350_gb300.build` "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, ci, cl = ctypes.c_void_p, ctypes.c_int, ctypes.c_long
+    lib.bttb_plan_create.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, ctypes.c_uint, vp]
+    lib.bttb_plan_grid.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    lib.bttb_set_generators.argtypes = [vp, vp, ci, ci]
+    lib.bttb_matvec.argtypes = [vp, vp, vp, ci, cl, ci, ci]
+    lib.bttb_gmres_solve.argtypes = [vp, vp, vp, ci, cl, ctypes.POINTER(GmresOpts), ctypes.POINTER(ColResult)]
+    lib.bttb_block_jacobi_apply.argtypes = [vp, vp, vp, ci, cl, ci]
+    lib.bttb_get_spectrum_bin.argtypes = [vp, ci, ci, ctypes.POINTER(ctypes.c_double)]
+    lib.bttb_profile.argtypes = [vp, ci]
+    lib.bttb_profile_read.argtypes = [vp, ci, ctypes.POINTER(KernelStats)]
+    lib.bttb_plan_workspace_bytes.argtypes = [vp]
+    lib.bttb_plan_workspace_bytes.restype = ctypes.c_size_t
+    lib.bttb_plan_destroy.argtypes = [vp]
+    lib.bttb_last_error.argtypes = [vp]
+    lib.bttb_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("bttb_plan_workspace_bytes", "bttb_last_error"):
+            getattr(lib, name).restype = ci
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, plan=None, soft_ok: bool = False) -> int:
+    if rc < 0 or (rc > 0 and not soft_ok):
+        msg = load_library().bttb_last_error(plan).decode()
+        raise BttbError(rc, msg)
+    return rc
+
+
+def _ptr(t) -> int:
+    """Address of a torch tensor or numpy array."""
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ---------------------------------------------------------------- C names
+
+def bttb_plan_create(nx: int, ny: int, b: int, max_rhs: int = 1, prec_mask: int = 0, stream=None):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.bttb_plan_create(ctypes.byref(h), nx, ny, b, max_rhs, prec_mask, _stream_handle(stream)))
+    return h
+
+
+def bttb_plan_grid(plan) -> tuple[int, int]:
+    mx, my = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().bttb_plan_grid(plan, ctypes.byref(mx), ctypes.byref(my)), plan)
+    return mx.value, my.value
+
+
+def bttb_set_generators(plan, gen) -> None:
+    """gen: complex128/complex64 array or tensor of shape (2ny-1, 2nx-1, b, b), host or device."""
+    is_host = not (hasattr(gen, "is_cuda") and gen.is_cuda)
+    if hasattr(gen, "is_contiguous"):
+        assert gen.is_contiguous()
+        dt = BTTB_C128 if str(gen.dtype) == "torch.complex128" else BTTB_C64
+    else:
+        import numpy as np
+        assert gen.flags["C_CONTIGUOUS"]
+        dt = BTTB_C128 if gen.dtype == np.complex128 else BTTB_C64
+    _check(load_library().bttb_set_generators(plan, _ptr(gen), dt, int(is_host)), plan)
+
+
+def bttb_matvec(plan, x, y, nrhs: int, ld: int, dtype: int, prec: int) -> None:
+    _check(load_library().bttb_matvec(plan, _ptr(x), _ptr(y), nrhs, ld, dtype, prec), plan)
+
+
+def bttb_block_jacobi_apply(plan, x, z, nrhs: int, ld: int, dtype: int) -> None:
+    _check(load_library().bttb_block_jacobi_apply(plan, _ptr(x), _ptr(z), nrhs, ld, dtype), plan)
+
+
+def bttb_gmres_solve(plan, V, I, nrhs: int, ld: int, opts: GmresOpts) -> tuple[int, list[ColResult]]:
+    res = (ColResult * nrhs)()
+    rc = load_library().bttb_gmres_solve(plan, _ptr(V), _ptr(I), nrhs, ld, ctypes.byref(opts), res)
+    _check(rc, plan, soft_ok=True)
+    return rc, list(res)
+
+
+def bttb_get_spectrum_bin(plan, ky: int, kx: int, b: int):
+    import numpy as np
+    out = np.empty((b, b), dtype=np.complex128)
+    _check(load_library().bttb_get_spectrum_bin(plan, ky, kx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           plan)
+    return out
+
+
+def bttb_profile(plan, enable: bool) -> None:
+    _check(load_library().bttb_profile(plan, int(bool(enable))), plan)
+
+
+def bttb_profile_read(plan, which: int) -> KernelStats:
+    st = KernelStats()
+    _check(load_library().bttb_profile_read(plan, which, ctypes.byref(st)), plan)
+    return st
+
+
+def bttb_plan_workspace_bytes(plan) -> int:
+    return int(load_library().bttb_plan_workspace_bytes(plan))
+
+
+def bttb_plan_destroy(plan) -> None:
+    if plan:
+        _check(load_library().bttb_plan_destroy(plan))
+
+
+def bttb_last_error(plan=None) -> str:
+    return load_library().bttb_last_error(plan).decode()
+
+
+# ---------------------------------------------------------------- convenience
+
+def gmres_opts(tol=1e-8, restart=50, max_iters=5000, pc=BTTB_PC_NONE, inner=BTTB_MV_FP64, use_x0=False,
+               host_io=False, history=None) -> GmresOpts:
+    o = GmresOpts()
+    o.tol, o.restart, o.max_iters, o.pc, o.inner = tol, restart, max_iters, pc, inner
+    o.use_x0, o.host_io = int(bool(use_x0)), int(bool(host_io))
+    if history is not None:
+        o.history = history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        o.history_len = history.shape[0]
+    return o
+
+
+class Plan:
+    """Owner of a bttb_plan handle (destroyed on close / garbage collection)."""
+
+    def __init__(self, nx, ny, b, max_rhs=1, prec_mask=0, stream=None):
+        self.nx, self.ny, self.b, self.max_rhs = nx, ny, b, max_rhs
+        self.n = nx * ny * b
+        self.handle = bttb_plan_create(nx, ny, b, max_rhs, prec_mask, stream)
+        self.mx, self.my = bttb_plan_grid(self.handle)
+
+    def set_generators(self, gen):
+        bttb_set_generators(self.handle, gen)
+
+    def matvec(self, x, y=None, prec=BTTB_MV_FP64):
+        """x: (k, N) or (N,) complex tensor on the GPU; returns y = Z x of the same shape."""
+        import torch
+        xs = x.reshape(-1, self.n)
+        if y is None:
+            y = torch.empty_like(xs)
+        dt = BTTB_C128 if xs.dtype == torch.complex128 else BTTB_C64
+        bttb_matvec(self.handle, xs, y, xs.shape[0], self.n, dt, prec)
+        return y.reshape(x.shape)
+
+    def block_jacobi(self, x):
+        import torch
+        xs = x.reshape(-1, self.n)
+        z = torch.empty_like(xs)
+        dt = BTTB_C128 if xs.dtype == torch.complex128 else BTTB_C64
+        bttb_block_jacobi_apply(self.handle, xs, z, xs.shape[0], self.n, dt)
+        return z.reshape(x.shape)
+
+    def solve(self, V, I=None, **kw):
+        """V: (k, N) complex128 (GPU tensor, or host tensor with host_io=True)."""
+        import torch
+        vs = V.reshape(-1, self.n)
+        if I is None:
+            I = torch.zeros_like(vs)
+        opts = gmres_opts(**kw)
+        rc, res = bttb_gmres_solve(self.handle, vs, I, vs.shape[0], self.n, opts)
+        return I.reshape(V.shape), rc, res
+
+    def spectrum_bin(self, ky, kx):
+        return bttb_get_spectrum_bin(self.handle, ky, kx, self.b)
+
+    def workspace_bytes(self):
+        return bttb_plan_workspace_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            bttb_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

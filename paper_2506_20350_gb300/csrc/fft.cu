@@ -1,0 +1,422 @@
+// Batched mixed-radix FFT passes and the generator spectrum.
+//
+// The multilevel FFT of the paper (Sec. III-A, App. A/B) transforms, for
+// every basis index, a sequence of cells along one level of the array with
+// the other level held fixed.  In memory the basis index is the fastest, so a
+// pass is a batch of strided 1-D transforms whose batch index is contiguous.
+// One CTA takes P consecutive batch indices (P a power of two), stages the
+// P interleaved sequences in shared memory (zero-padded to M, Eq. (xc2)),
+// and runs a Stockham autosort FFT with radix 2/3/4/5 butterflies; consecutive
+// threads work on consecutive batch indices, so every shared-memory access is
+// conflict-free and every global access is a coalesced run of P elements.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "arith.cuh"
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace bttb {
+
+int smallest_5smooth(int n) {
+    for (int m = n < 1 ? 1 : n;; ++m) {
+        int r = m;
+        for (int f : {2, 3, 5})
+            while (r % f == 0) r /= f;
+        if (r == 1) return m;
+    }
+}
+
+static void split_df(long double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (long double)hi);
+}
+
+int fft_plan_init(Plan *p, FftPlan &f, int M) {
+    f.M = M;
+    f.nst = 0;
+    int r = M;
+    const int order[4] = {4, 2, 3, 5};
+    for (int oi = 0; oi < 4; ++oi) {
+        int R = order[oi];
+        while (r % R == 0 && r > 1) {
+            if (f.nst >= kMaxRadixStages) return set_error(p, BTTB_ERR_INVALID_ARG, "FFT length has too many factors");
+            f.radix[f.nst++] = R;
+            r /= R;
+        }
+    }
+    if (r != 1) return set_error(p, BTTB_ERR_INVALID_ARG, "FFT length is not 5-smooth");
+    const int ntab = M + 5;
+    std::vector<double2> t64(ntab);
+    std::vector<float4> tdf(ntab);
+    std::vector<float2> t32(ntab);
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    std::vector<long double> re(ntab), im(ntab);
+    for (int t = 0; t < M; ++t) {
+        long double a = -two_pi * (long double)t / (long double)M;
+        re[t] = cosl(a);
+        im[t] = sinl(a);
+    }
+    const long double sq5 = sqrtl(5.0L);
+    const long double consts[5] = {(sq5 - 1.0L) / 4.0L, -(sq5 + 1.0L) / 4.0L, sqrtl((5.0L + sq5) / 8.0L),
+                                   sqrtl((5.0L - sq5) / 8.0L), sqrtl(3.0L) / 2.0L};
+    for (int c = 0; c < 5; ++c) {
+        re[M + c] = consts[c];
+        im[M + c] = 0.0L;
+    }
+    for (int t = 0; t < ntab; ++t) {
+        t64[t] = make_double2((double)re[t], (double)im[t]);
+        float rh, rl, ih, il;
+        split_df(re[t], rh, rl);
+        split_df(im[t], ih, il);
+        tdf[t] = make_float4(rh, ih, rl, il);
+        t32[t] = make_float2(rh, ih);
+    }
+    cudaError_t e;
+    if ((e = cudaMalloc(&f.tw_f64, ntab * sizeof(double2))) != cudaSuccess) return check_cuda(p, e, "twiddles");
+    if ((e = cudaMalloc(&f.tw_df, ntab * sizeof(float4))) != cudaSuccess) return check_cuda(p, e, "twiddles");
+    if ((e = cudaMalloc(&f.tw_f32, ntab * sizeof(float2))) != cudaSuccess) return check_cuda(p, e, "twiddles");
+    cudaMemcpy(f.tw_f64, t64.data(), ntab * sizeof(double2), cudaMemcpyHostToDevice);
+    cudaMemcpy(f.tw_df, tdf.data(), ntab * sizeof(float4), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(f.tw_f32, t32.data(), ntab * sizeof(float2), cudaMemcpyHostToDevice);
+    return check_cuda(p, e, "twiddle upload");
+}
+
+void fft_plan_free(FftPlan &f) {
+    cudaFree(f.tw_f64);
+    cudaFree(f.tw_df);
+    cudaFree(f.tw_f32);
+    f.tw_f64 = nullptr;
+    f.tw_df = nullptr;
+    f.tw_f32 = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Radix butterflies.  sg = -1 for the forward transform (exp(-2 pi i kn/R)),
+// +1 for the inverse (unnormalised).  The radix-3 and radix-5 forms are the
+// usual symmetric splittings into sums and differences of mirrored inputs.
+// ---------------------------------------------------------------------------
+template <class A>
+struct Butterfly {
+    using C = typename A::C;
+    using K = typename A::K;
+
+    __device__ static void r2(C *v) {
+        C a = A::add(v[0], v[1]), b = A::sub(v[0], v[1]);
+        v[0] = a;
+        v[1] = b;
+    }
+    __device__ static void r4(C *v, int sg) {
+        C a0 = A::add(v[0], v[2]), a1 = A::sub(v[0], v[2]);
+        C a2 = A::add(v[1], v[3]), a3 = A::mul_i(A::sub(v[1], v[3]), sg);
+        v[0] = A::add(a0, a2);
+        v[2] = A::sub(a0, a2);
+        v[1] = A::add(a1, a3);
+        v[3] = A::sub(a1, a3);
+    }
+    __device__ static void r3(C *v, int sg, K s3) {
+        C s = A::add(v[1], v[2]), d = A::sub(v[1], v[2]);
+        C y0 = A::add(v[0], s);
+        C t = A::sub(v[0], A::half(s));
+        C u = A::mul_i(A::mul_k(d, s3), sg);
+        v[0] = y0;
+        v[1] = A::add(t, u);
+        v[2] = A::sub(t, u);
+    }
+    __device__ static void r5(C *v, int sg, K c1, K c2, K s1, K s2) {
+        C a1 = A::add(v[1], v[4]), a2 = A::add(v[2], v[3]);
+        C b1 = A::sub(v[1], v[4]), b2 = A::sub(v[2], v[3]);
+        C y0 = A::add(A::add(v[0], a1), a2);
+        C t1 = A::add(A::add(v[0], A::mul_k(a1, c1)), A::mul_k(a2, c2));
+        C t2 = A::add(A::add(v[0], A::mul_k(a1, c2)), A::mul_k(a2, c1));
+        C u1 = A::mul_i(A::add(A::mul_k(b1, s1), A::mul_k(b2, s2)), sg);
+        C u2 = A::mul_i(A::sub(A::mul_k(b1, s2), A::mul_k(b2, s1)), sg);
+        v[0] = y0;
+        v[1] = A::add(t1, u1);
+        v[4] = A::sub(t1, u1);
+        v[2] = A::add(t2, u2);
+        v[3] = A::sub(t2, u2);
+    }
+};
+
+template <class A>
+__device__ __forceinline__ typename A::K real_const(const typename A::C &c);
+template <>
+__device__ __forceinline__ double real_const<F64N>(const double2 &c) { return c.x; }
+template <>
+__device__ __forceinline__ df real_const<DF64>(const cdf &c) { return df{c.rh, c.rl}; }
+template <>
+__device__ __forceinline__ float real_const<F32>(const float2 &c) { return c.x; }
+
+template <class A>
+__device__ __forceinline__ typename A::C scale_by(typename A::C v, double s);
+template <>
+__device__ __forceinline__ double2 scale_by<F64N>(double2 v, double s) { return make_double2(v.x * s, v.y * s); }
+template <>
+__device__ __forceinline__ cdf scale_by<DF64>(cdf v, double s) { return DF64::mul_k(v, df_from_double(s)); }
+template <>
+__device__ __forceinline__ float2 scale_by<F32>(float2 v, double s) {
+    float f = (float)s;
+    return make_float2(v.x * f, v.y * f);
+}
+
+constexpr int kFftThreads = 256;
+
+template <class A, int INF, int OUTF, bool INV>
+__global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) {
+    using C = typename A::C;
+    using K = typename A::K;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *buf0 = tw + (a.M + 8);
+    C *buf1 = buf0 + (long)a.M * a.P;
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int o = blockIdx.x, c = blockIdx.z;
+    const int p0 = blockIdx.y * a.P;
+    const int P = a.P, lP = a.log2P, M = a.M;
+
+    const C *twg = reinterpret_cast<const C *>(a.tw);
+    for (int i = tid; i < M + 5; i += nt) tw[i] = twg[i];
+
+    long ibase = (long)c * a.in_cs + (long)o * a.in_os;
+    if (a.in_sel) ibase += (long)(*a.in_sel) * a.in_sel_stride;
+    const double scl = a.in_scale ? a.in_scale[c] : 1.0;
+    for (int idx = tid; idx < M * P; idx += nt) {
+        const int n = idx >> lP, pp = idx & (P - 1), pi = p0 + pp;
+        C v = A::zero();
+        if (n < a.nin && pi < a.pdim) {
+            v = load_vec<A, INF>(a.in, ibase + (long)n * a.in_ns + pi);
+            if (a.in_scale) v = scale_by<A>(v, scl);
+        }
+        buf0[idx] = v;
+    }
+    __syncthreads();
+
+    const K s3 = real_const<A>(tw[M + 4]);
+    const K c1 = real_const<A>(tw[M + 0]), c2 = real_const<A>(tw[M + 1]);
+    const K s1 = real_const<A>(tw[M + 2]), s2 = real_const<A>(tw[M + 3]);
+    const int sg = INV ? 1 : -1;
+
+    C *src = buf0, *dst = buf1;
+    int Ns = 1;
+    for (int s = 0; s < a.nst; ++s) {
+        const int R = a.radix[s];
+        const int m = M / R;
+        const int tstep = M / (Ns * R);
+        for (int idx = tid; idx < m * P; idx += nt) {
+            const int j = idx >> lP, pp = idx & (P - 1);
+            const int k = j % Ns;
+            C v[5];
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < R) v[r] = src[((long)(j + r * m) << lP) + pp];
+            if (k != 0) {
+#pragma unroll
+                for (int r = 1; r < 5; ++r)
+                    if (r < R) v[r] = A::cmul(v[r], tw[r * k * tstep], INV);
+            }
+            switch (R) {
+                case 2: Butterfly<A>::r2(v); break;
+                case 3: Butterfly<A>::r3(v, sg, s3); break;
+                case 4: Butterfly<A>::r4(v, sg); break;
+                default: Butterfly<A>::r5(v, sg, c1, c2, s1, s2); break;
+            }
+            const int dbase = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < R) dst[((long)(dbase + r * Ns) << lP) + pp] = v[r];
+        }
+        __syncthreads();
+        C *t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+    }
+
+    const long obase = (long)c * a.out_cs + (long)o * a.out_os;
+    for (int idx = tid; idx < a.nout * P; idx += nt) {
+        const int n = idx >> lP, pp = idx & (P - 1), pi = p0 + pp;
+        if (pi < a.pdim) store_vec<A, OUTF>(a.out, obase + (long)n * a.out_ns + pi, src[idx]);
+    }
+}
+
+template <class A, int INF, int OUTF, bool INV>
+static int launch_one(Plan *p, const FftPass &a) {
+    using C = typename A::C;
+    size_t smem = ((size_t)a.M + 8 + 2 * (size_t)a.M * a.P) * sizeof(C);
+    auto kern = fft_pass_kernel<A, INF, OUTF, INV>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return check_cuda(p, e, "fft smem attribute");
+    }
+    dim3 grid(a.O, (a.pdim + a.P - 1) / a.P, a.ncols);
+    const int tok = prof_begin(p, BTTB_K_FFT);
+    kern<<<grid, kFftThreads, smem, p->stream>>>(a);
+    count_launch(p);
+    auto esz = [](int f) { return f == FMT_C128 ? 16.0 : (f == FMT_C64 ? 8.0 : 16.0); };
+    prof_end(p, tok, (double)a.O * a.pdim * a.ncols * (a.nin * esz(INF) + a.nout * esz(OUTF)));
+    return check_cuda(p, cudaGetLastError(), "fft pass launch");
+}
+
+template <class A>
+static int dispatch_fmt(Plan *p, const FftPass &a, int infmt, int outfmt, bool inv) {
+    constexpr int NF = native_fmt<A>;
+    if (!inv) {
+        if (outfmt != NF) return set_error(p, BTTB_ERR_INVALID_ARG, "forward pass writes native format only");
+        switch (infmt) {
+            case FMT_C128: return launch_one<A, FMT_C128, NF, false>(p, a);
+            case FMT_C64: return launch_one<A, FMT_C64, NF, false>(p, a);
+            default: return launch_one<A, FMT_CDF, NF, false>(p, a);
+        }
+    } else {
+        if (infmt != NF) return set_error(p, BTTB_ERR_INVALID_ARG, "inverse pass reads native format only");
+        switch (outfmt) {
+            case FMT_C128: return launch_one<A, NF, FMT_C128, true>(p, a);
+            case FMT_C64: return launch_one<A, NF, FMT_C64, true>(p, a);
+            default: return launch_one<A, NF, FMT_CDF, true>(p, a);
+        }
+    }
+}
+
+static int choose_P(int M, int pdim, size_t elem) {
+    int P = 1;
+    while (P < 16 && P < pdim) P <<= 1;
+    while (P > 1 && ((size_t)M + 8 + 2 * (size_t)M * P) * elem > 96 * 1024) P >>= 1;
+    return P;
+}
+
+int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool inverse) {
+    const FftPlan &f = (a.M == p->fx.M) ? p->fx : p->fy;
+    if (f.M != a.M) return set_error(p, BTTB_ERR_INVALID_ARG, "no FFT plan for this length");
+    a.nst = f.nst;
+    for (int i = 0; i < f.nst; ++i) a.radix[i] = f.radix[i];
+    size_t elem = prec == PREC_F32 ? 8 : 16;
+    a.P = choose_P(a.M, a.pdim, elem);
+    a.log2P = 0;
+    while ((1 << a.log2P) < a.P) ++a.log2P;
+    if (a.O <= 0 || a.ncols <= 0 || a.pdim <= 0) return BTTB_OK;
+    switch (prec) {
+        case PREC_F64N: a.tw = f.tw_f64; return dispatch_fmt<F64N>(p, a, infmt, outfmt, inverse);
+        case PREC_F32: a.tw = f.tw_f32; return dispatch_fmt<F32>(p, a, infmt, outfmt, inverse);
+        default: a.tw = f.tw_df; return dispatch_fmt<DF64>(p, a, infmt, outfmt, inverse);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Generator spectrum (one-time, binary64): Eq. (circL2) places T[i,j] at cell
+// slot (i mod mx, j mod my); Eq. (multL) needs the 2-D DFT of that block
+// column for each of the b*b entries.
+// ---------------------------------------------------------------------------
+__global__ void gen_check_kernel(const double2 *g, long count, int *err) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+        double2 v = g[i];
+        if (!isfinite(v.x) || !isfinite(v.y)) atomicOr(err, DEVERR_NONFINITE);
+    }
+}
+
+__global__ void gen_widen_kernel(const float2 *src, double2 *dst, long count) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
+        dst[i] = make_double2(src[i].x, src[i].y);
+}
+
+// w[sy][sx][e] = T[i,j][e] at (sx, sy) = (i mod mx, j mod my), zero elsewhere.
+__global__ void gen_scatter_kernel(const double2 *gen, double2 *w, int nx, int ny, int mx, int my, int bb) {
+    const int sx = blockIdx.x, sy = blockIdx.y;
+    int i = sx < nx ? sx : sx - mx;       // offsets 0..nx-1 then -(nx-1)..-1
+    int j = sy < ny ? sy : sy - my;
+    const bool on = (i > -nx && i < nx && j > -ny && j < ny);
+    double2 *dst = w + ((long)sy * mx + sx) * bb;
+    const double2 *src = on ? gen + ((long)(j + ny - 1) * (2 * nx - 1) + (i + nx - 1)) * bb : nullptr;
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) dst[e] = on ? src[e] : make_double2(0.0, 0.0);
+}
+
+// Scale by 1/(mx*my), transpose each bin to column-major, split into copies.
+__global__ void gen_finish_kernel(const double2 *w, long bins, int b, long gbs, double scale, float2 *hi,
+                                  float2 *lo, double2 *f64, int *err) {
+    const long bin = blockIdx.x;
+    const int bb = b * b;
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) {
+        const int pr = e / b, q = e % b;           // source entry (p, q) row-major
+        double2 v = w[bin * bb + e];
+        v.x *= scale;
+        v.y *= scale;
+        if (!isfinite(v.x) || !isfinite(v.y)) atomicOr(err, DEVERR_NONFINITE);
+        const long d = bin * gbs + (long)q * b + pr;
+        if (f64) f64[d] = v;
+        if (hi) {
+            df r = df_from_double(v.x), i = df_from_double(v.y);
+            hi[d] = make_float2(r.hi, i.hi);
+            if (lo) lo[d] = make_float2(r.lo, i.lo);
+        }
+    }
+}
+
+int spectrum_compute(Plan *p, const void *gen, bttb_dtype dtype, int gen_is_host) {
+    const int nx = p->nx, ny = p->ny, b = p->b, mx = p->mx, my = p->my;
+    const long bb = (long)b * b;
+    const long ngen = (long)(2 * nx - 1) * (2 * ny - 1) * bb;
+    const long nw = p->bins * bb;
+    double2 *g64 = nullptr, *w1 = nullptr, *w2 = nullptr;
+    void *gtmp = nullptr;
+    cudaError_t e;
+    int rc = BTTB_OK;
+    auto fail = [&](cudaError_t ee, const char *what) {
+        rc = check_cuda(p, ee, what);
+        return rc;
+    };
+    if ((e = cudaMalloc(&g64, ngen * sizeof(double2))) != cudaSuccess) { fail(e, "generator buffer"); goto done; }
+    if ((e = cudaMalloc(&w1, nw * sizeof(double2))) != cudaSuccess) { fail(e, "spectrum workspace"); goto done; }
+    if ((e = cudaMalloc(&w2, nw * sizeof(double2))) != cudaSuccess) { fail(e, "spectrum workspace"); goto done; }
+    if (dtype == BTTB_C128) {
+        e = cudaMemcpyAsync(g64, gen, ngen * sizeof(double2),
+                            gen_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, p->stream);
+        if (e != cudaSuccess) { fail(e, "generator copy"); goto done; }
+    } else {
+        const void *src = gen;
+        if (gen_is_host) {
+            if ((e = cudaMalloc(&gtmp, ngen * sizeof(float2))) != cudaSuccess) { fail(e, "generator copy"); goto done; }
+            e = cudaMemcpyAsync(gtmp, gen, ngen * sizeof(float2), cudaMemcpyHostToDevice, p->stream);
+            if (e != cudaSuccess) { fail(e, "generator copy"); goto done; }
+            src = gtmp;
+        }
+        gen_widen_kernel<<<256, 256, 0, p->stream>>>((const float2 *)src, g64, ngen);
+    }
+    gen_check_kernel<<<256, 256, 0, p->stream>>>(g64, ngen, p->d_err);
+    gen_scatter_kernel<<<dim3(mx, my), 256, 0, p->stream>>>(g64, w1, nx, ny, mx, my, (int)bb);
+    count_launch(p, dtype == BTTB_C128 ? 2 : 3);
+    if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "scatter"); goto done; }
+    {
+        // x level: transforms over sx for each (sy, entry)
+        FftPass a{};
+        a.in = w1; a.out = w2;
+        a.in_cs = a.out_cs = 0;
+        a.in_os = a.out_os = (long)mx * bb;
+        a.in_ns = a.out_ns = bb;
+        a.O = my; a.pdim = (int)bb; a.ncols = 1;
+        a.nin = a.nout = mx; a.M = mx;
+        if ((rc = fft_pass_launch(p, a, PREC_F64N, FMT_C128, FMT_C128, false)) != BTTB_OK) goto done;
+        // y level: transforms over sy for each (kx, entry)
+        FftPass c{};
+        c.in = w2; c.out = w1;
+        c.in_os = c.out_os = bb;
+        c.in_ns = c.out_ns = (long)mx * bb;
+        c.O = mx; c.pdim = (int)bb; c.ncols = 1;
+        c.nin = c.nout = my; c.M = my;
+        if ((rc = fft_pass_launch(p, c, PREC_F64N, FMT_C128, FMT_C128, false)) != BTTB_OK) goto done;
+    }
+    gen_finish_kernel<<<(unsigned)p->bins, 256, 0, p->stream>>>(w1, p->bins, b, p->gbs, 1.0 / ((double)mx * my),
+                                                                 p->ghat_hi, p->ghat_lo, p->ghat_f64, p->d_err);
+    count_launch(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "spectrum finish"); goto done; }
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) { fail(e, "spectrum sync"); goto done; }
+done:
+    cudaFree(g64);
+    cudaFree(w1);
+    cudaFree(w2);
+    cudaFree(gtmp);
+    return rc;
+}
+
+}  // namespace bttb

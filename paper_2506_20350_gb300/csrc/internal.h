@@ -1,0 +1,127 @@
+// Host-side plan object and the internal launch interface shared by the
+// translation units of libbttb.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bttb.h"
+
+namespace bttb {
+
+constexpr int kMaxRadixStages = 24;
+constexpr int kMaxM = 2048;          // largest FFT length (grid side) supported
+constexpr int kContractKC = 4;       // right-hand sides per pass of the block product
+
+// Radix plan and twiddle tables of one FFT length.  Tables hold
+// exp(-2 pi i t / M) for t < M, followed by five real constants of the
+// radix-3/5 butterflies in the real parts: cos(2pi/5), cos(4pi/5),
+// sin(2pi/5), sin(4pi/5), sin(pi/3).
+struct FftPlan {
+    int M = 0;
+    int nst = 0;
+    int radix[kMaxRadixStages] = {};
+    double2 *tw_f64 = nullptr;   // device
+    float4 *tw_df = nullptr;     // device, double-float {re.hi, im.hi, re.lo, im.lo}
+    float2 *tw_f32 = nullptr;    // device
+};
+
+// One batched strided 1-D FFT pass (see fft.cu).
+struct FftPass {
+    const void *in;
+    void *out;
+    long in_cs, in_os, in_ns;     // strides (elements) of column, outer index, element index
+    long out_cs, out_os, out_ns;
+    const int *in_sel;            // optional device index: input offset += (*in_sel) * in_sel_stride
+    long in_sel_stride;
+    const double *in_scale;       // optional device per-column scale applied on load (binary64)
+    int O;                        // number of outer indices
+    int pdim;                     // contiguous inner count (bases, or b*b entries)
+    int ncols;
+    int nin, nout;                // nonzero input elements, kept output elements
+    int M, nst;
+    int radix[kMaxRadixStages];
+    const void *tw;
+    int P, log2P;                 // inner chunk per CTA (power of two)
+};
+
+enum Prec { PREC_DF64 = BTTB_MV_FP64, PREC_F32 = BTTB_MV_FP32, PREC_F64N = BTTB_MV_FP64_NATIVE };
+
+struct GmresWork;
+
+struct Plan {
+    int nx = 0, ny = 0, b = 0, mx = 0, my = 0, max_rhs = 0;
+    long n = 0;                   // nx*ny*b
+    long bins = 0;                // mx*my
+    unsigned prec_mask = 0;
+    cudaStream_t stream = nullptr;
+    int dev = 0, nsm = 0;
+    size_t smem_optin = 0;
+    FftPlan fx, fy;
+
+    // Spectrum copies, scaled by 1/(mx*my).  Bin k holds its b x b block
+    // column-major (entry (p, q) at q*b + p) at offset k*gbs elements.
+    float2 *ghat_hi = nullptr;    // binary32 rounding of the spectrum
+    float2 *ghat_lo = nullptr;    // binary32 remainder (double-float low plane)
+    double2 *ghat_f64 = nullptr;  // binary64 copy
+    long gbs = 0;
+    bool have_gen = false;
+
+    // Block-Jacobi: R_0^{-1} (row-major b x b, binary32) for P_K of Sec. III-B.
+    float2 *bj_inv = nullptr;
+    bool bj_ready = false;
+
+    // Product workspace: two buffers of bins * ubs * 16 bytes.
+    void *wsA = nullptr, *wsB = nullptr;
+    long ubs = 0;                 // bin stride (elements) of the spectral vectors
+    size_t ws_bytes = 0;
+
+    GmresWork *gw = nullptr;
+    int *d_err = nullptr;         // device error word
+    size_t bytes_held = 0;
+
+    // Profiling (bttb_profile): event pairs around timed launches, launch count.
+    struct ProfRec { int ev0, ev1, kid; double bytes; };
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    int ev_used = 0;
+    std::vector<ProfRec> recs;
+    long launches = 0;
+};
+
+// Profiling helpers (bttb.cu).  prof_begin returns a token for prof_end, or -1.
+int prof_begin(Plan *p, int kid);
+void prof_end(Plan *p, int token, double bytes);
+inline void count_launch(Plan *p, int n = 1) { p->launches += n; }
+
+// Thread-local error message helpers (bttb.cu).
+int set_error(Plan *p, int code, const std::string &msg);
+int check_cuda(Plan *p, cudaError_t e, const char *what);
+
+// fft.cu
+int fft_plan_init(Plan *p, FftPlan &f, int M);
+void fft_plan_free(FftPlan &f);
+int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool inverse);
+int spectrum_compute(Plan *p, const void *gen, bttb_dtype dtype, int gen_is_host);
+int smallest_5smooth(int n);
+
+// contract.cu
+int contract_launch(Plan *p, int prec, const void *u, void *v, int k);
+
+// matvec.cu
+// y[:, c] = Z x[:, c]; xfmt/yfmt are VecFmt values; in_sel/in_scale as in FftPass.
+int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int nrhs, int prec,
+               const int *in_sel = nullptr, long in_sel_stride = 0, const double *in_scale = nullptr);
+int block_jacobi_run(Plan *p, const void *x, int xfmt, long ldx, void *z, int zfmt, long ldz, int nrhs,
+                     const int *in_sel = nullptr, long in_sel_stride = 0);
+int block_jacobi_setup(Plan *p, const double2 *t00_host);
+
+// gmres.cu
+int gmres_solve(Plan *p, const void *V, void *I, int nrhs, long ld, const bttb_gmres_opts *o,
+                bttb_col_result *out);
+void gmres_free(Plan *p);
+
+}  // namespace bttb

@@ -1,0 +1,229 @@
+// The multilevel-FFT product y = Z x (Sec. II-C and III-A) as five
+// stream-ordered passes over the plan workspace:
+//   1. pad + forward FFT along the cells of each row      x  -> U  (ny rows kept)
+//   2. forward FFT along the rows of each column          U  -> u^ (all my rows)
+//   3. per-bin block product (contract.cu)                u^ -> v^
+//   4. inverse FFT along the rows, crop to ny rows        v^ -> V
+//   5. inverse FFT along the cells, crop to nx cells      V  -> y
+// Passes 1/2 together are the forward 2-level blockwise FFT of App. B (the
+// padding of Eq. (xc2) is implicit: the zero slots are never read, the pass
+// zero-fills them on chip); passes 4/5 are its inverse with the crop of
+// Sec. II-C.  The 1/(mx my) of the inverse is folded into the stored spectrum.
+//
+// Layouts (elements of the precision's native complex type):
+//   U, V : [c][iy][kx][p]         at c*ny*mx*b + iy*mx*b + kx*b + p
+//   u^,v^: [bin][c][p]            at (ky*mx + kx)*ubs + c*b + p
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "arith.cuh"
+#include "internal.h"
+
+namespace bttb {
+
+static int native_of(int prec) { return prec == PREC_F64N ? FMT_C128 : (prec == PREC_F32 ? FMT_C64 : FMT_CDF); }
+
+int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int nrhs, int prec,
+               const int *in_sel, long in_sel_stride, const double *in_scale) {
+    const int nx = p->nx, ny = p->ny, b = p->b, mx = p->mx, my = p->my;
+    const int NF = native_of(prec);
+    const long plane = (long)ny * mx * b;
+    int rc;
+
+    FftPass a{};
+    a.in = x; a.out = p->wsB;
+    a.in_cs = ldx; a.in_os = (long)nx * b; a.in_ns = b;
+    a.out_cs = plane; a.out_os = (long)mx * b; a.out_ns = b;
+    a.in_sel = in_sel; a.in_sel_stride = in_sel_stride; a.in_scale = in_scale;
+    a.O = ny; a.pdim = b; a.ncols = nrhs;
+    a.nin = nx; a.nout = mx; a.M = mx;
+    if ((rc = fft_pass_launch(p, a, prec, xfmt, NF, false)) != BTTB_OK) return rc;
+
+    FftPass c{};
+    c.in = p->wsB; c.out = p->wsA;
+    c.in_cs = plane; c.in_os = b; c.in_ns = (long)mx * b;
+    c.out_cs = b; c.out_os = p->ubs; c.out_ns = (long)mx * p->ubs;
+    c.O = mx; c.pdim = b; c.ncols = nrhs;
+    c.nin = ny; c.nout = my; c.M = my;
+    if ((rc = fft_pass_launch(p, c, prec, NF, NF, false)) != BTTB_OK) return rc;
+
+    if ((rc = contract_launch(p, prec, p->wsA, p->wsB, nrhs)) != BTTB_OK) return rc;
+
+    FftPass d{};
+    d.in = p->wsB; d.out = p->wsA;
+    d.in_cs = b; d.in_os = p->ubs; d.in_ns = (long)mx * p->ubs;
+    d.out_cs = plane; d.out_os = b; d.out_ns = (long)mx * b;
+    d.O = mx; d.pdim = b; d.ncols = nrhs;
+    d.nin = my; d.nout = ny; d.M = my;
+    if ((rc = fft_pass_launch(p, d, prec, NF, NF, true)) != BTTB_OK) return rc;
+
+    FftPass e{};
+    e.in = p->wsA; e.out = y;
+    e.in_cs = plane; e.in_os = (long)mx * b; e.in_ns = b;
+    e.out_cs = ldy; e.out_os = (long)nx * b; e.out_ns = b;
+    e.O = ny; e.pdim = b; e.ncols = nrhs;
+    e.nin = mx; e.nout = nx; e.M = mx;
+    return fft_pass_launch(p, e, prec, NF, yfmt, true);
+}
+
+// ---------------------------------------------------------------------------
+// Block-Jacobi preconditioner P_K (Sec. III-B): every cell's b-block is
+// multiplied by R_0^{-1}, R_0 = T[0,0].  The inverse is formed once on the
+// host from an LU factorisation with partial pivoting (binary64) and applied
+// in binary32 as a batched b x b GEMV: it only steers the Krylov space of a
+// flexible GMRES, which stores the preconditioned vectors it used.
+// ---------------------------------------------------------------------------
+constexpr int kBjThreads = 256;
+
+template <int INF, int OUTF>
+__global__ void __launch_bounds__(kBjThreads) bj_apply_kernel(const float2 *rinv, const void *x, long ldx, void *z,
+                                                               long ldz, int b, int ncells, int cpb,
+                                                               const int *in_sel, long in_sel_stride,
+                                                               int rinv_in_smem) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *xs = reinterpret_cast<float2 *>(smem_raw);       // cpb*b
+    float2 *rsm = xs + (long)cpb * b;                         // b*b, row-major (when it fits)
+    const float2 *rs = rinv_in_smem ? rsm : rinv;
+    const int c = blockIdx.y;
+    const int cell0 = blockIdx.x * cpb;
+    const int nc = min(cpb, ncells - cell0);
+    if (rinv_in_smem)
+        for (int i = threadIdx.x; i < b * b; i += blockDim.x) rsm[i] = rinv[i];
+    long xoff = (long)c * ldx + (long)cell0 * b;
+    if (in_sel) xoff += (long)(*in_sel) * in_sel_stride;
+    for (int i = threadIdx.x; i < nc * b; i += blockDim.x) xs[i] = load_vec<F32, INF>(x, xoff + i);
+    __syncthreads();
+    long zoff = (long)c * ldz + (long)cell0 * b;
+    if (in_sel) zoff += (long)(*in_sel) * in_sel_stride;       // same selected column slot on output
+    for (int o = threadIdx.x; o < nc * b; o += blockDim.x) {
+        const int cl = o / b, pr = o % b;
+        const float2 *row = rs + (long)pr * b;
+        const float2 *xv = xs + (long)cl * b;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int q = 0; q < b; ++q) {
+            float2 g = row[q], u = xv[q];
+            acc.x = fmaf(g.x, u.x, acc.x);
+            acc.x = fmaf(-g.y, u.y, acc.x);
+            acc.y = fmaf(g.x, u.y, acc.y);
+            acc.y = fmaf(g.y, u.x, acc.y);
+        }
+        store_vec<F32, OUTF>(z, zoff + o, acc);
+    }
+}
+
+template <int INF, int OUTF>
+static int bj_launch(Plan *p, const void *x, long ldx, void *z, long ldz, int nrhs, const int *in_sel,
+                     long in_sel_stride) {
+    const int b = p->b, ncells = p->nx * p->ny;
+    int cpb = (8 * 1024) / b;                                  // cells per CTA
+    if (cpb < 1) cpb = 1;
+    if (cpb > ncells) cpb = ncells;
+    const size_t xs_bytes = (size_t)cpb * b * sizeof(float2);
+    const size_t r_bytes = (size_t)b * b * sizeof(float2);
+    const int in_smem = (xs_bytes + r_bytes <= 160 * 1024) ? 1 : 0;
+    const size_t smem = xs_bytes + (in_smem ? r_bytes : 0);
+    auto kern = bj_apply_kernel<INF, OUTF>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return check_cuda(p, e, "block-Jacobi smem attribute");
+    }
+    dim3 grid((ncells + cpb - 1) / cpb, nrhs);
+    kern<<<grid, kBjThreads, smem, p->stream>>>(p->bj_inv, x, ldx, z, ldz, b, ncells, cpb, in_sel, in_sel_stride,
+                                                in_smem);
+    count_launch(p);
+    return check_cuda(p, cudaGetLastError(), "block-Jacobi launch");
+}
+
+int block_jacobi_run(Plan *p, const void *x, int xfmt, long ldx, void *z, int zfmt, long ldz, int nrhs,
+                     const int *in_sel, long in_sel_stride) {
+    if (!p->bj_ready) return set_error(p, BTTB_ERR_NO_GENERATORS, "block-Jacobi needs bttb_set_generators first");
+#define BJ_CASE(I, O)                                     \
+    if (xfmt == I && zfmt == O) return bj_launch<I, O>(p, x, ldx, z, ldz, nrhs, in_sel, in_sel_stride);
+    BJ_CASE(FMT_C128, FMT_C128)
+    BJ_CASE(FMT_C64, FMT_C64)
+    BJ_CASE(FMT_CDF, FMT_CDF)
+#undef BJ_CASE
+    return set_error(p, BTTB_ERR_INVALID_ARG, "block-Jacobi: unsupported format pair");
+}
+
+// LU with partial pivoting of the b x b self block (binary64), then its
+// inverse column by column; singular pivots are reported, not divided by.
+int block_jacobi_setup(Plan *p, const double2 *t00) {
+    const int b = p->b;
+    std::vector<double> ar(2L * b * b);
+    for (long i = 0; i < (long)b * b; ++i) {
+        ar[2 * i] = t00[i].x;
+        ar[2 * i + 1] = t00[i].y;
+    }
+    auto A = [&](int r, int c) -> double * { return &ar[2 * ((long)r * b + c)]; };
+    std::vector<int> piv(b);
+    double amax = 0.0;
+    for (long i = 0; i < (long)b * b; ++i) amax = std::max(amax, std::hypot(ar[2 * i], ar[2 * i + 1]));
+    for (int k = 0; k < b; ++k) {
+        int pk = k;
+        double best = std::hypot(A(k, k)[0], A(k, k)[1]);
+        for (int i = k + 1; i < b; ++i) {
+            double v = std::hypot(A(i, k)[0], A(i, k)[1]);
+            if (v > best) { best = v; pk = i; }
+        }
+        piv[k] = pk;
+        if (!(best > 1e-300) || best < 1e-15 * amax) {
+            p->bj_ready = false;
+            return set_error(p, BTTB_ERR_SINGULAR, "block-Jacobi: T[0,0] is singular to working precision");
+        }
+        if (pk != k)
+            for (int j = 0; j < b; ++j) std::swap(A(k, j)[0], A(pk, j)[0]), std::swap(A(k, j)[1], A(pk, j)[1]);
+        const double dr = A(k, k)[0], di = A(k, k)[1], dd = dr * dr + di * di;
+        for (int i = k + 1; i < b; ++i) {
+            double *l = A(i, k);
+            const double lr = (l[0] * dr + l[1] * di) / dd, li = (l[1] * dr - l[0] * di) / dd;
+            l[0] = lr;
+            l[1] = li;
+            for (int j = k + 1; j < b; ++j) {
+                double *t = A(i, j);
+                const double *u = A(k, j);
+                t[0] -= lr * u[0] - li * u[1];
+                t[1] -= lr * u[1] + li * u[0];
+            }
+        }
+    }
+    std::vector<float2> inv((long)b * b);
+    std::vector<double> col(2 * b);
+    for (int e = 0; e < b; ++e) {
+        // solve R_0 x = e_e: permute, forward with unit L, back with U
+        for (int i = 0; i < b; ++i) col[2 * i] = col[2 * i + 1] = 0.0;
+        col[2 * e] = 1.0;
+        for (int k = 0; k < b; ++k)
+            if (piv[k] != k) std::swap(col[2 * k], col[2 * piv[k]]), std::swap(col[2 * k + 1], col[2 * piv[k] + 1]);
+        for (int i = 0; i < b; ++i)
+            for (int k = 0; k < i; ++k) {
+                const double *l = A(i, k);
+                col[2 * i] -= l[0] * col[2 * k] - l[1] * col[2 * k + 1];
+                col[2 * i + 1] -= l[0] * col[2 * k + 1] + l[1] * col[2 * k];
+            }
+        for (int i = b - 1; i >= 0; --i) {
+            double sr = col[2 * i], si = col[2 * i + 1];
+            for (int k = i + 1; k < b; ++k) {
+                const double *u = A(i, k);
+                sr -= u[0] * col[2 * k] - u[1] * col[2 * k + 1];
+                si -= u[0] * col[2 * k + 1] + u[1] * col[2 * k];
+            }
+            const double dr = A(i, i)[0], di = A(i, i)[1], dd = dr * dr + di * di;
+            col[2 * i] = (sr * dr + si * di) / dd;
+            col[2 * i + 1] = (si * dr - sr * di) / dd;
+        }
+        for (int i = 0; i < b; ++i) inv[(long)i * b + e] = make_float2((float)col[2 * i], (float)col[2 * i + 1]);
+    }
+    if (!p->bj_inv) {
+        cudaError_t e = cudaMalloc(&p->bj_inv, (size_t)b * b * sizeof(float2));
+        if (e != cudaSuccess) return check_cuda(p, e, "block-Jacobi buffer");
+        p->bytes_held += (size_t)b * b * sizeof(float2);
+    }
+    cudaError_t e = cudaMemcpy(p->bj_inv, inv.data(), (size_t)b * b * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return check_cuda(p, e, "block-Jacobi upload");
+    p->bj_ready = true;
+    return BTTB_OK;
+}
+
+}  // namespace bttb

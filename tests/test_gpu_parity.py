@@ -1,0 +1,297 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: the FP64 product (double-float or binary64) within 1e-12 relative
+of the oracle, the binary32 product within 1e-5 relative, every solve at the
+requested relative residual as measured with the oracle's product.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import arrays
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def bt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_20350_gb300 import build
+    build.build()
+    import paper_2506_20350_gb300 as m
+    m.load_library()
+    return m
+
+
+def _dev(x_kn):
+    return torch.from_numpy(np.ascontiguousarray(x_kn)).cuda()
+
+
+def _rand(rng, k, n):
+    return rng.standard_normal((k, n)) + 1j * rng.standard_normal((k, n))
+
+
+def _check(y, ref, tol, what=""):
+    scale = np.abs(ref).max()
+    err_inf = np.abs(y - ref).max() / scale
+    err_2 = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert err_inf <= tol and err_2 <= tol, f"{what}: max-rel {err_inf:.3e}, norm-rel {err_2:.3e} (tol {tol})"
+    return err_2
+
+
+ALL_PRECS = (1 << 0) | (1 << 1) | (1 << 2)
+
+
+# ------------------------------------------------------------------ products
+
+def test_tiny_product_all_precisions(bt):
+    c = arrays.CONFIGS["tiny"]
+    gen = arrays.generator_blocks(c["nx"], c["ny"], c["b"], c["seed"])
+    plan = bt.Plan(c["nx"], c["ny"], c["b"], max_rhs=3, prec_mask=ALL_PRECS)
+    plan.set_generators(gen)
+    assert (plan.mx, plan.my) == (8, 8)
+    x = _rand(np.random.default_rng(1), 3, plan.n)
+    ref = oracle.matvec(gen, x.T).T
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64).cpu().numpy(), ref, FP64_TOL, "df64")
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64_NATIVE).cpu().numpy(), ref, FP64_TOL, "binary64")
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP32).cpu().numpy(), ref, FP32_TOL, "binary32")
+    x32 = _dev(x.astype(np.complex64))
+    _check(plan.matvec(x32, prec=bt.BTTB_MV_FP32).cpu().numpy(), oracle.matvec(gen, x.astype(np.complex64).T).T,
+           FP32_TOL, "binary32 c64 io")
+
+
+@pytest.mark.parametrize("nx,ny,b,k", [
+    (5, 3, 7, 3),      # odd b, ragged chunks
+    (1, 1, 5, 1),      # single cell: dense GEMV
+    (1, 6, 3, 2),      # one column of cells
+    (7, 1, 4, 1),      # one row: 1-level block Toeplitz
+    (2, 2, 1, 5),      # scalar blocks, two contraction groups
+    (13, 9, 16, 2),    # grid 25 x 18: radix 5, 3, 2
+    (33, 5, 24, 1),    # grid 72 x 9
+    (4, 3, 96, 2),     # wide blocks: the spectrum is streamed in column chunks
+    (3, 2, 256, 1),    # largest b
+])
+def test_product_random_generators(bt, nx, ny, b, k):
+    gen = arrays.random_generator_blocks(nx, ny, b, seed=100 + nx + ny + b)
+    plan = bt.Plan(nx, ny, b, max_rhs=k, prec_mask=ALL_PRECS)
+    plan.set_generators(gen)
+    x = _rand(np.random.default_rng(2), k, plan.n)
+    ref = oracle.matvec(gen, x.T).T
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64).cpu().numpy(), ref, FP64_TOL, "df64")
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64_NATIVE).cpu().numpy(), ref, FP64_TOL, "binary64")
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP32).cpu().numpy(), ref, FP32_TOL, "binary32")
+
+
+def test_product_padded_leading_dimension_and_groups(bt):
+    nx, ny, b, k = 6, 4, 10, 9          # 9 columns -> three passes of the block product
+    gen = arrays.random_generator_blocks(nx, ny, b, seed=7)
+    plan = bt.Plan(nx, ny, b, max_rhs=k)
+    plan.set_generators(gen)
+    n = plan.n
+    ld = n + 13
+    x = _rand(np.random.default_rng(3), k, ld)
+    xd = _dev(x)
+    yd = torch.full_like(xd, 7.0 + 7.0j)
+    bt.bttb_matvec(plan.handle, xd, yd, k, ld, bt.BTTB_C128, bt.BTTB_MV_FP64)
+    y = yd.cpu().numpy()
+    ref = oracle.matvec(gen, x[:, :n].T).T
+    _check(y[:, :n], ref, FP64_TOL, "ld-padded")
+    assert np.all(y[:, n:] == 7.0 + 7.0j), "product wrote past N in a padded column"
+    bt.bttb_matvec(plan.handle, xd, yd, 0, ld, bt.BTTB_C128, bt.BTTB_MV_FP64)   # empty call is a no-op
+
+
+def test_largest_grid(bt):
+    nx, ny, b = 1024, 2, 2                # grid side 2048, the maximum
+    gen = arrays.random_generator_blocks(nx, ny, b, seed=8)
+    plan = bt.Plan(nx, ny, b)
+    plan.set_generators(gen)
+    assert plan.mx == 2048
+    x = _rand(np.random.default_rng(4), 1, plan.n)
+    _check(plan.matvec(_dev(x)).cpu().numpy(), oracle.matvec(gen, x.T).T, FP64_TOL, "largest grid")
+
+
+@pytest.mark.parametrize("nx,ny", [(5, 4), (3, 3), (6, 1)])
+def test_bccb_eigenpairs_on_gpu(bt, nx, ny):
+    gen, c = arrays.periodic_generator_blocks(nx, ny, seed=9)
+    lam = np.fft.fft2(c)
+    ix = np.tile(np.arange(nx), ny)
+    iy = np.repeat(np.arange(ny), nx)
+    modes = np.stack([np.exp(2j * np.pi * (kx * ix / nx + ky * iy / ny)) for ky in range(ny) for kx in range(nx)])
+    lam_row = np.array([lam[kx, ky] for ky in range(ny) for kx in range(nx)])
+    plan = bt.Plan(nx, ny, 1, max_rhs=nx * ny)
+    plan.set_generators(gen)
+    y = plan.matvec(_dev(modes)).cpu().numpy()
+    assert np.abs(y - lam_row[:, None] * modes).max() <= 1e-12 * np.abs(lam).max()
+
+
+def test_spectrum_matches_oracle(bt):
+    nx, ny, b = 5, 3, 4
+    gen = arrays.random_generator_blocks(nx, ny, b, seed=11)
+    plan = bt.Plan(nx, ny, b, prec_mask=ALL_PRECS)
+    plan.set_generators(gen)
+    ref = oracle.spectrum(gen, plan.mx, plan.my) / (plan.mx * plan.my)
+    for ky in range(plan.my):
+        for kx in range(plan.mx):
+            got = plan.spectrum_bin(ky, kx)
+            assert np.abs(got - ref[ky, kx]).max() <= 1e-13 * np.abs(ref).max()
+    plan_df = bt.Plan(nx, ny, b)
+    plan_df.set_generators(gen)
+    got = plan_df.spectrum_bin(1, 2)
+    assert np.abs(got - ref[1, 2]).max() <= 1e-13 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ full size
+
+@pytest.fixture(scope="module")
+def precision_case(bt):
+    c = arrays.CONFIGS["precision"]
+    gen = arrays.generator_blocks(c["nx"], c["ny"], c["b"], c["seed"])
+    plan = bt.Plan(c["nx"], c["ny"], c["b"], max_rhs=1, prec_mask=ALL_PRECS)
+    plan.set_generators(gen)
+    x = _rand(np.random.default_rng(5), 1, plan.n)
+    ref = oracle.matvec(gen, x.T).T           # O(N^2) brute force, 2.9e9 complex MACs
+    return c, gen, plan, x, ref
+
+
+def test_full_size_product(bt, precision_case):
+    c, gen, plan, x, ref = precision_case
+    assert (plan.mx, plan.my) == (60, 60)
+    e64 = _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64).cpu().numpy(), ref, FP64_TOL, "df64 30x30")
+    e64n = _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64_NATIVE).cpu().numpy(), ref, FP64_TOL, "binary64 30x30")
+    e32 = _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP32).cpu().numpy(), ref, FP32_TOL, "binary32 30x30")
+    print(f"30x30 b=60 product error vs oracle: df64 {e64:.2e}, binary64 {e64n:.2e}, binary32 {e32:.2e}")
+
+
+def test_full_size_sampled_rows(bt, precision_case):
+    c, gen, plan, x, ref = precision_case
+    y = plan.matvec(_dev(x)).cpu().numpy()[0]
+    rows = np.unique(np.concatenate([np.arange(0, 60), plan.n - 1 - np.arange(60),
+                                     np.random.default_rng(6).integers(0, plan.n, 200)]))
+    sampled = oracle.matvec_rows(gen, x[0], rows)
+    assert np.abs(y[rows] - sampled).max() <= FP64_TOL * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ solves
+
+def test_tiny_solve_matches_lu(bt):
+    c = arrays.CONFIGS["tiny"]
+    nx, ny, b = c["nx"], c["ny"], c["b"]
+    gen = arrays.generator_blocks(nx, ny, b, c["seed"])
+    cells = [(1, 1), (0, 0), (3, 2)]
+    v = arrays.port_excitations(nx, ny, b, cells).T.copy()
+    plan = bt.Plan(nx, ny, b, max_rhs=3)
+    plan.set_generators(gen)
+    sol, rc, res = plan.solve(_dev(v), tol=c["tol"], restart=c["restart"])
+    assert rc == bt.BTTB_OK
+    x = sol.cpu().numpy()
+    x_lu = oracle.lu_solve(oracle.assemble(gen), v.T).T
+    rr = oracle.relres(gen, v.T, x.T)
+    for col in range(3):
+        assert res[col].status == bt.BTTB_OK
+        assert rr[col] <= c["tol"], rr
+        assert abs(res[col].relres_true - rr[col]) <= 1e-3 * c["tol"] + 1e-12 * rr[col]
+        assert np.linalg.norm(x[col] - x_lu[col]) <= 1e-8 * np.linalg.norm(x_lu[col])
+
+
+@pytest.mark.parametrize("inner", ["fp64", "fp32"])
+def test_precision_solve(bt, precision_case, inner):
+    c, gen, plan, _, _ = precision_case
+    v = arrays.centre_excitation(c["nx"], c["ny"], c["b"])[None, :]
+    hist = np.zeros(64)
+    prec = bt.BTTB_MV_FP64 if inner == "fp64" else bt.BTTB_MV_FP32
+    sol, rc, res = plan.solve(_dev(v), tol=c["tol"], restart=c["restart"], inner=prec, history=hist)
+    assert rc == bt.BTTB_OK, bt.bttb_last_error()
+    rr = oracle.relres(gen, v.T, sol.cpu().numpy().T)[0]
+    print(f"30x30 solve inner={inner}: {res[0].iters} iterations, {res[0].cycles} cycles, oracle relres {rr:.3e}")
+    assert rr <= c["tol"]
+
+
+def test_block_jacobi_apply_matches_oracle(bt):
+    nx, ny, b = 4, 3, 12
+    gen = arrays.generator_blocks(nx, ny, b, seed=12)
+    plan = bt.Plan(nx, ny, b, max_rhs=2)
+    plan.set_generators(gen)
+    x = _rand(np.random.default_rng(13), 2, plan.n)
+    z = plan.block_jacobi(_dev(x)).cpu().numpy()
+    _check(z, oracle.block_jacobi_apply(gen, x.T).T, FP32_TOL, "block-Jacobi")
+
+
+def test_block_jacobi_solve(bt):
+    c = arrays.CONFIGS["tiny"]
+    nx, ny, b = c["nx"], c["ny"], c["b"]
+    gen = arrays.generator_blocks(nx, ny, b, c["seed"])
+    v = arrays.port_excitations(nx, ny, b, [(1, 1)]).T.copy()
+    plan = bt.Plan(nx, ny, b)
+    plan.set_generators(gen)
+    _, _, res0 = plan.solve(_dev(v), tol=c["tol"])
+    sol, rc, res = plan.solve(_dev(v), tol=c["tol"], pc=bt.BTTB_PC_BLOCK_JACOBI)
+    assert rc == bt.BTTB_OK
+    assert oracle.relres(gen, v.T, sol.cpu().numpy().T)[0] <= c["tol"]
+    assert res[0].iters <= res0[0].iters
+
+
+def test_host_io_and_initial_guess(bt):
+    c = arrays.CONFIGS["tiny"]
+    nx, ny, b = c["nx"], c["ny"], c["b"]
+    gen = arrays.generator_blocks(nx, ny, b, c["seed"])
+    v = arrays.port_excitations(nx, ny, b, [(2, 1)]).T.copy()
+    plan = bt.Plan(nx, ny, b)
+    plan.set_generators(gen)
+    vh = torch.from_numpy(v)
+    ih = torch.zeros_like(vh)
+    _, rc, res = plan.solve(vh, ih, tol=1e-10, host_io=True)
+    assert rc == bt.BTTB_OK
+    assert oracle.relres(gen, v.T, ih.numpy().T)[0] <= 1e-10
+    x_lu = torch.from_numpy(oracle.lu_solve(oracle.assemble(gen), v.T).T.copy()).cuda()
+    _, rc, res = plan.solve(_dev(v), x_lu.clone(), tol=1e-10, use_x0=True)
+    assert rc == bt.BTTB_OK and res[0].iters == 0
+
+
+# ------------------------------------------------------------------ failure paths (host-side)
+
+def test_not_converged_status(bt):
+    c = arrays.CONFIGS["tiny"]
+    gen = arrays.generator_blocks(c["nx"], c["ny"], c["b"], c["seed"])
+    v = arrays.port_excitations(c["nx"], c["ny"], c["b"], [(1, 1)]).T.copy()
+    plan = bt.Plan(c["nx"], c["ny"], c["b"])
+    plan.set_generators(gen)
+    sol, rc, res = plan.solve(_dev(v), tol=1e-12, max_iters=3, restart=50)
+    assert rc == bt.BTTB_NOT_CONVERGED and res[0].status == bt.BTTB_NOT_CONVERGED
+    assert res[0].iters == 3
+    rr = oracle.relres(gen, v.T, sol.cpu().numpy().T)[0]
+    assert abs(res[0].relres_true - rr) <= 1e-9
+
+
+def test_error_codes(bt):
+    c = arrays.CONFIGS["tiny"]
+    nx, ny, b = c["nx"], c["ny"], c["b"]
+    plan = bt.Plan(nx, ny, b, max_rhs=1)
+    x = _dev(np.ones((1, plan.n), dtype=np.complex128))
+    with pytest.raises(bt.BttbError) as e:
+        plan.matvec(x)
+    assert e.value.code == bt.BTTB_ERR_NO_GENERATORS
+    gen = arrays.generator_blocks(nx, ny, b, c["seed"])
+    bad = gen.copy()
+    bad[2, 3, 1, 1] = np.nan
+    with pytest.raises(bt.BttbError) as e:
+        plan.set_generators(bad)
+    assert e.value.code == bt.BTTB_ERR_NONFINITE
+    plan.set_generators(gen)
+    with pytest.raises(bt.BttbError) as e:
+        bt.bttb_matvec(plan.handle, x, x.clone(), 2, plan.n, bt.BTTB_C128, bt.BTTB_MV_FP64)
+    assert e.value.code == bt.BTTB_ERR_INVALID_ARG
+    with pytest.raises(bt.BttbError) as e:
+        bt.bttb_matvec(plan.handle, x, x.clone(), 1, plan.n, bt.BTTB_C128, bt.BTTB_MV_FP64_NATIVE)
+    assert e.value.code == bt.BTTB_ERR_INVALID_ARG           # copy not kept by this plan
+    zero_self = gen.copy()
+    zero_self[ny - 1, nx - 1] = 0.0
+    plan.set_generators(zero_self)
+    with pytest.raises(bt.BttbError) as e:
+        plan.solve(x, pc=bt.BTTB_PC_BLOCK_JACOBI)
+    assert e.value.code == bt.BTTB_ERR_SINGULAR

@@ -189,6 +189,36 @@ typedef struct {
 int bttb_profile(bttb_plan plan, int enable);
 int bttb_profile_read(bttb_plan plan, int which, bttb_kernel_stats *out);
 
+/*
+ * FP64 (double-float) product y = Z x for callers that cannot allocate
+ * device memory -- for example a plug-in whose host application reserves all
+ * GPU memory at load time, or code running while a CUDA graph is captured.
+ * Such callers cannot create a plan (a plan allocates its spectrum and
+ * workspace).  The paper has no counterpart of this entry point.
+ *
+ * The caller passes the generator blocks (device, complex128, the layout of
+ * bttb_set_generators), x and y (device, complex128, column stride ld >= N)
+ * and a stream.  The spectrum of the generators, its FFT work buffers, the
+ * twiddle tables and the product workspace are computed on every call inside
+ * one fixed file-scope __device__ array of 64 MiB, which every GPU that loads
+ * the library holds until the process exits.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.
+ *   - Sizes whose scratch exceeds 64 MiB are rejected with
+ *     BTTB_ERR_INVALID_ARG and a message giving the bytes needed (roughly:
+ *     2*(mx*my*b*b*16) + 2*(mx*my*nrhs*b*16) bytes; the 4x4, b=12 array fits,
+ *     the 30x30, b=60 array does not).
+ *   - All calls on a device share the array and it keeps the last call's
+ *     contents; each call rewrites every buffer before reading it and clears
+ *     the error word.  Calls that overlap on the GPU (different streams or
+ *     host threads) race on the array: serialise them.
+ *   - The first call on a device looks up the array's address
+ *     (cudaGetSymbolAddress, once per device, with that device current):
+ *     make that first call before any stream capture begins.
+ * Stream-ordered; does not synchronise.
+ */
+int bttb_matvec_noalloc(int nx, int ny, int b, const void *gen, const void *x, void *y, int nrhs, long ld,
+                        void *cuda_stream);
+
 /* Bytes of device memory the plan holds (spectrum copies and workspace). */
 size_t bttb_plan_workspace_bytes(bttb_plan plan);
 

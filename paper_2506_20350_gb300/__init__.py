@@ -29,7 +29,7 @@ BTTB_K_BLOCK_PRODUCT, BTTB_K_FFT, BTTB_K_ALL, BTTB_K_BLOCK_PRODUCT_PREC = 0, 1, 
 
 EXPORTS = ("bttb_plan_create", "bttb_plan_grid", "bttb_set_generators", "bttb_matvec",
            "bttb_gmres_solve", "bttb_block_jacobi_apply", "bttb_get_spectrum_bin",
-           "bttb_profile", "bttb_profile_read",
+           "bttb_profile", "bttb_profile_read", "bttb_matvec_noalloc",
            "bttb_plan_workspace_bytes", "bttb_plan_destroy", "bttb_last_error")
 
 
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bttb_get_spectrum_bin.argtypes = [vp, ci, ci, ctypes.POINTER(ctypes.c_double)]
     lib.bttb_profile.argtypes = [vp, ci]
     lib.bttb_profile_read.argtypes = [vp, ci, ctypes.POINTER(KernelStats)]
+    lib.bttb_matvec_noalloc.argtypes = [ci, ci, ci, vp, vp, vp, ci, cl, vp]
     lib.bttb_plan_workspace_bytes.argtypes = [vp]
     lib.bttb_plan_workspace_bytes.restype = ctypes.c_size_t
     lib.bttb_plan_destroy.argtypes = [vp]
@@ -169,6 +170,12 @@ def bttb_profile_read(plan, which: int) -> KernelStats:
     st = KernelStats()
     _check(load_library().bttb_profile_read(plan, which, ctypes.byref(st)), plan)
     return st
+
+
+def bttb_matvec_noalloc(nx: int, ny: int, b: int, gen, x, y, nrhs: int, ld: int, stream=None) -> None:
+    """Allocation-free FP64 product for small arrays (see include/bttb.h); all tensors on the device."""
+    _check(load_library().bttb_matvec_noalloc(nx, ny, b, _ptr(gen), _ptr(x), _ptr(y), nrhs, ld,
+                                              _stream_handle(stream)))
 
 
 def bttb_plan_workspace_bytes(plan) -> int:

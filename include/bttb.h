@@ -132,7 +132,14 @@ typedef struct {
     double *history;     /* optional HOST array: true relative residual of column 0
                             at the start of each restart cycle                     */
     int history_len;     /* capacity of history                                    */
+    int flags;           /* OR of BTTB_GMRES_* below; 0 = defaults                 */
 } bttb_gmres_opts;
+
+/* Each restart cycle (m Arnoldi steps, back substitution, update) runs as one
+ * CUDA graph replayed per cycle; finished columns make the remaining kernels of
+ * the cycle exit at once.  BTTB_GMRES_NO_GRAPH launches the same kernels from
+ * the host instead, with one host synchronisation per step. */
+enum { BTTB_GMRES_NO_GRAPH = 1 };
 
 typedef struct {
     int status;          /* BTTB_OK, BTTB_NOT_CONVERGED or BTTB_BREAKDOWN          */

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libbttb.so")
 BTTB_C64, BTTB_C128 = 0, 1
 BTTB_MV_FP64, BTTB_MV_FP32, BTTB_MV_FP64_NATIVE = 0, 1, 2
 BTTB_PC_NONE, BTTB_PC_BLOCK_JACOBI = 0, 1
+BTTB_GMRES_NO_GRAPH = 1
 BTTB_OK, BTTB_NOT_CONVERGED, BTTB_BREAKDOWN = 0, 1, 2
 BTTB_ERR_INVALID_ARG, BTTB_ERR_CUDA, BTTB_ERR_OOM = -1, -2, -3
 BTTB_ERR_NO_GENERATORS, BTTB_ERR_TIMEOUT, BTTB_ERR_NONFINITE, BTTB_ERR_SINGULAR = -4, -5, -6, -7
@@ -43,7 +44,7 @@ class GmresOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("pc", ctypes.c_int), ("inner", ctypes.c_int), ("use_x0", ctypes.c_int),
                 ("host_io", ctypes.c_int), ("history", ctypes.POINTER(ctypes.c_double)),
-                ("history_len", ctypes.c_int)]
+                ("history_len", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
 class KernelStats(ctypes.Structure):
@@ -194,9 +195,9 @@ def bttb_last_error(plan=None) -> str:
 # ---------------------------------------------------------------- convenience
 
 def gmres_opts(tol=1e-8, restart=50, max_iters=5000, pc=BTTB_PC_NONE, inner=BTTB_MV_FP64, use_x0=False,
-               host_io=False, history=None) -> GmresOpts:
+               host_io=False, history=None, flags=0) -> GmresOpts:
     o = GmresOpts()
-    o.tol, o.restart, o.max_iters, o.pc, o.inner = tol, restart, max_iters, pc, inner
+    o.tol, o.restart, o.max_iters, o.pc, o.inner, o.flags = tol, restart, max_iters, pc, inner, flags
     o.use_x0, o.host_io = int(bool(use_x0)), int(bool(host_io))
     if history is not None:
         o.history = history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -29,8 +29,19 @@ int check_cuda(Plan *p, cudaError_t e, const char *what) {
     return set_error(p, e == cudaErrorMemoryAllocation ? BTTB_ERR_OOM : BTTB_ERR_CUDA, m);
 }
 
+constexpr int kSinkToken = 1 << 30;
+
 int prof_begin(Plan *p, int kid) {
     if (!p->prof) return -1;
+    if (p->sink) {
+        if (kid < BTTB_K_BLOCK_PRODUCT_PREC) return -1;      // in graphs only the block product is timed
+        Plan::GraphRec r{nullptr, nullptr, kid, 0.0, p->sink_step};
+        if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess) return -1;
+        // External: captured as an event-record node that timestamps every replay
+        cudaEventRecordWithFlags(r.e0, p->stream, cudaEventRecordExternal);
+        p->sink->push_back(r);
+        return kSinkToken + (int)p->sink->size() - 1;
+    }
     if (p->ev_used + 2 > (int)p->ev_pool.size()) {
         for (int i = 0; i < 64; ++i) {
             cudaEvent_t e;
@@ -47,6 +58,12 @@ int prof_begin(Plan *p, int kid) {
 
 void prof_end(Plan *p, int token, double bytes) {
     if (token < 0 || !p->prof) return;
+    if (token >= kSinkToken) {
+        Plan::GraphRec &r = (*p->sink)[token - kSinkToken];
+        r.bytes = bytes;
+        cudaEventRecordWithFlags(r.e1, p->stream, cudaEventRecordExternal);
+        return;
+    }
     Plan::ProfRec &r = p->recs[token];
     r.bytes = bytes;
     cudaEventRecord(p->ev_pool[r.ev1], p->stream);
@@ -285,6 +302,7 @@ int bttb_profile(bttb_plan plan, int enable) {
         p.recs.clear();
         p.ev_used = 0;
         p.launches = 0;
+        for (int i = 0; i < Plan::kMaxKid; ++i) p.acc_ms[i] = p.acc_bytes[i] = 0.0, p.acc_n[i] = 0;
     }
     p.prof = enable != 0;
     return BTTB_OK;
@@ -301,6 +319,13 @@ int bttb_profile_read(bttb_plan plan, int which, bttb_kernel_stats *out) {
     if (which == BTTB_K_ALL) {
         out->launches = p.launches;
         return BTTB_OK;
+    }
+    for (int kid = 0; kid < Plan::kMaxKid; ++kid) {
+        const bool match = kid == which || (which == BTTB_K_BLOCK_PRODUCT && kid >= BTTB_K_BLOCK_PRODUCT_PREC);
+        if (!match) continue;
+        out->ms += p.acc_ms[kid];
+        out->launches += p.acc_n[kid];
+        out->bytes += p.acc_bytes[kid];
     }
     for (const Plan::ProfRec &r : p.recs) {
         const bool match = r.kid == which || (which == BTTB_K_BLOCK_PRODUCT && r.kid >= BTTB_K_BLOCK_PRODUCT_PREC);

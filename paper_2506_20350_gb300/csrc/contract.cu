@@ -1,6 +1,6 @@
 // Per-bin block product  v_k = G_k u_k  (Eq. (multL): the block-diagonal
 // matrix diag_b(F C_1) applied to the transformed vector), for every bin k of
-// the mx x my grid and up to kContractKC right-hand sides at a time.
+// the mx x my grid and up to four right-hand sides per launch.
 //
 // This kernel streams the whole spectrum once per product and is bound by HBM
 // bandwidth.  Design:
@@ -26,8 +26,8 @@
 namespace bttb {
 
 constexpr int kConsumerWarps = 8;
-constexpr int kContractThreads = (kConsumerWarps + 1) * 32;
 constexpr int kMaxStages = 8;
+
 
 struct ContractArgs {
     const void *g0, *g1;          // spectrum planes (g1: double-float low plane)
@@ -35,7 +35,8 @@ struct ContractArgs {
     const void *u;                // transformed vectors, column c0 of the group
     void *v;
     long ubs;                     // bin stride of u/v (elements)
-    int nbins, b, kc;             // kc = columns in this group (<= kContractKC)
+    int nbins, b, kc;             // kc = columns in this group (<= the launch width KC)
+    const int *active;            // optional per-column flags of this group (offset to column c0)
     int Qc, nchunks, G, nstages;
     uint32_t st_bytes, off_g1, off_u, red_off;
     int *err;
@@ -87,135 +88,164 @@ template <class A> struct GElem { using T = float2; static constexpr int planes 
 template <> struct GElem<DF64> { using T = float2; static constexpr int planes = 2; };
 template <> struct GElem<F64N> { using T = double2; static constexpr int planes = 1; };
 
+// Two consecutive rows of one spectrum column, loaded as one vector.
+template <class GT> struct Pair;
+template <> struct Pair<float2> {
+    using V = float4;
+    __device__ static float2 lo(const V &v) { return make_float2(v.x, v.y); }
+    __device__ static float2 hi(const V &v) { return make_float2(v.z, v.w); }
+};
+template <> struct Pair<double2> {
+    struct __align__(32) V { double2 a, b; };
+    __device__ static double2 lo(const V &v) { return v.a; }
+    __device__ static double2 hi(const V &v) { return v.b; }
+};
+
 __host__ __device__ constexpr uint32_t round_up16(uint32_t x) { return (x + 15u) & ~15u; }
 __host__ __device__ constexpr uint32_t round_up128(uint32_t x) { return (x + 127u) & ~127u; }
 
-template <class A>
-__global__ void __launch_bounds__(kContractThreads, 1) contract_kernel(const ContractArgs a) {
+// KC: right-hand sides per launch (compile time); R: rows per lane (b <= 32 R).
+//
+// One warp owns one bin at a time: lane l accumulates rows l*R .. l*R+R-1 over
+// all columns, so a bin needs no cross-warp reduction and no barrier.  Each
+// warp streams its bins' column chunks through a private ring of kWarpStages
+// shared-memory stages (lane 0 issues the bulk copies kWarpStages-1 items
+// ahead; an mbarrier per stage counts the bytes in).  Bins are dealt out
+// round-robin over CTAs, then over the CTA's warps.
+constexpr int kWarpStages = 2;
+
+template <class A, int KC, int R, bool VEC>
+__global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const ContractArgs a) {
     using C = typename A::C;
     using GT = typename GElem<A>::T;
     constexpr int NPL = GElem<A>::planes;
-    constexpr int KC = kContractKC;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + kMaxStages;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 2 * kMaxStages * sizeof(uint64_t));
-    unsigned char *stages = smem + 256;
-    C *red = reinterpret_cast<C *>(smem + a.red_off);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0) {
-        for (int s = 0; s < a.nstages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumerWarps);
-        }
-        *abort_flag = 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (a.active) {                                        // skip a group of finished columns (uniform)
+        bool any = false;
+        for (int c = 0; c < a.kc; ++c) any |= a.active[c] != 0;
+        if (!any) return;
+    }
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem) + warp * kWarpStages;
+    unsigned char *stages = smem + 256 + (size_t)warp * kWarpStages * a.st_bytes;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8 * kConsumerWarps * kWarpStages);
+    if (threadIdx.x == 0) *abort_flag = 0;
+    if (lane == 0) {
+        for (int s = 0; s < kWarpStages; ++s) mbar_init(&full[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
 
-    const int total = a.nbins * a.nchunks;
     const int b = a.b;
+    // bins of this warp: blockIdx.x + gridDim.x * (warp + kConsumerWarps * r)
+    const int first = blockIdx.x + gridDim.x * warp;
+    const int step = gridDim.x * kConsumerWarps;
+    const int nbw = first < a.nbins ? (a.nbins - 1 - first) / step + 1 : 0;
+    const int nitems = nbw * a.nchunks;
+    const uint64_t pol_stream = l2_policy_evict_first();
+    const uint64_t pol_keep = l2_policy_evict_last();
 
-    if (warp == kConsumerWarps) {
-        // ---------------- producer ----------------
-        if (lane == 0) {
-            const uint64_t pol_stream = l2_policy_evict_first();
-            const uint64_t pol_keep = l2_policy_evict_last();
-            int i = 0;
-            int issued_last = -1;
-            for (int w = blockIdx.x * a.nchunks; w < total; ++w, ++i) {
-                if (w % a.nchunks == 0 && i > 0) w += (gridDim.x - 1) * a.nchunks;   // next bin of this CTA
-                if (w >= total) break;
-                const int s = i % a.nstages;
-                const uint32_t ph = (uint32_t)(i / a.nstages) & 1u;
-                if (!mbar_wait_bounded(&empty[s], ph ^ 1u, abort_flag)) break;
-                const int bin = w / a.nchunks, ch = w % a.nchunks;
-                const int q0 = ch * a.Qc;
-                const int qn = min(a.Qc, b - q0);
-                const uint32_t gbytes = round_up16((uint32_t)(qn * b) * (uint32_t)sizeof(GT));
-                const uint32_t ubytes = round_up16((uint32_t)(a.kc * b) * (uint32_t)sizeof(C));
-                unsigned char *st = stages + (size_t)s * a.st_bytes;
-                mbar_arrive_expect_tx(&full[s], gbytes * NPL + ubytes);
-                const long goff = (long)bin * a.gbs + (long)q0 * b;
-                bulk_g2s(st, reinterpret_cast<const GT *>(a.g0) + goff, gbytes, &full[s], pol_stream);
-                if (NPL == 2)
-                    bulk_g2s(st + a.off_g1, reinterpret_cast<const GT *>(a.g1) + goff, gbytes, &full[s], pol_stream);
-                bulk_g2s(st + a.off_u, reinterpret_cast<const C *>(a.u) + (long)bin * a.ubs, ubytes, &full[s],
-                         pol_keep);
-                issued_last = i;
-            }
-            if (*abort_flag) {
-                // Drain the copies that may still be in flight before exiting.
-                for (int d = issued_last; d >= 0 && d > issued_last - a.nstages; --d)
-                    mbar_wait_drain(&full[d % a.nstages], (uint32_t)(d / a.nstages) & 1u);
-                atomicOr(a.err, DEVERR_TIMEOUT);
-            }
+    auto issue = [&](int it) {
+        const int s = it % kWarpStages;
+        const int bin = first + step * (it / a.nchunks), ch = it % a.nchunks;
+        const int q0 = ch * a.Qc;
+        const int qn = min(a.Qc, b - q0);
+        const uint32_t gbytes = round_up16((uint32_t)(qn * b) * (uint32_t)sizeof(GT));
+        const uint32_t ubytes = round_up16((uint32_t)(a.kc * b) * (uint32_t)sizeof(C));
+        unsigned char *st = stages + (size_t)s * a.st_bytes;
+        mbar_arrive_expect_tx(&full[s], gbytes * NPL + ubytes);
+        const long goff = (long)bin * a.gbs + (long)q0 * b;
+        bulk_g2s(st, reinterpret_cast<const GT *>(a.g0) + goff, gbytes, &full[s], pol_stream);
+        if (NPL == 2)
+            bulk_g2s(st + a.off_g1, reinterpret_cast<const GT *>(a.g1) + goff, gbytes, &full[s], pol_stream);
+        bulk_g2s(st + a.off_u, reinterpret_cast<const C *>(a.u) + (long)bin * a.ubs, ubytes, &full[s], pol_keep);
+    };
+    if (lane == 0)
+        for (int it = 0; it < kWarpStages - 1 && it < nitems; ++it) issue(it);
+
+    Acc<A> acc[KC][R];
+    const int p0 = lane * R;
+    bool failed = false;
+    for (int it = 0; it < nitems; ++it) {
+        const int s = it % kWarpStages;
+        const uint32_t ph = (uint32_t)(it / kWarpStages) & 1u;
+        // keep kWarpStages-1 items in flight: the stage refilled now was released last iteration
+        if (lane == 0 && it + kWarpStages - 1 < nitems) issue(it + kWarpStages - 1);
+        const int bin = first + step * (it / a.nchunks), ch = it % a.nchunks;
+        if (!failed && !mbar_wait_bounded(&full[s], ph, abort_flag)) {
+            failed = true;
+            if (lane == 0) atomicOr(a.err, DEVERR_TIMEOUT);
         }
-        return;
-    }
-
-    // ---------------- consumers ----------------
-    const int nact = a.G * b;
-    const bool active = tid < nact;
-    const int p = active ? tid % b : 0;
-    const int g = active ? tid / b : 0;
-    Acc<A> acc[KC];
-    int i = 0;
-    for (int w = blockIdx.x * a.nchunks; w < total; ++w, ++i) {
-        if (w % a.nchunks == 0 && i > 0) w += (gridDim.x - 1) * a.nchunks;       // next bin of this CTA
-        if (w >= total) break;
-        const int s = i % a.nstages;
-        const uint32_t ph = (uint32_t)(i / a.nstages) & 1u;
-        const int bin = w / a.nchunks, ch = w % a.nchunks;
-        const bool ok = mbar_wait_bounded(&full[s], ph, abort_flag);
-        if (!ok && lane == 0) atomicOr(a.err, DEVERR_TIMEOUT);
         if (ch == 0) {
 #pragma unroll
-            for (int c = 0; c < KC; ++c) acc[c].zero();
+            for (int c = 0; c < KC; ++c)
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[c][r].zero();
         }
-        if (ok && active) {
+        if (!failed) {
             const int q0 = ch * a.Qc;
             const int qn = min(a.Qc, b - q0);
-            const int qa = (g * qn) / a.G, qb = ((g + 1) * qn) / a.G;
             const unsigned char *st = stages + (size_t)s * a.st_bytes;
-            const GT *gs0 = reinterpret_cast<const GT *>(st);
-            const GT *gs1 = reinterpret_cast<const GT *>(st + a.off_g1);
-            const C *us = reinterpret_cast<const C *>(st + a.off_u);
-#pragma unroll 4
-            for (int q = qa; q < qb; ++q) {
-                const GT gv0 = gs0[q * b + p];
-                const GT gv1 = NPL == 2 ? gs1[q * b + p] : gv0;
+            const GT *gs0 = reinterpret_cast<const GT *>(st) + p0;
+            const GT *gs1 = reinterpret_cast<const GT *>(st + a.off_g1) + p0;
+            const C *us = reinterpret_cast<const C *>(st + a.off_u) + q0;
+            if (p0 < b) {
+#pragma unroll 2
+                for (int q = 0; q < qn; ++q) {
+                    if constexpr (R == 2 && VEC) {               // b even: row pairs are 16-byte aligned
+                        using PV = typename Pair<GT>::V;
+                        const PV v0 = *reinterpret_cast<const PV *>(gs0 + q * b);
+                        const PV v1 = NPL == 2 ? *reinterpret_cast<const PV *>(gs1 + q * b) : v0;
 #pragma unroll
-                for (int c = 0; c < KC; ++c)
-                    if (c < a.kc) acc[c].mac(gv0, gv1, us[c * b + q0 + q]);
+                        for (int c = 0; c < KC; ++c) {
+                            const C u = us[c * b + q];
+                            acc[c][0].mac(Pair<GT>::lo(v0), Pair<GT>::lo(v1), u);
+                            acc[c][1].mac(Pair<GT>::hi(v0), Pair<GT>::hi(v1), u);
+                        }
+                    } else {
+                        GT v0[R], v1[R];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            v0[r] = p0 + r < b ? gs0[q * b + r] : GT{};
+                            v1[r] = NPL == 2 && p0 + r < b ? gs1[q * b + r] : v0[r];
+                        }
+#pragma unroll
+                        for (int c = 0; c < KC; ++c) {
+                            const C u = us[c * b + q];
+#pragma unroll
+                            for (int r = 0; r < R; ++r) acc[c][r].mac(v0[r], v1[r], u);
+                        }
+                    }
+                }
             }
         }
+        // all lanes are done reading stage s before lane 0 may refill it (next iteration)
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-        if (ch == a.nchunks - 1) {
-            if (active) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (ch == a.nchunks - 1 && !failed) {
 #pragma unroll
-                for (int c = 0; c < KC; ++c)
-                    if (c < a.kc) red[((long)g * KC + c) * b + p] = acc[c].result();
-            }
-            named_barrier_sync(1, kConsumerWarps * 32);
-            for (int idx = tid; idx < a.kc * b; idx += kConsumerWarps * 32) {
-                const int c = idx / b, pr = idx % b;
-                C sum = red[(long)c * b + pr];
-                for (int gg = 1; gg < a.G; ++gg) sum = A::add(sum, red[((long)gg * KC + c) * b + pr]);
-                store_vec<A, native_fmt<A>>(a.v, (long)bin * a.ubs + (long)c * b + pr, sum);
-            }
-            named_barrier_sync(1, kConsumerWarps * 32);
+            for (int c = 0; c < KC; ++c)
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (c < a.kc && p0 + r < b)
+                        store_vec<A, native_fmt<A>>(a.v, (long)bin * a.ubs + (long)c * b + p0 + r, acc[c][r].result());
         }
+    }
+    if (failed && lane == 0) {
+        // drain copies that may still be in flight into this warp's stages
+        for (int d = nitems - 1; d >= 0 && d >= nitems - kWarpStages; --d)
+            mbar_wait_drain(&full[d % kWarpStages], (uint32_t)(d / kWarpStages) & 1u);
     }
 }
 
 template <class A>
 constexpr int prec_of() { return A::kind == 0 ? BTTB_MV_FP64 : (A::kind == 1 ? BTTB_MV_FP32 : BTTB_MV_FP64_NATIVE); }
 
-template <class A>
-static int launch_contract(Plan *p, const void *u, void *v, int k) {
+// Largest number of right-hand sides one launch of the block product carries.
+template <class A> constexpr int max_kc() { return A::kind == 1 ? 4 : 2; }
+
+template <class A, int KC, int R, bool VEC>
+static int launch_contract_impl(Plan *p, const void *u, void *v, int k, const int *active) {
     using C = typename A::C;
     using GT = typename GElem<A>::T;
     constexpr int NPL = GElem<A>::planes;
@@ -226,8 +256,6 @@ static int launch_contract(Plan *p, const void *u, void *v, int k) {
     a.nbins = (int)p->bins;
     a.b = b;
     a.err = p->d_err;
-    a.G = (kConsumerWarps * 32) / b;
-    if (a.G < 1) a.G = 1;
     if constexpr (A::kind == 0) {
         a.g0 = p->ghat_hi;
         a.g1 = p->ghat_lo;
@@ -241,45 +269,44 @@ static int launch_contract(Plan *p, const void *u, void *v, int k) {
     if (!a.g0 || (NPL == 2 && !a.g1))
         return set_error(p, BTTB_ERR_INVALID_ARG, "plan does not keep the spectrum copy this precision reads");
 
-    const size_t budget = p->smem_optin > 0 ? p->smem_optin : 200 * 1024;
-    const uint32_t ubytes_max = round_up128((uint32_t)(kContractKC * b) * sizeof(C));
-    const uint32_t red_bytes = round_up128((uint32_t)(a.G * kContractKC * b) * sizeof(C));
-    // Largest chunk of columns such that >= 3 stages fit (>= 2 for very wide blocks).
+    // Per-warp stages: largest column chunk whose kConsumerWarps * kWarpStages stages fit.
+    const size_t budget = (p->smem_optin > 0 ? p->smem_optin : 200 * 1024) - 256;
+    const uint32_t ubytes_max = round_up128((uint32_t)(KC * b) * sizeof(C));
     int Qc = b;
-    int nst = 0;
     for (; Qc >= 1; --Qc) {
         if (Qc < b && (Qc * b) % 2) continue;             // keep 16-byte aligned chunk starts
-        uint32_t gbytes = round_up128((uint32_t)(Qc * b) * sizeof(GT));
-        uint32_t st = gbytes * NPL + ubytes_max;
-        size_t avail = budget - 256 - red_bytes;
-        int ns = (int)(avail / st);
-        if (ns > kMaxStages) ns = kMaxStages;
-        if (ns >= 3 || (ns >= 2 && Qc <= 8)) {
-            nst = ns;
-            break;
-        }
+        const size_t st = (size_t)round_up128((uint32_t)(Qc * b) * sizeof(GT)) * NPL + ubytes_max;
+        if (st * kConsumerWarps * kWarpStages <= budget) break;
     }
-    if (Qc < 1 || nst < 2) return set_error(p, BTTB_ERR_INVALID_ARG, "block too large for the shared-memory pipeline");
+    if (Qc < 1) return set_error(p, BTTB_ERR_INVALID_ARG, "block too large for the shared-memory pipeline");
+    {   // balance the chunks (e.g. 60 columns as 3 x 20, not 29 + 29 + 2)
+        const int nch = (b + Qc - 1) / Qc;
+        int q2 = (b + nch - 1) / nch;
+        if (q2 < b && (q2 * b) % 2) ++q2;
+        if (q2 <= Qc) Qc = q2;
+    }
+    const uint32_t gbytes = round_up128((uint32_t)(Qc * b) * sizeof(GT));
     a.Qc = Qc;
     a.nchunks = (b + Qc - 1) / Qc;
-    a.nstages = nst;
-    const uint32_t gbytes = round_up128((uint32_t)(Qc * b) * sizeof(GT));
+    a.nstages = kWarpStages;
     a.off_g1 = gbytes;
     a.off_u = gbytes * NPL;
     a.st_bytes = gbytes * NPL + ubytes_max;
-    a.red_off = 256 + a.st_bytes * nst;
-    const size_t smem = a.red_off + red_bytes;
+    const size_t smem = 256 + (size_t)a.st_bytes * kConsumerWarps * kWarpStages;
 
-    auto kern = contract_kernel<A>;
+    auto kern = contract_kernel<A, KC, R, VEC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return check_cuda(p, e, "contract smem attribute");
-    const int grid = a.nbins < p->nsm ? a.nbins : p->nsm;     // whole bins per CTA, chunks in order
-    for (int c0 = 0; c0 < k; c0 += kContractKC) {
-        a.kc = (k - c0) < kContractKC ? (k - c0) : kContractKC;
+    const long warps_needed = a.nbins;
+    int grid = (int)((warps_needed + kConsumerWarps - 1) / kConsumerWarps);
+    if (grid > p->nsm) grid = p->nsm;
+    for (int c0 = 0; c0 < k; c0 += KC) {
+        a.kc = (k - c0) < KC ? (k - c0) : KC;
         a.u = reinterpret_cast<const C *>(u) + (long)c0 * b;
         a.v = reinterpret_cast<C *>(v) + (long)c0 * b;
+        a.active = active ? active + c0 : nullptr;
         const int tok = prof_begin(p, BTTB_K_BLOCK_PRODUCT_PREC + prec_of<A>());
-        kern<<<grid, kContractThreads, smem, p->stream>>>(a);
+        kern<<<grid, kConsumerWarps * 32, smem, p->stream>>>(a);
         count_launch(p);
         // algorithmic bytes: spectrum planes once, transformed vectors in and out
         prof_end(p, tok, (double)a.nbins * ((double)b * b * sizeof(GT) * NPL + 2.0 * a.kc * b * sizeof(C)));
@@ -289,11 +316,43 @@ static int launch_contract(Plan *p, const void *u, void *v, int k) {
     return BTTB_OK;
 }
 
-int contract_launch(Plan *p, int prec, const void *u, void *v, int k) {
+template <class A, int KC, int R>
+static int launch_contract_kc(Plan *p, const void *u, void *v, int k, const int *active) {
+    if (R == 2 && p->b % 2 == 0) return launch_contract_impl<A, KC, R, true>(p, u, v, k, active);
+    return launch_contract_impl<A, KC, R, false>(p, u, v, k, active);
+}
+
+// Launch width KC times rows per lane R is kept <= 8 accumulators per lane.
+template <class A, int R>
+static int launch_contract_r(Plan *p, const void *u, void *v, int k, const int *active) {
+    constexpr int KM = (max_kc<A>() * R > 8) ? (8 / R > 0 ? 8 / R : 1) : max_kc<A>();
+    if constexpr (KM >= 4) {
+        if (k >= 3) return launch_contract_kc<A, 4, R>(p, u, v, k, active);
+    }
+    if constexpr (KM >= 2) {
+        if (k >= 2) return launch_contract_kc<A, 2, R>(p, u, v, k, active);
+    }
+    return launch_contract_kc<A, 1, R>(p, u, v, k, active);
+}
+
+template <class A>
+static int launch_contract(Plan *p, const void *u, void *v, int k, const int *active) {
+    const int R = (p->b + 31) / 32;
+    switch (R) {
+        case 1: return launch_contract_r<A, 1>(p, u, v, k, active);
+        case 2: return launch_contract_r<A, 2>(p, u, v, k, active);
+        case 3: return launch_contract_r<A, 3>(p, u, v, k, active);
+        case 4: return launch_contract_r<A, 4>(p, u, v, k, active);
+        case 5: case 6: return launch_contract_r<A, 6>(p, u, v, k, active);
+        default: return launch_contract_r<A, 8>(p, u, v, k, active);
+    }
+}
+
+int contract_launch(Plan *p, int prec, const void *u, void *v, int k, const int *active) {
     switch (prec) {
-        case PREC_F32: return launch_contract<F32>(p, u, v, k);
-        case PREC_F64N: return launch_contract<F64N>(p, u, v, k);
-        default: return launch_contract<DF64>(p, u, v, k);
+        case PREC_F32: return launch_contract<F32>(p, u, v, k, active);
+        case PREC_F64N: return launch_contract<F64N>(p, u, v, k, active);
+        default: return launch_contract<DF64>(p, u, v, k, active);
     }
 }
 

@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int o = blockIdx.x, c = blockIdx.z;
+    if (a.active && !a.active[c]) return;                  // finished column (uniform per CTA)
     const int p0 = blockIdx.y * a.P;
     const int P = a.P, lP = a.log2P, M = a.M;
 

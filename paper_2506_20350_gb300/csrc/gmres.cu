@@ -34,7 +34,17 @@ struct GmresWork {
     int *active = nullptr, *steps = nullptr, *bdown = nullptr, *mlimit = nullptr, *d_j = nullptr, *d_any = nullptr;
     double2 *io = nullptr;        // staging for host_io
     int *h_any = nullptr;         // pinned
+    int *act_cycle = nullptr;     // columns active at the start of the cycle
+    unsigned *counters = nullptr; // 3k per-column arrival counters + 1 global (fused step kernels)
+    int *d_any_step = nullptr;    // largest step + 1 after which some column continued
     size_t bytes = 0;
+    // Captured restart cycle (graph mode).
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t cycle_exec = nullptr;
+    int graph_inner = -1;
+    bool graph_prof = false;
+    long launches_per_cycle = 0;
+    std::vector<Plan::GraphRec> grecs;
 };
 
 constexpr int kVecThreads = 256;
@@ -208,116 +218,356 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
 
-// One Givens step per active column (binary64 scalars); advances j.
-__global__ void givens_kernel(double2 *H, const double2 *hacc, const double *beta2, double *cs, double2 *sn,
-                              double2 *gv, int *active, int *steps, int *bdown, const int *mlimit,
-                              const double *target, double *inv_beta, int m, int k, int *d_j, int *d_any,
-                              int *err) {
-    const int j = *d_j;
-    int any = 0;
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        if (!active[c]) continue;
-        double2 *Hc = H + (long)c * (m + 1) * m;
-        const double2 *ha = hacc + (long)c * (m + 1);
-        double2 *g = gv + (long)c * (m + 1);
-        double *csc = cs + (long)c * m;
-        double2 *snc = sn + (long)c * m;
+// One Givens step of column c by one warp (binary64 scalars).  The lanes stage
+// the Hessenberg column and the earlier rotations in shared memory (3m+2
+// double2 at `wsm`), lane 0 applies the rotations in order from there.
+// Returns (on every lane) whether the column continues.
+__device__ int givens_column(int c, int j, int m, double2 *wsm, double2 *H, const double2 *hacc,
+                             const double *beta2, double *cs, double2 *sn, double2 *gv, int *active, int *steps,
+                             int *bdown, const int *mlimit, const double *target, double *inv_beta, int *err) {
+    const int lane = threadIdx.x & 31;
+    double2 *hcol = wsm;                                        // m+1 entries
+    double2 *snw = hcol + (m + 1);                              // m entries
+    double *csw = reinterpret_cast<double *>(snw + m);          // m entries
+    double2 *Hc = H + (long)c * (m + 1) * m;
+    const double2 *ha = hacc + (long)c * (m + 1);
+    double zn2 = 0.0;
+    for (int i = lane; i <= j; i += 32) {
+        const double2 h = ha[i];
+        hcol[i] = h;
+        zn2 += h.x * h.x + h.y * h.y;
+    }
+    for (int i = lane; i < j; i += 32) {
+        snw[i] = sn[(long)c * m + i];
+        csw[i] = cs[(long)c * m + i];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) zn2 += __shfl_xor_sync(0xffffffffu, zn2, off);
+    __syncwarp();
+    int cont = 0;
+    if (lane == 0) {
         const double beta = sqrt(fmax(beta2[c], 0.0));
-        double zn = beta * beta;
-        for (int i = 0; i <= j; ++i) {
-            const double2 h = ha[i];
-            Hc[i + (long)j * (m + 1)] = h;
-            zn += h.x * h.x + h.y * h.y;
-        }
-        zn = sqrt(zn);
+        const double zn = sqrt(zn2 + beta * beta);
         if (!isfinite(zn)) {
             atomicOr(err, DEVERR_NONFINITE);
             active[c] = 0;
-            continue;
-        }
-        for (int i = 0; i < j; ++i) {
-            const double2 a0 = Hc[i + (long)j * (m + 1)], a1 = Hc[i + 1 + (long)j * (m + 1)];
-            const double2 s = snc[i];
-            const double2 t0 = make_double2(csc[i] * a0.x + (s.x * a1.x - s.y * a1.y),
-                                            csc[i] * a0.y + (s.x * a1.y + s.y * a1.x));
-            const double2 cs_ = conj2(s);
-            const double2 t1 = make_double2(-(cs_.x * a0.x - cs_.y * a0.y) + csc[i] * a1.x,
-                                            -(cs_.x * a0.y + cs_.y * a0.x) + csc[i] * a1.y);
-            Hc[i + (long)j * (m + 1)] = t0;
-            Hc[i + 1 + (long)j * (m + 1)] = t1;
-        }
-        const double2 a = Hc[j + (long)j * (m + 1)];
-        const double aa = hypot(a.x, a.y);
-        const double rho = hypot(aa, beta);
-        double c_;
-        double2 s_;
-        if (aa == 0.0) {
-            c_ = 0.0;
-            s_ = make_double2(1.0, 0.0);
         } else {
-            c_ = aa / rho;
-            s_ = make_double2(a.x / aa * beta / rho, a.y / aa * beta / rho);
-        }
-        csc[j] = c_;
-        snc[j] = s_;
-        Hc[j + (long)j * (m + 1)] = make_double2(c_ * a.x + s_.x * beta, c_ * a.y + s_.y * beta);
-        const double2 gj = g[j];
-        const double2 ms = conj2(s_);
-        g[j + 1] = make_double2(-(ms.x * gj.x - ms.y * gj.y), -(ms.x * gj.y + ms.y * gj.x));
-        g[j] = make_double2(c_ * gj.x, c_ * gj.y);
-        steps[c] = j + 1;
-        const bool bd = !(beta > 1e-14 * zn);
-        if (bd) bdown[c] = 1;
-        const double est = hypot(g[j + 1].x, g[j + 1].y);
-        const bool done = bd || est <= target[c] || (j + 1) >= mlimit[c];
-        if (done) {
-            active[c] = 0;
-        } else {
-            inv_beta[c] = 1.0 / beta;
-            any = 1;
+            for (int i = 0; i < j; ++i) {
+                const double2 a0 = hcol[i], a1 = hcol[i + 1], s = snw[i];
+                const double ci = csw[i];
+                hcol[i] = make_double2(ci * a0.x + (s.x * a1.x - s.y * a1.y), ci * a0.y + (s.x * a1.y + s.y * a1.x));
+                // -conj(s) a0 + c a1
+                hcol[i + 1] = make_double2(-(s.x * a0.x + s.y * a0.y) + ci * a1.x,
+                                           -(s.x * a0.y - s.y * a0.x) + ci * a1.y);
+            }
+            const double2 a = hcol[j];
+            const double aa = hypot(a.x, a.y);
+            const double rho = hypot(aa, beta);
+            double c_;
+            double2 s_;
+            if (aa == 0.0) {
+                c_ = 0.0;
+                s_ = make_double2(1.0, 0.0);
+            } else {
+                c_ = aa / rho;
+                s_ = make_double2(a.x / aa * beta / rho, a.y / aa * beta / rho);
+            }
+            cs[(long)c * m + j] = c_;
+            sn[(long)c * m + j] = s_;
+            hcol[j] = make_double2(c_ * a.x + s_.x * beta, c_ * a.y + s_.y * beta);
+            double2 *g = gv + (long)c * (m + 1);
+            const double2 gj = g[j];
+            // g[j+1] = -conj(s) g[j] ; g[j] = c g[j]
+            g[j + 1] = make_double2(-(s_.x * gj.x + s_.y * gj.y), -(s_.x * gj.y - s_.y * gj.x));
+            g[j] = make_double2(c_ * gj.x, c_ * gj.y);
+            steps[c] = j + 1;
+            const bool bd = !(beta > 1e-14 * zn);
+            if (bd) bdown[c] = 1;
+            const double est = hypot(g[j + 1].x, g[j + 1].y);
+            const bool done = bd || est <= target[c] || (j + 1) >= mlimit[c];
+            if (done) {
+                active[c] = 0;
+            } else {
+                inv_beta[c] = 1.0 / beta;
+                cont = 1;
+            }
         }
     }
-    any = __syncthreads_or(any);
-    if (threadIdx.x == 0) {
-        *d_j = j + 1;
-        *d_any = any;
+    __syncwarp();
+    for (int i = lane; i <= j; i += 32) Hc[i + (long)j * (m + 1)] = hcol[i];
+    return __shfl_sync(0xffffffffu, cont, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Fused Arnoldi-step kernels.  One CTA = 256 consecutive entries of one
+// column; grid (nblk, k).  Partial sums of a column are combined by the last
+// CTA of that column to arrive (per-column counter, fixed summation order).
+// ---------------------------------------------------------------------------
+constexpr int kStepNB = 256;
+constexpr int kStepWarps = kStepNB / 32;
+
+// Per-CTA partial dots conj(B_i) . x over the CTA's chunk for i < cnt, x staged
+// in xs; warp w takes i = w, w+8, ...  Result to part[(c*maxcnt + i)*nblk + blk].
+__device__ __forceinline__ void cta_dots(const float4 *basis, long bs_i, long boff, const float4 *xs, int len,
+                                         int cnt, float4 *part, long pbase, int nblk, int blk) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < cnt; i += kStepWarps) {
+        const float4 *bv = basis + (long)i * bs_i + boff;
+        dacc re{0.f, 0.f}, im{0.f, 0.f};
+#pragma unroll 4
+        for (int e = lane; e < len; e += 32) {
+            const float4 v = bv[e], x = xs[e];
+            dacc_mac(re, v.x, v.z, x.x, x.z);
+            dacc_mac(re, v.y, v.w, x.y, x.w);
+            dacc_mac(im, v.x, v.z, x.y, x.w);
+            dacc_mac(im, -v.y, -v.w, x.x, x.z);
+        }
+        warp_reduce_dacc(re);
+        warp_reduce_dacc(im);
+        if (lane == 0) {
+            const df r = dacc_result(re), q = dacc_result(im);
+            part[(pbase + i) * nblk + blk] = make_float4(r.hi, q.hi, r.lo, q.lo);
+        }
     }
 }
 
-// y = H^{-1} g (upper triangular, steps[c] x steps[c]), stored as double-float.
-__global__ void finish_kernel(const double2 *H, const double2 *gv, const int *steps, float4 *ycoef, int m, int k,
-                              const int *was_active) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < k; c += gridDim.x * blockDim.x) {
-        if (!was_active[c]) continue;
-        const int kk = steps[c];
-        const double2 *Hc = H + (long)c * (m + 1) * m;
-        const double2 *g = gv + (long)c * (m + 1);
-        double2 y[201];
-        for (int i = kk - 1; i >= 0; --i) {
-            double2 s = g[i];
-            for (int l = i + 1; l < kk; ++l) {
-                const double2 t = cmul(Hc[i + (long)l * (m + 1)], y[l]);
-                s.x -= t.x;
-                s.y -= t.y;
-            }
-            const double2 d = Hc[i + (long)i * (m + 1)];
-            const double dd = d.x * d.x + d.y * d.y;
-            y[i] = dd > 0.0 ? make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd)
-                            : make_double2(0.0, 0.0);
+// Last CTA of column c: sum the partials of i < cnt in block order.
+// mode 0: hco = h, hacc = h ; mode 1: hco = h, hacc += h ; mode 2: beta2 = Re h_0
+__device__ __forceinline__ void last_cta_reduce(const float4 *part, long pbase, int nblk, int cnt, int mode,
+                                                float4 *hco, double2 *hacc, double *beta2, int c) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < cnt; i += kStepWarps) {
+        const float4 *pp = part + (pbase + i) * nblk;
+        dacc re{0.f, 0.f}, im{0.f, 0.f};
+        for (int e = lane; e < nblk; e += 32) {
+            const float4 v = __ldcg(pp + e);
+            dacc_add(re, dacc{v.x, v.z});
+            dacc_add(im, dacc{v.y, v.w});
         }
-        for (int i = 0; i < kk; ++i) ycoef[(long)c * (m + 1) + i] = F64N::to_cdf(y[i]);
+        warp_reduce_dacc(re);
+        warp_reduce_dacc(im);
+        if (lane == 0) {
+            const df r = dacc_result(re), q = dacc_result(im);
+            if (mode == 2) {
+                beta2[c] = df_to_double(r);
+            } else {
+                hco[pbase + i] = make_float4(r.hi, q.hi, r.lo, q.lo);
+                const double2 v = make_double2(df_to_double(r), df_to_double(q));
+                double2 &h = hacc[pbase + i];
+                h = mode == 0 ? v : make_double2(h.x + v.x, h.y + v.y);
+            }
+        }
+    }
+}
+
+// Returns true in every thread of the CTA that arrives last for column c.
+__device__ __forceinline__ bool arrive_last(unsigned *counter, int nblk) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(counter, 1u);
+        s_last = (prev == (unsigned)nblk - 1);
+        if (s_last) *counter = 0u;                 // ready for the next use
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// w -= sum_{i<cnt} B_i h_i for this thread's entry (compensated), returns the new value.
+__device__ __forceinline__ float4 cta_update_entry(const float4 *basis, long bs_i, long boff, const float4 *hs,
+                                                   int cnt, float4 x) {
+    dacc re{x.x, x.z}, im{x.y, x.w};
+#pragma unroll 8
+    for (int i = 0; i < cnt; ++i) {
+        const float4 v = basis[(long)i * bs_i + boff];
+        const float4 h = hs[i];                     // already negated
+        dacc_mac(re, v.x, v.z, h.x, h.z);
+        dacc_mac(re, -v.y, -v.w, h.y, h.w);
+        dacc_mac(im, v.x, v.z, h.y, h.w);
+        dacc_mac(im, v.y, v.w, h.x, h.z);
+    }
+    const df r = dacc_result(re), q = dacc_result(im);
+    return make_float4(r.hi, q.hi, r.lo, q.lo);
+}
+
+struct StepArgs {
+    const float4 *Vb;      // basis [i][c][n]
+    float4 *W;             // [c][n]
+    long n, bs_i, bs_c;
+    int m, k, nblk;
+    float4 *part;          // [c][m+1][nblk]
+    float4 *hco;           // [c][m+1]
+    double2 *hacc;         // [c][m+1]
+    double *beta2;
+    unsigned *cnt_a, *cnt_b, *cnt_c, *cnt_d;    // per-column arrival counters (cnt_d: one)
+    int *active;
+    int *d_j, *d_any_step;
+    // Givens
+    double2 *H, *gv, *sn;
+    double *cs, *inv_beta;
+    int *steps, *bdown;
+    const int *mlimit;
+    const double *target;
+    int *err;
+};
+
+// (A) first Gram-Schmidt pass: h = V_j^H w
+__global__ void __launch_bounds__(kStepNB) step_dots_kernel(const StepArgs a) {
+    __shared__ float4 xs[kStepNB];
+    const int c = blockIdx.y, blk = blockIdx.x;
+    if (!a.active[c]) return;
+    const int cnt = *a.d_j + 1;
+    const long n0 = (long)blk * kStepNB;
+    const int len = (int)min((long)kStepNB, a.n - n0);
+    if ((int)threadIdx.x < len) xs[threadIdx.x] = a.W[(long)c * a.n + n0 + threadIdx.x];
+    __syncthreads();
+    const long pbase = (long)c * (a.m + 1);
+    cta_dots(a.Vb, a.bs_i, (long)c * a.bs_c + n0, xs, len, cnt, a.part, pbase, a.nblk, blk);
+    if (!arrive_last(a.cnt_a + c, a.nblk)) return;
+    last_cta_reduce(a.part, pbase, a.nblk, cnt, 0, a.hco, a.hacc, nullptr, c);
+}
+
+// (B) w -= V h (first pass), then the second pass h2 = V^H w
+__global__ void __launch_bounds__(kStepNB) step_update_dots_kernel(const StepArgs a) {
+    __shared__ float4 xs[kStepNB];
+    extern __shared__ __align__(16) float4 hs[];          // m+1
+    const int c = blockIdx.y, blk = blockIdx.x;
+    if (!a.active[c]) return;
+    const int cnt = *a.d_j + 1;
+    const long pbase = (long)c * (a.m + 1);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const float4 h = a.hco[pbase + i];
+        hs[i] = make_float4(-h.x, -h.y, -h.z, -h.w);
+    }
+    __syncthreads();
+    const long n0 = (long)blk * kStepNB;
+    const int len = (int)min((long)kStepNB, a.n - n0);
+    const int t = threadIdx.x;
+    if (t < len) {
+        const long e = (long)c * a.n + n0 + t;
+        const float4 x = cta_update_entry(a.Vb, a.bs_i, (long)c * a.bs_c + n0 + t, hs, cnt, a.W[e]);
+        a.W[e] = x;
+        xs[t] = x;
+    }
+    __syncthreads();
+    cta_dots(a.Vb, a.bs_i, (long)c * a.bs_c + n0, xs, len, cnt, a.part, pbase, a.nblk, blk);
+    if (!arrive_last(a.cnt_b + c, a.nblk)) return;
+    last_cta_reduce(a.part, pbase, a.nblk, cnt, 1, a.hco, a.hacc, nullptr, c);
+}
+
+// (C) w -= V h2, beta^2 = ||w||^2, then (last CTA of the column) one Givens step
+__global__ void __launch_bounds__(kStepNB) step_update_norm_givens_kernel(const StepArgs a) {
+    __shared__ float4 xs[kStepNB];
+    extern __shared__ __align__(16) float4 dyn[];          // hs: m+1 float4, then Givens scratch
+    const int c = blockIdx.y, blk = blockIdx.x;
+    if (!a.active[c]) return;
+    const int j = *a.d_j, cnt = j + 1;
+    const long pbase = (long)c * (a.m + 1);
+    float4 *hs = dyn;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const float4 h = a.hco[pbase + i];
+        hs[i] = make_float4(-h.x, -h.y, -h.z, -h.w);
+    }
+    __syncthreads();
+    const long n0 = (long)blk * kStepNB;
+    const int len = (int)min((long)kStepNB, a.n - n0);
+    const int t = threadIdx.x;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t < len) {
+        const long e = (long)c * a.n + n0 + t;
+        x = cta_update_entry(a.Vb, a.bs_i, (long)c * a.bs_c + n0 + t, hs, cnt, a.W[e]);
+        a.W[e] = x;
+    }
+    xs[t] = x;
+    __syncthreads();
+    cta_dots(xs - (long)0, 0, 0, xs, len, 1, a.part, pbase, a.nblk, blk);   // ||w||^2 partial (i = 0)
+    if (!arrive_last(a.cnt_c + c, a.nblk)) return;
+    last_cta_reduce(a.part, pbase, a.nblk, 1, 2, nullptr, nullptr, a.beta2, c);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double2 *wsm = reinterpret_cast<double2 *>(dyn + (a.m + 1));
+        const int cont = givens_column(c, j, a.m, wsm, a.H, a.hacc, a.beta2, a.cs, a.sn, a.gv, a.active, a.steps,
+                                       a.bdown, a.mlimit, a.target, a.inv_beta, a.err);
+        if (threadIdx.x == 0 && cont) atomicMax(a.d_any_step, j + 1);
+    }
+}
+
+// (D) v_{j+1} = w / beta for continuing columns; the last CTA overall advances j.
+__global__ void __launch_bounds__(kStepNB) step_scale_advance_kernel(const StepArgs a) {
+    const int c = blockIdx.y, blk = blockIdx.x;
+    const int j = *a.d_j;
+    if (a.active[c]) {
+        const df s = df_from_double(a.inv_beta[c]);
+        const long n0 = (long)blk * kStepNB;
+        const long e = n0 + threadIdx.x;
+        if (e < a.n) {
+            const float4 x = a.W[(long)c * a.n + e];
+            const df r = df_mul(df{x.x, x.z}, s), q = df_mul(df{x.y, x.w}, s);
+            const_cast<float4 *>(a.Vb)[(long)(j + 1) * a.bs_i + (long)c * a.bs_c + e] =
+                make_float4(r.hi, q.hi, r.lo, q.lo);
+        }
+    }
+    if (arrive_last(a.cnt_d, a.nblk * a.k)) {
+        if (threadIdx.x == 0) *a.d_j = j + 1;
+    }
+}
+
+// y = H^{-1} g (upper triangular, steps[c] x steps[c]) for column c = blockIdx.x,
+// stored as double-float.  Column-oriented back substitution: one diagonal
+// division per step, the remaining right-hand side updated in parallel.
+constexpr int kFinishThreads = 128;
+
+__global__ void __launch_bounds__(kFinishThreads) finish_kernel(const double2 *H, const double2 *gv,
+                                                                const int *steps, float4 *ycoef, int m,
+                                                                const int *was_active) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int c = blockIdx.x;
+    if (!was_active[c]) return;
+    const int kk = steps[c];
+    double2 *rhs = reinterpret_cast<double2 *>(fsm);              // m+1
+    const double2 *Hc = H + (long)c * (m + 1) * m;
+    const double2 *g = gv + (long)c * (m + 1);
+    for (int i = threadIdx.x; i < kk; i += blockDim.x) rhs[i] = g[i];
+    __syncthreads();
+    for (int i = kk - 1; i >= 0; --i) {
+        const double2 d = Hc[i + (long)i * (m + 1)];
+        const double dd = d.x * d.x + d.y * d.y;
+        const double2 s = rhs[i];
+        const double2 yi = dd > 0.0 ? make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd)
+                                    : make_double2(0.0, 0.0);
+        for (int l = threadIdx.x; l < i; l += blockDim.x) {
+            const double2 t = cmul(Hc[l + (long)i * (m + 1)], yi);
+            rhs[l] = make_double2(rhs[l].x - t.x, rhs[l].y - t.y);
+        }
+        if (threadIdx.x == 0) ycoef[(long)c * (m + 1) + i] = F64N::to_cdf(yi);
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------------------------ host side
 
+static void drop_graph(GmresWork *g) {
+    if (g->cycle_exec) cudaGraphExecDestroy(g->cycle_exec);
+    g->cycle_exec = nullptr;
+    for (auto &r : g->grecs) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    g->grecs.clear();
+}
+
 static void free_work(GmresWork *g) {
     if (!g) return;
+    drop_graph(g);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     cudaFree(g->X); cudaFree(g->Vb); cudaFree(g->Zb); cudaFree(g->W); cudaFree(g->R); cudaFree(g->Vin);
     cudaFree(g->H); cudaFree(g->hacc); cudaFree(g->gv); cudaFree(g->sn); cudaFree(g->hco); cudaFree(g->ycoef);
     cudaFree(g->part); cudaFree(g->cs); cudaFree(g->beta2); cudaFree(g->vnorm); cudaFree(g->inv_beta);
     cudaFree(g->target); cudaFree(g->active); cudaFree(g->steps); cudaFree(g->bdown); cudaFree(g->mlimit);
-    cudaFree(g->d_j); cudaFree(g->d_any); cudaFree(g->io);
+    cudaFree(g->d_j); cudaFree(g->d_any); cudaFree(g->io); cudaFree(g->act_cycle);
+    cudaFree(g->counters); cudaFree(g->d_any_step);
     cudaFreeHost(g->h_any);
     delete g;
 }
@@ -330,14 +580,14 @@ void gmres_free(Plan *p) {
 
 static int ensure_work(Plan *p, int m, int k, bool flex, bool host_io) {
     GmresWork *g = p->gw;
-    if (g && g->m == m && g->k >= k && (g->flex || !flex) && (!host_io || g->io)) return BTTB_OK;
+    if (g && g->m == m && g->k == k && (g->flex || !flex) && (!host_io || g->io)) return BTTB_OK;
     gmres_free(p);
     g = new GmresWork();
     g->m = m;
     g->k = k;
     g->n = p->n;
     g->flex = flex;
-    g->NB = k <= 4 ? 256 : 1024;
+    g->NB = kStepNB;
     g->nblk = (int)((p->n + g->NB - 1) / g->NB);
     const long n = p->n;
     size_t total = 0;
@@ -366,11 +616,15 @@ static int ensure_work(Plan *p, int m, int k, bool flex, bool host_io) {
     alloc(&g->inv_beta, sizeof(double) * k);
     alloc(&g->target, sizeof(double) * k);
     alloc(&g->active, sizeof(int) * k);
+    alloc(&g->act_cycle, sizeof(int) * k);
     alloc(&g->steps, sizeof(int) * k);
     alloc(&g->bdown, sizeof(int) * k);
     alloc(&g->mlimit, sizeof(int) * k);
     alloc(&g->d_j, sizeof(int));
     alloc(&g->d_any, sizeof(int));
+    alloc(&g->counters, sizeof(unsigned) * (3 * (size_t)k + 1));
+    alloc(&g->d_any_step, sizeof(int));
+    if (ok && cudaMemset(g->counters, 0, sizeof(unsigned) * (3 * (size_t)k + 1)) != cudaSuccess) ok = false;
     if (host_io) alloc(&g->io, sizeof(double2) * k * n);
     if (ok && cudaMallocHost((void **)&g->h_any, sizeof(int)) != cudaSuccess) ok = false;
     g->bytes = total;
@@ -395,11 +649,122 @@ static int norm2_cols(Plan *p, GmresWork *g, const float4 *x, int k, const int *
     return check_cuda(p, cudaGetLastError(), "norm launch");
 }
 
+// One Arnoldi step for every active column, on p->stream (captured or not):
+// [block-Jacobi], the product, then the four fused Gram-Schmidt/Givens kernels.
+static int arnoldi_step(Plan *p, GmresWork *g, int inner) {
+    const int m = g->m, k = g->k;
+    const long n = p->n, bs_i = (long)k * n;
+    cudaStream_t st = p->stream;
+    int rc;
+    const float4 *src = g->Vb;
+    if (g->flex) {
+        rc = block_jacobi_run(p, g->Vb, FMT_CDF, n, g->Zb, FMT_CDF, n, k, g->d_j, bs_i, g->active);
+        if (rc != BTTB_OK) return rc;
+        src = g->Zb;
+    }
+    rc = matvec_run(p, src, FMT_CDF, n, g->W, FMT_CDF, n, k, inner, g->d_j, bs_i, nullptr, g->active);
+    if (rc != BTTB_OK) return rc;
+    StepArgs a{};
+    a.Vb = g->Vb;
+    a.W = g->W;
+    a.n = n;
+    a.bs_i = bs_i;
+    a.bs_c = n;
+    a.m = m;
+    a.k = k;
+    a.nblk = g->nblk;
+    a.part = g->part;
+    a.hco = g->hco;
+    a.hacc = g->hacc;
+    a.beta2 = g->beta2;
+    a.cnt_a = g->counters;
+    a.cnt_b = g->counters + k;
+    a.cnt_c = g->counters + 2 * k;
+    a.cnt_d = g->counters + 3 * k;
+    a.active = g->active;
+    a.d_j = g->d_j;
+    a.d_any_step = g->d_any_step;
+    a.H = g->H;
+    a.gv = g->gv;
+    a.sn = g->sn;
+    a.cs = g->cs;
+    a.inv_beta = g->inv_beta;
+    a.steps = g->steps;
+    a.bdown = g->bdown;
+    a.mlimit = g->mlimit;
+    a.target = g->target;
+    a.err = p->d_err;
+    const dim3 grid(g->nblk, k);
+    const size_t hs_bytes = (size_t)(m + 1) * sizeof(float4);
+    step_dots_kernel<<<grid, kStepNB, 0, st>>>(a);
+    step_update_dots_kernel<<<grid, kStepNB, hs_bytes, st>>>(a);
+    step_update_norm_givens_kernel<<<grid, kStepNB, hs_bytes + (size_t)(3 * m + 2) * sizeof(double2), st>>>(a);
+    step_scale_advance_kernel<<<grid, kStepNB, 0, st>>>(a);
+    count_launch(p, 4);
+    return check_cuda(p, cudaGetLastError(), "Arnoldi step launch");
+}
+
+// Back substitution and x += (preconditioned) basis * y for the columns of this cycle.
+static int cycle_finish(Plan *p, GmresWork *g) {
+    const int m = g->m, k = g->k;
+    const long n = p->n, bs_i = (long)k * n, bs_c = n;
+    const int vgrid = (int)std::min<long>((n + kVecThreads - 1) / kVecThreads, 1024);
+    finish_kernel<<<k, kFinishThreads, (m + 1) * sizeof(double2), p->stream>>>(g->H, g->gv, g->steps, g->ycoef, m,
+                                                                               g->act_cycle);
+    count_launch(p);
+    update_kernel<<<dim3(vgrid, k), kVecThreads, (m + 1) * sizeof(float4), p->stream>>>(
+        g->flex ? g->Zb : g->Vb, bs_i, bs_c, nullptr, g->steps, g->ycoef, m + 1, g->X, n, 1.f, g->act_cycle);
+    count_launch(p);
+    return check_cuda(p, cudaGetLastError(), "cycle finish launch");
+}
+
+// Capture m Arnoldi steps and the cycle finish into one executable graph.
+static int build_cycle_graph(Plan *p, GmresWork *g, int inner) {
+    drop_graph(g);
+    cudaError_t e;
+    if (!g->cap_stream && (e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return check_cuda(p, e, "capture stream");
+    cudaStream_t saved = p->stream;
+    const long launches0 = p->launches;
+    p->stream = g->cap_stream;
+    p->sink = &g->grecs;
+    if ((e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
+        p->stream = saved;
+        p->sink = nullptr;
+        return check_cuda(p, e, "begin capture");
+    }
+    int rc = BTTB_OK;
+    for (int step = 0; step < g->m && rc == BTTB_OK; ++step) {
+        p->sink_step = step;
+        rc = arnoldi_step(p, g, inner);
+    }
+    p->sink_step = g->m;
+    if (rc == BTTB_OK) rc = cycle_finish(p, g);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(g->cap_stream, &graph);
+    p->stream = saved;
+    p->sink = nullptr;
+    g->launches_per_cycle = p->launches - launches0;
+    p->launches = launches0;
+    if (rc != BTTB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return check_cuda(p, e, "end capture");
+    e = cudaGraphInstantiate(&g->cycle_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return check_cuda(p, e, "graph instantiate");
+    g->graph_inner = inner;
+    g->graph_prof = p->prof;
+    return BTTB_OK;
+}
+
 int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmres_opts *o,
                 bttb_col_result *out) {
     const int m = o->restart;
     const bool flex = o->pc == BTTB_PC_BLOCK_JACOBI;
     const int inner = o->inner;
+    const bool use_graph = !(o->flags & BTTB_GMRES_NO_GRAPH);
     int rc = ensure_work(p, m, k, flex, o->host_io != 0);
     if (rc != BTTB_OK) return rc;
     GmresWork *g = p->gw;
@@ -439,7 +804,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
     }
     if ((rc = norm2_cols(p, g, g->Vin, k, nullptr)) != BTTB_OK) return rc;
     std::vector<double> vn2(k), vnorm(k), b2(k), relres(k, 0.0), tgt(k);
-    std::vector<int> status(k, BTTB_OK), total(k, 0), cycles(k, 0), act(k), mlim(k), stp(k), bd(k);
+    std::vector<int> status(k, BTTB_OK), total(k, 0), cycles(k, 0), act(k), mlim(k), stp(k, 0), bd(k, 0);
     e = cudaMemcpyAsync(vn2.data(), g->beta2, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return check_cuda(p, e, "norm of V");
@@ -491,61 +856,55 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
         if (o->history && hist_n < o->history_len) o->history[hist_n++] = relres[0];
         if (!any) break;
         cudaMemcpyAsync(g->active, act.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(g->act_cycle, act.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(g->mlimit, mlim.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(g->target, tgt.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st);
         cudaMemsetAsync(g->bdown, 0, sizeof(int) * k, st);
         cudaMemsetAsync(g->steps, 0, sizeof(int) * k, st);
+        cudaMemsetAsync(g->d_any_step, 0, sizeof(int), st);
         cycle_start_kernel<<<1, 256, 0, st>>>(g->beta2, g->gv, g->inv_beta, m, k, g->active, g->d_j);
         count_launch(p);
         scale_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(g->R, g->Vb, bs_i, bs_c, g->d_j, g->inv_beta, n,
                                                              g->active);
         count_launch(p);
-        for (int step = 0; step < m; ++step) {
-            const float4 *src = g->Vb;
-            if (flex) {
-                rc = block_jacobi_run(p, g->Vb, FMT_CDF, n, g->Zb, FMT_CDF, n, k, g->d_j, bs_i);
-                if (rc != BTTB_OK) return rc;
-                src = g->Zb;
+        if (use_graph) {
+            if (!g->cycle_exec || g->graph_inner != inner || g->graph_prof != p->prof)
+                if ((rc = build_cycle_graph(p, g, inner)) != BTTB_OK) return rc;
+            if ((e = cudaGraphLaunch(g->cycle_exec, st)) != cudaSuccess) return check_cuda(p, e, "graph launch");
+            p->launches += g->launches_per_cycle;
+        } else {
+            for (int step = 0; step < m; ++step) {
+                if ((rc = arnoldi_step(p, g, inner)) != BTTB_OK) return rc;
+                e = cudaMemcpyAsync(g->h_any, g->d_any_step, sizeof(int), cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) return check_cuda(p, e, "Arnoldi step");
+                if (*g->h_any < step + 1) break;              // no column continued after this step
             }
-            rc = matvec_run(p, src, FMT_CDF, n, g->W, FMT_CDF, n, k, inner, g->d_j, bs_i);
-            if (rc != BTTB_OK) return rc;
-            for (int pass = 0; pass < 2; ++pass) {
-                dots_partial_kernel<<<dim3(g->nblk, k), kVecThreads, g->NB * sizeof(float4), st>>>(
-                    g->Vb, bs_i, bs_c, g->d_j, 0, g->W, n, g->NB, g->nblk, m + 1, g->part, g->active);
-                count_launch(p);
-                dots_reduce_kernel<<<dim3(m + 1, k), 32, 0, st>>>(g->part, g->nblk, g->d_j, 0, m + 1, g->hco, g->hacc,
-                                                                   pass, nullptr, g->active);
-                count_launch(p);
-                update_kernel<<<dim3(vgrid, k), kVecThreads, (m + 1) * sizeof(float4), st>>>(
-                    g->Vb, bs_i, bs_c, g->d_j, nullptr, g->hco, m + 1, g->W, n, -1.f, g->active);
-                count_launch(p);
-            }
-            if ((rc = norm2_cols(p, g, g->W, k, g->active)) != BTTB_OK) return rc;
-            givens_kernel<<<1, 256, 0, st>>>(g->H, g->hacc, g->beta2, g->cs, g->sn, g->gv, g->active, g->steps,
-                                             g->bdown, g->mlimit, g->target, g->inv_beta, m, k, g->d_j, g->d_any,
-                                             p->d_err);
-            count_launch(p);
-            scale_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(g->W, g->Vb, bs_i, bs_c, g->d_j, g->inv_beta, n,
-                                                                 g->active);
-            count_launch(p);
-            e = cudaMemcpyAsync(g->h_any, g->d_any, sizeof(int), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return check_cuda(p, e, "Arnoldi step");
-            if (!*g->h_any) break;
+            if ((rc = cycle_finish(p, g)) != BTTB_OK) return rc;
         }
-        // x += Z_basis y over the steps each column took in this cycle.
-        cudaMemcpyAsync(g->active, act.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st);
-        finish_kernel<<<(k + 127) / 128, 128, 0, st>>>(g->H, g->gv, g->steps, g->ycoef, m, k, g->active);
-        count_launch(p);
-        update_kernel<<<dim3(vgrid, k), kVecThreads, (m + 1) * sizeof(float4), st>>>(
-            flex ? g->Zb : g->Vb, bs_i, bs_c, nullptr, g->steps, g->ycoef, m + 1, g->X, n, 1.f, g->active);
-        count_launch(p);
         e = cudaMemcpyAsync(stp.data(), g->steps, sizeof(int) * k, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(bd.data(), g->bdown, sizeof(int) * k, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return check_cuda(p, e, "cycle end");
+        int maxsteps = 0;
         for (int c = 0; c < k; ++c)
-            if (act[c]) total[c] += stp[c];
+            if (act[c]) {
+                total[c] += stp[c];
+                maxsteps = std::max(maxsteps, stp[c]);
+            }
+        if (use_graph && p->prof) {
+            // Timed launches of the steps that did work (later steps exited at once).
+            for (const auto &r : g->grecs) {
+                if (r.step >= maxsteps && r.step < m) continue;
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) continue;
+                if (r.kid >= 0 && r.kid < Plan::kMaxKid) {
+                    p->acc_ms[r.kid] += ms;
+                    p->acc_bytes[r.kid] += r.bytes;
+                    p->acc_n[r.kid] += 1;
+                }
+            }
+        }
     }
 
     // Output

@@ -38,6 +38,7 @@ struct FftPass {
     const int *in_sel;            // optional device index: input offset += (*in_sel) * in_sel_stride
     long in_sel_stride;
     const double *in_scale;       // optional device per-column scale applied on load (binary64)
+    const int *active;            // optional device per-column flags: inactive columns are skipped
     int O;                        // number of outer indices
     int pdim;                     // contiguous inner count (bases, or b*b entries)
     int ncols;
@@ -90,6 +91,14 @@ struct Plan {
     int ev_used = 0;
     std::vector<ProfRec> recs;
     long launches = 0;
+    // While a graph is captured, timed launches get their own events, tagged
+    // with the Arnoldi step; accumulated after each replay into acc_*.
+    struct GraphRec { cudaEvent_t e0, e1; int kid; double bytes; int step; };
+    std::vector<GraphRec> *sink = nullptr;
+    int sink_step = 0;
+    static constexpr int kMaxKid = 32;
+    double acc_ms[kMaxKid] = {}, acc_bytes[kMaxKid] = {};
+    long acc_n[kMaxKid] = {};
 };
 
 // Profiling helpers (bttb.cu).  prof_begin returns a token for prof_end, or -1.
@@ -109,14 +118,15 @@ int spectrum_compute(Plan *p, const void *gen, bttb_dtype dtype, int gen_is_host
 int smallest_5smooth(int n);
 
 // contract.cu
-int contract_launch(Plan *p, int prec, const void *u, void *v, int k);
+int contract_launch(Plan *p, int prec, const void *u, void *v, int k, const int *active = nullptr);
 
 // matvec.cu
 // y[:, c] = Z x[:, c]; xfmt/yfmt are VecFmt values; in_sel/in_scale as in FftPass.
 int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int nrhs, int prec,
-               const int *in_sel = nullptr, long in_sel_stride = 0, const double *in_scale = nullptr);
+               const int *in_sel = nullptr, long in_sel_stride = 0, const double *in_scale = nullptr,
+               const int *active = nullptr);
 int block_jacobi_run(Plan *p, const void *x, int xfmt, long ldx, void *z, int zfmt, long ldz, int nrhs,
-                     const int *in_sel = nullptr, long in_sel_stride = 0);
+                     const int *in_sel = nullptr, long in_sel_stride = 0, const int *active = nullptr);
 int block_jacobi_setup(Plan *p, const double2 *t00_host);
 
 // gmres.cu

@@ -25,7 +25,7 @@ namespace bttb {
 static int native_of(int prec) { return prec == PREC_F64N ? FMT_C128 : (prec == PREC_F32 ? FMT_C64 : FMT_CDF); }
 
 int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int nrhs, int prec,
-               const int *in_sel, long in_sel_stride, const double *in_scale) {
+               const int *in_sel, long in_sel_stride, const double *in_scale, const int *active) {
     const int nx = p->nx, ny = p->ny, b = p->b, mx = p->mx, my = p->my;
     const int NF = native_of(prec);
     const long plane = (long)ny * mx * b;
@@ -35,7 +35,7 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     a.in = x; a.out = p->wsB;
     a.in_cs = ldx; a.in_os = (long)nx * b; a.in_ns = b;
     a.out_cs = plane; a.out_os = (long)mx * b; a.out_ns = b;
-    a.in_sel = in_sel; a.in_sel_stride = in_sel_stride; a.in_scale = in_scale;
+    a.in_sel = in_sel; a.in_sel_stride = in_sel_stride; a.in_scale = in_scale; a.active = active;
     a.O = ny; a.pdim = b; a.ncols = nrhs;
     a.nin = nx; a.nout = mx; a.M = mx;
     if ((rc = fft_pass_launch(p, a, prec, xfmt, NF, false)) != BTTB_OK) return rc;
@@ -44,17 +44,17 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     c.in = p->wsB; c.out = p->wsA;
     c.in_cs = plane; c.in_os = b; c.in_ns = (long)mx * b;
     c.out_cs = b; c.out_os = p->ubs; c.out_ns = (long)mx * p->ubs;
-    c.O = mx; c.pdim = b; c.ncols = nrhs;
+    c.O = mx; c.pdim = b; c.ncols = nrhs; c.active = active;
     c.nin = ny; c.nout = my; c.M = my;
     if ((rc = fft_pass_launch(p, c, prec, NF, NF, false)) != BTTB_OK) return rc;
 
-    if ((rc = contract_launch(p, prec, p->wsA, p->wsB, nrhs)) != BTTB_OK) return rc;
+    if ((rc = contract_launch(p, prec, p->wsA, p->wsB, nrhs, active)) != BTTB_OK) return rc;
 
     FftPass d{};
     d.in = p->wsB; d.out = p->wsA;
     d.in_cs = b; d.in_os = p->ubs; d.in_ns = (long)mx * p->ubs;
     d.out_cs = plane; d.out_os = b; d.out_ns = (long)mx * b;
-    d.O = mx; d.pdim = b; d.ncols = nrhs;
+    d.O = mx; d.pdim = b; d.ncols = nrhs; d.active = active;
     d.nin = my; d.nout = ny; d.M = my;
     if ((rc = fft_pass_launch(p, d, prec, NF, NF, true)) != BTTB_OK) return rc;
 
@@ -62,7 +62,7 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     e.in = p->wsA; e.out = y;
     e.in_cs = plane; e.in_os = (long)mx * b; e.in_ns = b;
     e.out_cs = ldy; e.out_os = (long)nx * b; e.out_ns = b;
-    e.O = ny; e.pdim = b; e.ncols = nrhs;
+    e.O = ny; e.pdim = b; e.ncols = nrhs; e.active = active;
     e.nin = mx; e.nout = nx; e.M = mx;
     return fft_pass_launch(p, e, prec, NF, yfmt, true);
 }
@@ -80,12 +80,13 @@ template <int INF, int OUTF>
 __global__ void __launch_bounds__(kBjThreads) bj_apply_kernel(const float2 *rinv, const void *x, long ldx, void *z,
                                                                long ldz, int b, int ncells, int cpb,
                                                                const int *in_sel, long in_sel_stride,
-                                                               int rinv_in_smem) {
+                                                               int rinv_in_smem, const int *active) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *xs = reinterpret_cast<float2 *>(smem_raw);       // cpb*b
     float2 *rsm = xs + (long)cpb * b;                         // b*b, row-major (when it fits)
     const float2 *rs = rinv_in_smem ? rsm : rinv;
     const int c = blockIdx.y;
+    if (active && !active[c]) return;
     const int cell0 = blockIdx.x * cpb;
     const int nc = min(cpb, ncells - cell0);
     if (rinv_in_smem)
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kBjThreads) bj_apply_kernel(const float2 *rinv
 
 template <int INF, int OUTF>
 static int bj_launch(Plan *p, const void *x, long ldx, void *z, long ldz, int nrhs, const int *in_sel,
-                     long in_sel_stride) {
+                     long in_sel_stride, const int *active) {
     const int b = p->b, ncells = p->nx * p->ny;
     int cpb = (8 * 1024) / b;                                  // cells per CTA
     if (cpb < 1) cpb = 1;
@@ -130,16 +131,16 @@ static int bj_launch(Plan *p, const void *x, long ldx, void *z, long ldz, int nr
     }
     dim3 grid((ncells + cpb - 1) / cpb, nrhs);
     kern<<<grid, kBjThreads, smem, p->stream>>>(p->bj_inv, x, ldx, z, ldz, b, ncells, cpb, in_sel, in_sel_stride,
-                                                in_smem);
+                                                in_smem, active);
     count_launch(p);
     return check_cuda(p, cudaGetLastError(), "block-Jacobi launch");
 }
 
 int block_jacobi_run(Plan *p, const void *x, int xfmt, long ldx, void *z, int zfmt, long ldz, int nrhs,
-                     const int *in_sel, long in_sel_stride) {
+                     const int *in_sel, long in_sel_stride, const int *active) {
     if (!p->bj_ready) return set_error(p, BTTB_ERR_NO_GENERATORS, "block-Jacobi needs bttb_set_generators first");
 #define BJ_CASE(I, O)                                     \
-    if (xfmt == I && zfmt == O) return bj_launch<I, O>(p, x, ldx, z, ldz, nrhs, in_sel, in_sel_stride);
+    if (xfmt == I && zfmt == O) return bj_launch<I, O>(p, x, ldx, z, ldz, nrhs, in_sel, in_sel_stride, active);
     BJ_CASE(FMT_C128, FMT_C128)
     BJ_CASE(FMT_C64, FMT_C64)
     BJ_CASE(FMT_CDF, FMT_CDF)

@@ -212,6 +212,31 @@ def test_precision_solve(bt, precision_case, inner):
     assert rr <= c["tol"]
 
 
+@pytest.mark.parametrize("pc", ["none", "bj"])
+def test_graph_and_host_driven_solves_agree(bt, pc):
+    c = arrays.CONFIGS["tiny"]
+    nx, ny, b = c["nx"], c["ny"], c["b"]
+    gen = arrays.generator_blocks(nx, ny, b, c["seed"])
+    v = arrays.port_excitations(nx, ny, b, [(1, 1), (2, 3)]).T.copy()
+    plan = bt.Plan(nx, ny, b, max_rhs=2)
+    plan.set_generators(gen)
+    kw = dict(tol=1e-10, restart=7, inner=bt.BTTB_MV_FP32,
+              pc=bt.BTTB_PC_BLOCK_JACOBI if pc == "bj" else bt.BTTB_PC_NONE)
+    s1, rc1, r1 = plan.solve(_dev(v), **kw)
+    s2, rc2, r2 = plan.solve(_dev(v), flags=bt.BTTB_GMRES_NO_GRAPH, **kw)
+    bt.bttb_profile(plan.handle, True)                   # graph rebuilt with timing nodes
+    s3, rc3, r3 = plan.solve(_dev(v), **kw)
+    st = bt.bttb_profile_read(plan.handle, bt.BTTB_K_BLOCK_PRODUCT)
+    bt.bttb_profile(plan.handle, False)
+    assert rc3 == bt.BTTB_OK and torch.equal(s1, s3)
+    assert st.launches > 0 and st.ms > 0 and st.bytes > 0
+    assert rc1 == rc2 == bt.BTTB_OK
+    assert [x.iters for x in r1] == [x.iters for x in r2]
+    assert torch.equal(s1, s2)
+    rr = oracle.relres(gen, v.T, s1.cpu().numpy().T)
+    assert np.all(rr <= 1e-10)
+
+
 def test_block_jacobi_apply_matches_oracle(bt):
     nx, ny, b = 4, 3, 12
     gen = arrays.generator_blocks(nx, ny, b, seed=12)

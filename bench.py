@@ -232,11 +232,12 @@ def run_ours(args):
     b64 = product_bytes(nx, ny, b, mx, my, "fp64")
     b32 = product_bytes(nx, ny, b, mx, my, "fp32")
 
-    def solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_NONE, Vt=V, It=I, host_io=False):
+    def solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_NONE, Vt=V, It=I, host_io=False, flags=0):
         with torch.cuda.stream(stream):
             if not host_io:
                 It.zero_()
-            _, rc, res = plan.solve(Vt, It, tol=tol, restart=restart, inner=inner, pc=pc, host_io=host_io)
+            _, rc, res = plan.solve(Vt, It, tol=tol, restart=restart, inner=inner, pc=pc, host_io=host_io,
+                                    flags=flags)
         if rc != bt.BTTB_OK:
             raise RuntimeError(f"solve failed rc={rc}: {bt.bttb_last_error()}")
         return res[0]
@@ -318,6 +319,19 @@ def run_ours(args):
         t = e0.elapsed_time(e1) / reps
         mv[name] = {"us": t * 1e3, "gbs": nb / (t / 1e3) / 1e9}
 
+    # per-kernel breakdown of one host-driven IR solve (CUDA events around every launch)
+    bt.bttb_profile(plan.handle, True)
+    solve(flags=bt.BTTB_GMRES_NO_GRAPH)
+    kids = {"fft_passes": bt.BTTB_K_FFT, "gs_dots": 3, "gs_update": 4, "norm_givens": 5, "normalise_advance": 6,
+            "block_product_fp32": bt.BTTB_K_BLOCK_PRODUCT_PREC + bt.BTTB_MV_FP32,
+            "block_product_doublefloat": bt.BTTB_K_BLOCK_PRODUCT_PREC + bt.BTTB_MV_FP64}
+    breakdown = {}
+    for name, kid in kids.items():
+        st = bt.bttb_profile_read(plan.handle, kid)
+        breakdown[name] = {"launches": st.launches, "avg_us": st.ms * 1e3 / max(st.launches, 1),
+                           "total_ms": st.ms}
+    bt.bttb_profile(plan.handle, False)
+
     # end to end through the C ABI with host buffers
     vh = torch.from_numpy(v_host).pin_memory()
     ih = torch.zeros_like(vh).pin_memory()
@@ -373,6 +387,7 @@ def run_ours(args):
                   "block_jacobi_ir_ms": bj_ms, "block_jacobi_ir_iters": bj_res.iters,
                   "speedup_bj_ir_vs_fp64": fp64_ms / bj_ms},
         "matvec": mv,
+        "step_breakdown_host_driven": breakdown,
     }
     print(json.dumps(line), flush=True)
     barrier(world)

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
     constexpr int NPL = GElem<A>::planes;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    pdl_wait();
     if (a.active) {                                        // skip a group of finished columns (uniform)
         bool any = false;
         for (int c = 0; c < a.kc; ++c) any |= a.active[c] != 0;
@@ -231,6 +232,7 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
                         store_vec<A, native_fmt<A>>(a.v, (long)bin * a.ubs + (long)c * b + p0 + r, acc[c][r].result());
         }
     }
+    pdl_trigger();
     if (failed && lane == 0) {
         // drain copies that may still be in flight into this warp's stages
         for (int d = nitems - 1; d >= 0 && d >= nitems - kWarpStages; --d)
@@ -306,8 +308,9 @@ static int launch_contract_impl(Plan *p, const void *u, void *v, int k, const in
         a.v = reinterpret_cast<C *>(v) + (long)c0 * b;
         a.active = active ? active + c0 : nullptr;
         const int tok = prof_begin(p, BTTB_K_BLOCK_PRODUCT_PREC + prec_of<A>());
-        kern<<<grid, kConsumerWarps * 32, smem, p->stream>>>(a);
+        e = launch_pdl(kern, dim3(grid), dim3(kConsumerWarps * 32), smem, p->stream, a);
         count_launch(p);
+        if (e != cudaSuccess) return check_cuda(p, e, "contract launch");
         // algorithmic bytes: spectrum planes once, transformed vectors in and out
         prof_end(p, tok, (double)a.nbins * ((double)b * b * sizeof(GT) * NPL + 2.0 * a.kc * b * sizeof(C)));
         e = cudaGetLastError();

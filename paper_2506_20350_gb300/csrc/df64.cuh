@@ -84,6 +84,43 @@ __device__ __forceinline__ df df_dot2(df a, df c, df b, df d, float sb) {
     return r;
 }
 
+// Reciprocal and square root: one Newton step from the binary32 estimate with
+// the residual formed exactly by FMA (Karp and Markstein, "High-precision
+// division and square root", ACM TOMS 1997); relative error ~2^-46.
+__device__ __forceinline__ df df_recip(df b) {
+    const float r0 = __frcp_rn(b.hi);
+    float e = __fmaf_rn(-b.hi, r0, 1.0f);          // 1 - b.hi r0, exact
+    e = __fmaf_rn(-b.lo, r0, e);
+    df r;
+    fast_two_sum(r0, __fmul_rn(r0, e), r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ df df_sqrt(df a) {
+    if (!(a.hi > 0.f)) return df{0.f, 0.f};
+    const float s0 = __fsqrt_rn(a.hi);
+    const float p = __fmul_rn(s0, s0);
+    const float pe = __fmaf_rn(s0, s0, -p);        // s0^2 = p + pe exactly
+    const float e = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
+    df r;
+    fast_two_sum(s0, __fdiv_rn(e, __fmul_rn(2.0f, s0)), r.hi, r.lo);
+    return r;
+}
+
+// Complex double-float helpers (value type; storage is cdf).
+struct dfc { df re, im; };
+__device__ __forceinline__ dfc dfc_load(cdf v) { return dfc{df{v.rh, v.rl}, df{v.ih, v.il}}; }
+__device__ __forceinline__ cdf dfc_store(dfc v) { return cdf{v.re.hi, v.im.hi, v.re.lo, v.im.lo}; }
+__device__ __forceinline__ dfc dfc_add(dfc a, dfc b) { return dfc{df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dfc dfc_sub(dfc a, dfc b) { return dfc{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ dfc dfc_conj(dfc a) { return dfc{a.re, df_neg(a.im)}; }
+__device__ __forceinline__ dfc dfc_neg(dfc a) { return dfc{df_neg(a.re), df_neg(a.im)}; }
+__device__ __forceinline__ dfc dfc_mul(dfc a, dfc b) {
+    return dfc{df_dot2(a.re, b.re, a.im, b.im, -1.f), df_dot2(a.re, b.im, a.im, b.re, 1.f)};
+}
+__device__ __forceinline__ dfc dfc_scale(dfc a, df k) { return dfc{df_mul(a.re, k), df_mul(a.im, k)}; }
+__device__ __forceinline__ df dfc_abs2(dfc a) { return df_dot2(a.re, a.re, a.im, a.im, 1.f); }
+
 // Conversions between binary64 and double-float (binary64 pipe, used only
 // at the boundary of the library: a handful of operations per element).
 __device__ __forceinline__ df df_from_double(double v) {

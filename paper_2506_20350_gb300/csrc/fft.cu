@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int o = blockIdx.x, c = blockIdx.z;
+    pdl_wait();
     if (a.active && !a.active[c]) return;                  // finished column (uniform per CTA)
     const int p0 = blockIdx.y * a.P;
     const int P = a.P, lP = a.log2P, M = a.M;
@@ -236,6 +237,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
         Ns *= R;
     }
 
+    pdl_trigger();                                         // the next pass may start launching
     const long obase = (long)c * a.out_cs + (long)o * a.out_os;
     for (int idx = tid; idx < a.nout * P; idx += nt) {
         const int n = idx >> lP, pp = idx & (P - 1), pi = p0 + pp;
@@ -254,8 +256,9 @@ static int launch_one(Plan *p, const FftPass &a) {
     }
     dim3 grid(a.O, (a.pdim + a.P - 1) / a.P, a.ncols);
     const int tok = prof_begin(p, BTTB_K_FFT);
-    kern<<<grid, kFftThreads, smem, p->stream>>>(a);
+    cudaError_t le = launch_pdl(kern, grid, dim3(kFftThreads), smem, p->stream, a);
     count_launch(p);
+    if (le != cudaSuccess) return check_cuda(p, le, "fft pass launch");
     auto esz = [](int f) { return f == FMT_C128 ? 16.0 : (f == FMT_C64 ? 8.0 : 16.0); };
     prof_end(p, tok, (double)a.O * a.pdim * a.ncols * (a.nin * esz(INF) + a.nout * esz(OUTF)));
     return check_cuda(p, cudaGetLastError(), "fft pass launch");

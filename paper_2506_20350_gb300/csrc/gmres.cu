@@ -9,9 +9,10 @@
 //   beta = ||w|| ; Givens rotations of the Hessenberg column ; v_{j+1} = w/beta
 // Every cycle starts from the true residual r = V - Z x computed with the FP64
 // product, so a cycle whose inner products are binary32 is one step of
-// iterative refinement (GMRES-IR).  All vectors, inner products and updates
-// are double-float (48-bit); Hessenberg, rotations and the triangular solve
-// are binary64 scalars.  Converged columns are masked.
+// iterative refinement (GMRES-IR).  Vectors, inner products, updates, the
+// Hessenberg matrix, the rotations and the triangular solve are all
+// double-float (48-bit significand) on the binary32 pipes: scalar binary64
+// code is slow on this GPU.  Converged columns are masked.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -28,9 +29,13 @@ struct GmresWork {
     bool flex = false;
     int NB = 0, nblk = 0;
     float4 *X = nullptr, *Vb = nullptr, *Zb = nullptr, *W = nullptr, *R = nullptr, *Vin = nullptr;
-    double2 *H = nullptr, *hacc = nullptr, *gv = nullptr, *sn = nullptr;
+    // Hessenberg [c][(m+1)*m] column-major, accumulated CGS coefficients [c][m+1],
+    // rotation sines [c][m] and right-hand side [c][m+1]: complex double-float;
+    // rotation cosines [c][m]: real double-float.
+    float4 *H = nullptr, *hacc = nullptr, *gv = nullptr, *sn = nullptr;
+    float2 *cs = nullptr;
     float4 *hco = nullptr, *ycoef = nullptr, *part = nullptr;
-    double *cs = nullptr, *beta2 = nullptr, *vnorm = nullptr, *inv_beta = nullptr, *target = nullptr;
+    double *beta2 = nullptr, *vnorm = nullptr, *inv_beta = nullptr, *target = nullptr;
     int *active = nullptr, *steps = nullptr, *bdown = nullptr, *mlimit = nullptr, *d_j = nullptr, *d_any = nullptr;
     double2 *io = nullptr;        // staging for host_io
     int *h_any = nullptr;         // pinned
@@ -78,82 +83,50 @@ __device__ __forceinline__ void warp_reduce_dacc(dacc &a) {
     }
 }
 
-// part[(c*maxcnt + i)*nblk + blk] = sum over the block's chunk of conj(B_i[n]) w[n]
-// for i < cnt, cnt = (*cnt_dev + 1) or cnt_fixed.  B_i of column c at
-// basis + i*bs_i + c*bs_c.
-__global__ void __launch_bounds__(kVecThreads) dots_partial_kernel(const float4 *basis, long bs_i, long bs_c,
-                                                                   const int *cnt_dev, int cnt_fixed,
-                                                                   const float4 *w, long n, int NB, int nblk,
-                                                                   int maxcnt, float4 *part, const int *active) {
-    extern __shared__ __align__(16) float4 wsm[];
+// ||x_c||^2 partials: part[c*pstride + blk] over the block's chunk of NB entries.
+__global__ void __launch_bounds__(kVecThreads) norm_partial_kernel(const float4 *x, long n, int NB, int nblk,
+                                                                   long pstride, float4 *part) {
+    __shared__ dacc red[kVecThreads / 32];
     const int c = blockIdx.y, blk = blockIdx.x;
-    if (active && !active[c]) return;
-    const int cnt = cnt_dev ? (*cnt_dev + 1) : cnt_fixed;
     const long n0 = (long)blk * NB;
     const int len = (int)min((long)NB, n - n0);
-    for (int e = threadIdx.x; e < len; e += blockDim.x) wsm[e] = w[(long)c * n + n0 + e];
+    dacc acc{0.f, 0.f};
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const float4 v = x[(long)c * n + n0 + e];
+        dacc_mac(acc, v.x, v.z, v.x, v.z);
+        dacc_mac(acc, v.y, v.w, v.y, v.w);
+    }
+    warp_reduce_dacc(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int i = warp; i < cnt; i += nw) {
-        const float4 *bv = basis + (long)i * bs_i + (long)c * bs_c + n0;
-        dacc re{0.f, 0.f}, im{0.f, 0.f};
-        for (int e = lane; e < len; e += 32) {
-            const float4 v = bv[e], x = wsm[e];
-            // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
-            dacc_mac(re, v.x, v.z, x.x, x.z);
-            dacc_mac(re, v.y, v.w, x.y, x.w);
-            dacc_mac(im, v.x, v.z, x.y, x.w);
-            dacc_mac(im, -v.y, -v.w, x.x, x.z);
-        }
-        warp_reduce_dacc(re);
-        warp_reduce_dacc(im);
-        if (lane == 0) {
-            df r = dacc_result(re), q = dacc_result(im);
-            part[((long)c * maxcnt + i) * nblk + blk] = make_float4(r.hi, q.hi, r.lo, q.lo);
-        }
+    if (threadIdx.x == 0) {
+        dacc t = red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) dacc_add(t, red[w]);
+        const df r = dacc_result(t);
+        part[(long)c * pstride + blk] = make_float4(r.hi, 0.f, r.lo, 0.f);
     }
 }
 
-// mode 0: hco = sum, hacc = sum ; mode 1: hco = sum, hacc += sum ; mode 2: out_real[c] = Re(sum)
-__global__ void dots_reduce_kernel(const float4 *part, int nblk, const int *cnt_dev, int cnt_fixed, int maxcnt,
-                                   float4 *hco, double2 *hacc, int mode, double *out_real, const int *active) {
-    const int i = blockIdx.x, c = blockIdx.y, lane = threadIdx.x;
-    if (active && !active[c]) return;
-    const int cnt = cnt_dev ? (*cnt_dev + 1) : cnt_fixed;
-    if (i >= cnt) return;
-    const float4 *pp = part + ((long)c * maxcnt + i) * nblk;
-    dacc re{0.f, 0.f}, im{0.f, 0.f};
+// beta2[c] = sum of the column's partials (one warp per column).
+__global__ void norm_final_kernel(const float4 *part, int nblk, long pstride, double *beta2) {
+    const int c = blockIdx.x, lane = threadIdx.x;
+    dacc acc{0.f, 0.f};
     for (int e = lane; e < nblk; e += 32) {
-        const float4 v = pp[e];
-        dacc_add(re, dacc{v.x, v.z});
-        dacc_add(im, dacc{v.y, v.w});
+        const float4 v = part[(long)c * pstride + e];
+        dacc_add(acc, dacc{v.x, v.z});
     }
-    warp_reduce_dacc(re);
-    warp_reduce_dacc(im);
-    if (lane == 0) {
-        df r = dacc_result(re), q = dacc_result(im);
-        if (mode == 2) {
-            out_real[c] = df_to_double(r);
-        } else {
-            hco[(long)c * maxcnt + i] = make_float4(r.hi, q.hi, r.lo, q.lo);
-            const double2 v = make_double2(df_to_double(r), df_to_double(q));
-            double2 &h = hacc[(long)c * maxcnt + i];
-            if (mode == 0) h = v;
-            else h = make_double2(h.x + v.x, h.y + v.y);
-        }
-    }
+    warp_reduce_dacc(acc);
+    if (lane == 0) beta2[c] = df_to_double(dacc_result(acc));
 }
 
-// w[c][n] += sgn * sum_{i < cnt} B_i[c][n] coef[c][i], with cnt = *cnt_dev + 1,
-// or cnt_col[c] per column when cnt_col is given.
+// w[c][n] += sgn * sum_{i < cnt_col[c]} B_i[c][n] coef[c][i]
 __global__ void __launch_bounds__(kVecThreads) update_kernel(const float4 *basis, long bs_i, long bs_c,
-                                                             const int *cnt_dev, const int *cnt_col,
-                                                             const float4 *coef, int maxcnt, float4 *w, long n,
-                                                             float sgn, const int *active) {
+                                                             const int *cnt_col, const float4 *coef, int maxcnt,
+                                                             float4 *w, long n, float sgn, const int *active) {
     extern __shared__ __align__(16) float4 csm[];
     const int c = blockIdx.y;
     if (active && !active[c]) return;
-    const int cnt = cnt_col ? cnt_col[c] : (*cnt_dev + 1);
+    const int cnt = cnt_col[c];
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         float4 h = coef[(long)c * maxcnt + i];
         csm[i] = make_float4(sgn * h.x, sgn * h.y, sgn * h.z, sgn * h.w);
@@ -176,13 +149,13 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(const float4 *basis
     }
 }
 
-// Vb[*d_j][c] = W[c] * inv_beta[c]
-__global__ void scale_kernel(const float4 *w, float4 *vb, long bs_i, long bs_c, const int *d_j,
+// Vb[j][c] = W[c] * inv_beta[c]
+__global__ void scale_kernel(const float4 *w, float4 *vb, long bs_i, long bs_c, int j,
                              const double *inv_beta, long n, const int *active) {
     const int c = blockIdx.y;
     if (active && !active[c]) return;
     const df s = df_from_double(inv_beta[c]);
-    float4 *dst = vb + (long)(*d_j) * bs_i + (long)c * bs_c;
+    float4 *dst = vb + (long)j * bs_i + (long)c * bs_c;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
         const float4 x = w[(long)c * n + e];
         const df r = df_mul(df{x.x, x.z}, s), q = df_mul(df{x.y, x.w}, s);
@@ -200,40 +173,35 @@ __global__ void resid_kernel(const float4 *vin, const float4 *zx, float4 *r, lon
 }
 
 // Start of a cycle: g = (beta0, 0, ...), inv_beta = 1/beta0, j = 0.
-__global__ void cycle_start_kernel(const double *beta2, double2 *gv, double *inv_beta, int m, int k,
-                                   const int *active, int *d_j) {
+__global__ void cycle_start_kernel(const double *beta2, float4 *gv, double *inv_beta, int m, int k,
+                                   const int *active) {
     for (int c = threadIdx.x; c < k; c += blockDim.x) {
         if (!active[c]) continue;
         const double b0 = sqrt(beta2[c]);
-        double2 *g = gv + (long)c * (m + 1);
-        g[0] = make_double2(b0, 0.0);
-        for (int i = 1; i <= m; ++i) g[i] = make_double2(0.0, 0.0);
+        float4 *g = gv + (long)c * (m + 1);
+        const df r = df_from_double(b0);
+        g[0] = make_float4(r.hi, 0.f, r.lo, 0.f);
+        for (int i = 1; i <= m; ++i) g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         inv_beta[c] = 1.0 / b0;
     }
-    if (threadIdx.x == 0) *d_j = 0;
 }
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
-
-// One Givens step of column c by one warp (binary64 scalars).  The lanes stage
-// the Hessenberg column and the earlier rotations in shared memory (3m+2
-// double2 at `wsm`), lane 0 applies the rotations in order from there.
-// Returns (on every lane) whether the column continues.
-__device__ int givens_column(int c, int j, int m, double2 *wsm, double2 *H, const double2 *hacc,
-                             const double *beta2, double *cs, double2 *sn, double2 *gv, int *active, int *steps,
-                             int *bdown, const int *mlimit, const double *target, double *inv_beta, int *err) {
+// One Givens step of column c by one warp, in double-float.  The lanes stage
+// the Hessenberg column and the earlier rotations in shared memory (`wsm`,
+// 3m+2 float4), lane 0 applies the rotations in order.  Returns (on every
+// lane) whether the column continues.
+__device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const float4 *hacc, double beta2,
+                             float2 *cs, float4 *sn, float4 *gv, int *active, int *steps, int *bdown,
+                             const int *mlimit, const double *target, double *inv_beta, int *err) {
     const int lane = threadIdx.x & 31;
-    double2 *hcol = wsm;                                        // m+1 entries
-    double2 *snw = hcol + (m + 1);                              // m entries
-    double *csw = reinterpret_cast<double *>(snw + m);          // m entries
-    double2 *Hc = H + (long)c * (m + 1) * m;
-    const double2 *ha = hacc + (long)c * (m + 1);
-    double zn2 = 0.0;
+    float4 *hcol = wsm;                                         // m+1 entries
+    float4 *snw = hcol + (m + 1);                               // m entries
+    float2 *csw = reinterpret_cast<float2 *>(snw + m);          // m entries
+    float4 *Hc = H + (long)c * (m + 1) * m;
+    const float4 *ha = hacc + (long)c * (m + 1);
+    float zn2 = 0.f;
     for (int i = lane; i <= j; i += 32) {
-        const double2 h = ha[i];
+        const float4 h = ha[i];
         hcol[i] = h;
         zn2 += h.x * h.x + h.y * h.y;
     }
@@ -246,49 +214,56 @@ __device__ int givens_column(int c, int j, int m, double2 *wsm, double2 *H, cons
     __syncwarp();
     int cont = 0;
     if (lane == 0) {
-        const double beta = sqrt(fmax(beta2[c], 0.0));
-        const double zn = sqrt(zn2 + beta * beta);
-        if (!isfinite(zn)) {
+        const df beta = df_sqrt(df_from_double(fmax(beta2, 0.0)));
+        const float zn = sqrtf(zn2 + beta.hi * beta.hi);
+        if (!isfinite(zn) || !isfinite(beta.hi)) {
             atomicOr(err, DEVERR_NONFINITE);
             active[c] = 0;
         } else {
             for (int i = 0; i < j; ++i) {
-                const double2 a0 = hcol[i], a1 = hcol[i + 1], s = snw[i];
-                const double ci = csw[i];
-                hcol[i] = make_double2(ci * a0.x + (s.x * a1.x - s.y * a1.y), ci * a0.y + (s.x * a1.y + s.y * a1.x));
-                // -conj(s) a0 + c a1
-                hcol[i + 1] = make_double2(-(s.x * a0.x + s.y * a0.y) + ci * a1.x,
-                                           -(s.x * a0.y - s.y * a0.x) + ci * a1.y);
+                const dfc a0 = dfc_load(*reinterpret_cast<const cdf *>(&hcol[i]));
+                const dfc a1 = dfc_load(*reinterpret_cast<const cdf *>(&hcol[i + 1]));
+                const dfc si = dfc_load(*reinterpret_cast<const cdf *>(&snw[i]));
+                const df ci{csw[i].x, csw[i].y};
+                // (a0, a1) <- (c a0 + s a1, -conj(s) a0 + c a1)
+                const dfc n0 = dfc_add(dfc_scale(a0, ci), dfc_mul(si, a1));
+                const dfc n1 = dfc_sub(dfc_scale(a1, ci), dfc_mul(dfc_conj(si), a0));
+                *reinterpret_cast<cdf *>(&hcol[i]) = dfc_store(n0);
+                *reinterpret_cast<cdf *>(&hcol[i + 1]) = dfc_store(n1);
             }
-            const double2 a = hcol[j];
-            const double aa = hypot(a.x, a.y);
-            const double rho = hypot(aa, beta);
-            double c_;
-            double2 s_;
-            if (aa == 0.0) {
-                c_ = 0.0;
-                s_ = make_double2(1.0, 0.0);
+            const dfc a = dfc_load(*reinterpret_cast<const cdf *>(&hcol[j]));
+            const df aa2 = dfc_abs2(a);
+            const df rho = df_sqrt(df_add(aa2, df_mul(beta, beta)));
+            df c_;
+            dfc s_;
+            if (!(aa2.hi > 0.f)) {
+                c_ = df{0.f, 0.f};
+                s_ = dfc{df{1.f, 0.f}, df{0.f, 0.f}};
             } else {
-                c_ = aa / rho;
-                s_ = make_double2(a.x / aa * beta / rho, a.y / aa * beta / rho);
+                const df aa = df_sqrt(aa2);
+                const df inv_rho = df_recip(rho);
+                c_ = df_mul(aa, inv_rho);
+                s_ = dfc_scale(a, df_mul(df_mul(beta, inv_rho), df_recip(aa)));   // (a/|a|) beta/rho
             }
-            cs[(long)c * m + j] = c_;
-            sn[(long)c * m + j] = s_;
-            hcol[j] = make_double2(c_ * a.x + s_.x * beta, c_ * a.y + s_.y * beta);
-            double2 *g = gv + (long)c * (m + 1);
-            const double2 gj = g[j];
-            // g[j+1] = -conj(s) g[j] ; g[j] = c g[j]
-            g[j + 1] = make_double2(-(s_.x * gj.x + s_.y * gj.y), -(s_.x * gj.y - s_.y * gj.x));
-            g[j] = make_double2(c_ * gj.x, c_ * gj.y);
+            cs[(long)c * m + j] = make_float2(c_.hi, c_.lo);
+            *reinterpret_cast<cdf *>(&sn[(long)c * m + j]) = dfc_store(s_);
+            // new diagonal c a + s beta
+            const dfc hj = dfc_add(dfc_scale(a, c_), dfc_scale(s_, beta));
+            *reinterpret_cast<cdf *>(&hcol[j]) = dfc_store(hj);
+            float4 *g = gv + (long)c * (m + 1);
+            const dfc gj = dfc_load(*reinterpret_cast<const cdf *>(&g[j]));
+            const dfc gj1 = dfc_neg(dfc_mul(dfc_conj(s_), gj));         // g[j+1] = -conj(s) g[j]
+            *reinterpret_cast<cdf *>(&g[j + 1]) = dfc_store(gj1);
+            *reinterpret_cast<cdf *>(&g[j]) = dfc_store(dfc_scale(gj, c_));
             steps[c] = j + 1;
-            const bool bd = !(beta > 1e-14 * zn);
+            const bool bd = !(beta.hi > 1e-14f * zn);
             if (bd) bdown[c] = 1;
-            const double est = hypot(g[j + 1].x, g[j + 1].y);
+            const double est = sqrt(df_to_double(dfc_abs2(gj1)));
             const bool done = bd || est <= target[c] || (j + 1) >= mlimit[c];
             if (done) {
                 active[c] = 0;
             } else {
-                inv_beta[c] = 1.0 / beta;
+                inv_beta[c] = 1.0 / df_to_double(beta);
                 cont = 1;
             }
         }
@@ -299,47 +274,130 @@ __device__ int givens_column(int c, int j, int m, double2 *wsm, double2 *H, cons
 }
 
 // ---------------------------------------------------------------------------
-// Fused Arnoldi-step kernels.  One CTA = 256 consecutive entries of one
-// column; grid (nblk, k).  Partial sums of a column are combined by the last
-// CTA of that column to arrive (per-column counter, fixed summation order).
+// Arnoldi-step kernels.  Partial sums of a column are combined by the last CTA
+// of that column to arrive (per-column counter, fixed summation order).
 // ---------------------------------------------------------------------------
 constexpr int kStepNB = 256;
-constexpr int kStepWarps = kStepNB / 32;
 
-// Per-CTA partial dots conj(B_i) . x over the CTA's chunk for i < cnt, x staged
-// in xs; warp w takes i = w, w+8, ...  Result to part[(c*maxcnt + i)*nblk + blk].
-__device__ __forceinline__ void cta_dots(const float4 *basis, long bs_i, long boff, const float4 *xs, int len,
-                                         int cnt, float4 *part, long pbase, int nblk, int blk) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < cnt; i += kStepWarps) {
-        const float4 *bv = basis + (long)i * bs_i + boff;
-        dacc re{0.f, 0.f}, im{0.f, 0.f};
-#pragma unroll 4
-        for (int e = lane; e < len; e += 32) {
-            const float4 v = bv[e], x = xs[e];
-            dacc_mac(re, v.x, v.z, x.x, x.z);
-            dacc_mac(re, v.y, v.w, x.y, x.w);
-            dacc_mac(im, v.x, v.z, x.y, x.w);
-            dacc_mac(im, -v.y, -v.w, x.x, x.z);
-        }
-        warp_reduce_dacc(re);
-        warp_reduce_dacc(im);
-        if (lane == 0) {
-            const df r = dacc_result(re), q = dacc_result(im);
-            part[(pbase + i) * nblk + blk] = make_float4(r.hi, q.hi, r.lo, q.lo);
-        }
+// Returns true in every thread of the CTA that arrives last on `counter`.
+__device__ __forceinline__ bool arrive_last(unsigned *counter, int total) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(counter, 1u);
+        s_last = (prev == (unsigned)total - 1);
+        if (s_last) *counter = 0u;                 // ready for the next use
     }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
 }
 
-// Last CTA of column c: sum the partials of i < cnt in block order.
-// mode 0: hco = h, hacc = h ; mode 1: hco = h, hacc += h ; mode 2: beta2 = Re h_0
-__device__ __forceinline__ void last_cta_reduce(const float4 *part, long pbase, int nblk, int cnt, int mode,
-                                                float4 *hco, double2 *hacc, double *beta2, int c) {
+// Gram-Schmidt dots: CTA (blk, ich, c) covers entries [blk*kDotNE, +kDotNE) of
+// column c; warp w takes basis vector i = ich*kDotIW + w.  CTAs whose vectors
+// are all beyond j exit without arriving; the last of the rest sums the
+// partials in block order: mode 0 sets hco = hacc = h, mode 1 sets hco = h and
+// adds h to hacc.
+constexpr int kDotNE = 1024;
+constexpr int kDotIW = 8;
+
+struct StepArgs {
+    const float4 *Vb;      // basis [i][c][n]
+    float4 *W;             // [c][n]
+    long n, bs_i, bs_c;
+    int m, k;
+    int nblk_dot, ich;     // dots grid
+    int nblk_vec;          // update / scale grid (kStepNB entries per CTA)
+    float4 *part;          // [c][m+1][nblk_dot] (dots), reused as [c][nblk_vec] (norm)
+    long pstride;          // (m+1)*max(nblk_dot, nblk_vec) per column
+    float4 *hco;           // [c][m+1]
+    float4 *hacc;          // [c][m+1]
+    unsigned *cnt_a, *cnt_b, *cnt_c, *cnt_d;
+    int *active;
+    int *d_any_step;
+    float4 *H, *gv, *sn;
+    float2 *cs;
+    double *inv_beta;
+    int *steps, *bdown;
+    const int *mlimit;
+    const double *target;
+    int *err;
+};
+
+// Pass 0 forms its coefficients in binary32 from the hi parts (the double-float
+// second pass projects out whatever they miss, so h = h1 + h2 keeps full
+// accuracy); pass 1 is double-float throughout.
+__global__ void __launch_bounds__(kDotIW * 32) step_dots_kernel(const StepArgs a, int mode, unsigned *counter,
+                                                                 int j) {
+    const int blk = blockIdx.x, c = blockIdx.z;
+    pdl_wait();
+    if (!a.active[c]) return;
+    const int cnt = j + 1;
+    const int nich = (cnt + kDotIW - 1) / kDotIW;
+    if ((int)blockIdx.y >= nich) return;                  // no vector of this CTA is in use
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < cnt; i += kStepWarps) {
-        const float4 *pp = part + (pbase + i) * nblk;
+    const int i = blockIdx.y * kDotIW + warp;
+    const long n0 = (long)blk * kDotNE;
+    const int len = (int)min((long)kDotNE, a.n - n0);
+    float4 *part = a.part + (long)c * a.pstride;
+    if (i < cnt && mode == 0) {
+        const float4 *bv = a.Vb + (long)i * a.bs_i + (long)c * a.bs_c + n0;
+        const float4 *xv = a.W + (long)c * a.n + n0;
+        float re = 0.f, im = 0.f, re1 = 0.f, im1 = 0.f;
+#pragma unroll 8
+        for (int e = lane; e < len; e += 64) {
+            const float4 v = bv[e], x = xv[e];
+            re = fmaf(v.x, x.x, fmaf(v.y, x.y, re));
+            im = fmaf(v.x, x.y, fmaf(-v.y, x.x, im));
+            if (e + 32 < len) {
+                const float4 v2 = bv[e + 32], x2 = xv[e + 32];
+                re1 = fmaf(v2.x, x2.x, fmaf(v2.y, x2.y, re1));
+                im1 = fmaf(v2.x, x2.y, fmaf(-v2.y, x2.x, im1));
+            }
+        }
+        re += re1;
+        im += im1;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, off);
+            im += __shfl_xor_sync(0xffffffffu, im, off);
+        }
+        if (lane == 0) part[(long)i * a.nblk_dot + blk] = make_float4(re, im, 0.f, 0.f);
+    } else if (i < cnt) {
+        const float4 *bv = a.Vb + (long)i * a.bs_i + (long)c * a.bs_c + n0;
+        const float4 *xv = a.W + (long)c * a.n + n0;
+        dacc re0{0.f, 0.f}, im0{0.f, 0.f}, re1{0.f, 0.f}, im1{0.f, 0.f};
+#pragma unroll 4
+        for (int e = lane; e < len; e += 64) {
+            const float4 v = bv[e], x = xv[e];
+            dacc_mac(re0, v.x, v.z, x.x, x.z);
+            dacc_mac(re0, v.y, v.w, x.y, x.w);
+            dacc_mac(im0, v.x, v.z, x.y, x.w);
+            dacc_mac(im0, -v.y, -v.w, x.x, x.z);
+            if (e + 32 < len) {
+                const float4 v2 = bv[e + 32], x2 = xv[e + 32];
+                dacc_mac(re1, v2.x, v2.z, x2.x, x2.z);
+                dacc_mac(re1, v2.y, v2.w, x2.y, x2.w);
+                dacc_mac(im1, v2.x, v2.z, x2.y, x2.w);
+                dacc_mac(im1, -v2.y, -v2.w, x2.x, x2.z);
+            }
+        }
+        dacc_add(re0, re1);
+        dacc_add(im0, im1);
+        warp_reduce_dacc(re0);
+        warp_reduce_dacc(im0);
+        if (lane == 0) {
+            const df r = dacc_result(re0), q = dacc_result(im0);
+            part[(long)i * a.nblk_dot + blk] = make_float4(r.hi, q.hi, r.lo, q.lo);
+        }
+    }
+    pdl_trigger();
+    if (!arrive_last(counter + c, a.nblk_dot * nich)) return;
+    for (int ii = warp; ii < cnt; ii += kDotIW) {
+        const float4 *pp = part + (long)ii * a.nblk_dot;
         dacc re{0.f, 0.f}, im{0.f, 0.f};
-        for (int e = lane; e < nblk; e += 32) {
+        for (int e = lane; e < a.nblk_dot; e += 32) {
             const float4 v = __ldcg(pp + e);
             dacc_add(re, dacc{v.x, v.z});
             dacc_add(im, dacc{v.y, v.w});
@@ -348,31 +406,17 @@ __device__ __forceinline__ void last_cta_reduce(const float4 *part, long pbase, 
         warp_reduce_dacc(im);
         if (lane == 0) {
             const df r = dacc_result(re), q = dacc_result(im);
-            if (mode == 2) {
-                beta2[c] = df_to_double(r);
+            const long hidx = (long)c * (a.m + 1) + ii;
+            a.hco[hidx] = make_float4(r.hi, q.hi, r.lo, q.lo);
+            if (mode == 0) {
+                a.hacc[hidx] = make_float4(r.hi, q.hi, r.lo, q.lo);
             } else {
-                hco[pbase + i] = make_float4(r.hi, q.hi, r.lo, q.lo);
-                const double2 v = make_double2(df_to_double(r), df_to_double(q));
-                double2 &h = hacc[pbase + i];
-                h = mode == 0 ? v : make_double2(h.x + v.x, h.y + v.y);
+                const float4 o = a.hacc[hidx];
+                const df nr = df_add(df{o.x, o.z}, r), ni = df_add(df{o.y, o.w}, q);
+                a.hacc[hidx] = make_float4(nr.hi, ni.hi, nr.lo, ni.lo);
             }
         }
     }
-}
-
-// Returns true in every thread of the CTA that arrives last for column c.
-__device__ __forceinline__ bool arrive_last(unsigned *counter, int nblk) {
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(counter, 1u);
-        s_last = (prev == (unsigned)nblk - 1);
-        if (s_last) *counter = 0u;                 // ready for the next use
-    }
-    __syncthreads();
-    if (s_last) __threadfence();
-    return s_last != 0;
 }
 
 // w -= sum_{i<cnt} B_i h_i for this thread's entry (compensated), returns the new value.
@@ -392,116 +436,65 @@ __device__ __forceinline__ float4 cta_update_entry(const float4 *basis, long bs_
     return make_float4(r.hi, q.hi, r.lo, q.lo);
 }
 
-struct StepArgs {
-    const float4 *Vb;      // basis [i][c][n]
-    float4 *W;             // [c][n]
-    long n, bs_i, bs_c;
-    int m, k, nblk;
-    float4 *part;          // [c][m+1][nblk]
-    float4 *hco;           // [c][m+1]
-    double2 *hacc;         // [c][m+1]
-    double *beta2;
-    unsigned *cnt_a, *cnt_b, *cnt_c, *cnt_d;    // per-column arrival counters (cnt_d: one)
-    int *active;
-    int *d_j, *d_any_step;
-    // Givens
-    double2 *H, *gv, *sn;
-    double *cs, *inv_beta;
-    int *steps, *bdown;
-    const int *mlimit;
-    const double *target;
-    int *err;
-};
-
-// (A) first Gram-Schmidt pass: h = V_j^H w
-__global__ void __launch_bounds__(kStepNB) step_dots_kernel(const StepArgs a) {
-    __shared__ float4 xs[kStepNB];
+// w -= V h (one entry per thread).  With `last` set (second pass) the kernel
+// also forms ||w||^2 and the last CTA of the column runs its Givens step.
+__global__ void __launch_bounds__(kStepNB) step_update_kernel(const StepArgs a, int last, int j) {
+    extern __shared__ __align__(16) float4 dyn[];          // hs: m+1, then Givens scratch 3m+2
+    __shared__ dacc red[kStepNB / 32];
     const int c = blockIdx.y, blk = blockIdx.x;
+    pdl_wait();
     if (!a.active[c]) return;
-    const int cnt = *a.d_j + 1;
-    const long n0 = (long)blk * kStepNB;
-    const int len = (int)min((long)kStepNB, a.n - n0);
-    if ((int)threadIdx.x < len) xs[threadIdx.x] = a.W[(long)c * a.n + n0 + threadIdx.x];
-    __syncthreads();
-    const long pbase = (long)c * (a.m + 1);
-    cta_dots(a.Vb, a.bs_i, (long)c * a.bs_c + n0, xs, len, cnt, a.part, pbase, a.nblk, blk);
-    if (!arrive_last(a.cnt_a + c, a.nblk)) return;
-    last_cta_reduce(a.part, pbase, a.nblk, cnt, 0, a.hco, a.hacc, nullptr, c);
-}
-
-// (B) w -= V h (first pass), then the second pass h2 = V^H w
-__global__ void __launch_bounds__(kStepNB) step_update_dots_kernel(const StepArgs a) {
-    __shared__ float4 xs[kStepNB];
-    extern __shared__ __align__(16) float4 hs[];          // m+1
-    const int c = blockIdx.y, blk = blockIdx.x;
-    if (!a.active[c]) return;
-    const int cnt = *a.d_j + 1;
-    const long pbase = (long)c * (a.m + 1);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const float4 h = a.hco[pbase + i];
-        hs[i] = make_float4(-h.x, -h.y, -h.z, -h.w);
-    }
-    __syncthreads();
-    const long n0 = (long)blk * kStepNB;
-    const int len = (int)min((long)kStepNB, a.n - n0);
-    const int t = threadIdx.x;
-    if (t < len) {
-        const long e = (long)c * a.n + n0 + t;
-        const float4 x = cta_update_entry(a.Vb, a.bs_i, (long)c * a.bs_c + n0 + t, hs, cnt, a.W[e]);
-        a.W[e] = x;
-        xs[t] = x;
-    }
-    __syncthreads();
-    cta_dots(a.Vb, a.bs_i, (long)c * a.bs_c + n0, xs, len, cnt, a.part, pbase, a.nblk, blk);
-    if (!arrive_last(a.cnt_b + c, a.nblk)) return;
-    last_cta_reduce(a.part, pbase, a.nblk, cnt, 1, a.hco, a.hacc, nullptr, c);
-}
-
-// (C) w -= V h2, beta^2 = ||w||^2, then (last CTA of the column) one Givens step
-__global__ void __launch_bounds__(kStepNB) step_update_norm_givens_kernel(const StepArgs a) {
-    __shared__ float4 xs[kStepNB];
-    extern __shared__ __align__(16) float4 dyn[];          // hs: m+1 float4, then Givens scratch
-    const int c = blockIdx.y, blk = blockIdx.x;
-    if (!a.active[c]) return;
-    const int j = *a.d_j, cnt = j + 1;
-    const long pbase = (long)c * (a.m + 1);
+    const int cnt = j + 1;
     float4 *hs = dyn;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const float4 h = a.hco[pbase + i];
+        const float4 h = a.hco[(long)c * (a.m + 1) + i];
         hs[i] = make_float4(-h.x, -h.y, -h.z, -h.w);
     }
     __syncthreads();
-    const long n0 = (long)blk * kStepNB;
-    const int len = (int)min((long)kStepNB, a.n - n0);
-    const int t = threadIdx.x;
-    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (t < len) {
-        const long e = (long)c * a.n + n0 + t;
-        x = cta_update_entry(a.Vb, a.bs_i, (long)c * a.bs_c + n0 + t, hs, cnt, a.W[e]);
-        a.W[e] = x;
+    const long e = (long)blk * kStepNB + threadIdx.x;
+    dacc nrm{0.f, 0.f};
+    if (e < a.n) {
+        float4 &wv = a.W[(long)c * a.n + e];
+        const float4 x = cta_update_entry(a.Vb, a.bs_i, (long)c * a.bs_c + e, hs, cnt, wv);
+        wv = x;
+        dacc_mac(nrm, x.x, x.z, x.x, x.z);
+        dacc_mac(nrm, x.y, x.w, x.y, x.w);
     }
-    xs[t] = x;
+    pdl_trigger();
+    if (!last) return;
+    warp_reduce_dacc(nrm);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = nrm;
     __syncthreads();
-    cta_dots(xs - (long)0, 0, 0, xs, len, 1, a.part, pbase, a.nblk, blk);   // ||w||^2 partial (i = 0)
-    if (!arrive_last(a.cnt_c + c, a.nblk)) return;
-    last_cta_reduce(a.part, pbase, a.nblk, 1, 2, nullptr, nullptr, a.beta2, c);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double2 *wsm = reinterpret_cast<double2 *>(dyn + (a.m + 1));
-        const int cont = givens_column(c, j, a.m, wsm, a.H, a.hacc, a.beta2, a.cs, a.sn, a.gv, a.active, a.steps,
-                                       a.bdown, a.mlimit, a.target, a.inv_beta, a.err);
-        if (threadIdx.x == 0 && cont) atomicMax(a.d_any_step, j + 1);
+    float4 *part = a.part + (long)c * a.pstride;
+    if (threadIdx.x == 0) {
+        dacc t = red[0];
+        for (int w = 1; w < kStepNB / 32; ++w) dacc_add(t, red[w]);
+        const df r = dacc_result(t);
+        part[blk] = make_float4(r.hi, 0.f, r.lo, 0.f);
+    }
+    if (!arrive_last(a.cnt_c + c, a.nblk_vec)) return;
+    if (warp == 0) {
+        dacc t{0.f, 0.f};
+        for (int b2 = lane; b2 < a.nblk_vec; b2 += 32) {
+            const float4 v = __ldcg(part + b2);
+            dacc_add(t, dacc{v.x, v.z});
+        }
+        warp_reduce_dacc(t);
+        const double beta2 = df_to_double(dacc_result(t));
+        const int cont = givens_column(c, j, a.m, dyn + (a.m + 1), a.H, a.hacc, beta2, a.cs, a.sn, a.gv, a.active,
+                                       a.steps, a.bdown, a.mlimit, a.target, a.inv_beta, a.err);
+        if (lane == 0 && cont) atomicMax(a.d_any_step, j + 1);
     }
 }
 
-// (D) v_{j+1} = w / beta for continuing columns; the last CTA overall advances j.
-__global__ void __launch_bounds__(kStepNB) step_scale_advance_kernel(const StepArgs a) {
+// v_{j+1} = w / beta for continuing columns.
+__global__ void __launch_bounds__(kStepNB) step_scale_kernel(const StepArgs a, int j) {
     const int c = blockIdx.y, blk = blockIdx.x;
-    const int j = *a.d_j;
+    pdl_wait();
     if (a.active[c]) {
         const df s = df_from_double(a.inv_beta[c]);
-        const long n0 = (long)blk * kStepNB;
-        const long e = n0 + threadIdx.x;
+        const long e = (long)blk * kStepNB + threadIdx.x;
         if (e < a.n) {
             const float4 x = a.W[(long)c * a.n + e];
             const df r = df_mul(df{x.x, x.z}, s), q = df_mul(df{x.y, x.w}, s);
@@ -509,39 +502,44 @@ __global__ void __launch_bounds__(kStepNB) step_scale_advance_kernel(const StepA
                 make_float4(r.hi, q.hi, r.lo, q.lo);
         }
     }
-    if (arrive_last(a.cnt_d, a.nblk * a.k)) {
-        if (threadIdx.x == 0) *a.d_j = j + 1;
-    }
+    pdl_trigger();
 }
 
 // y = H^{-1} g (upper triangular, steps[c] x steps[c]) for column c = blockIdx.x,
-// stored as double-float.  Column-oriented back substitution: one diagonal
-// division per step, the remaining right-hand side updated in parallel.
+// in double-float.  Column-oriented back substitution: one diagonal division
+// per step, the remaining right-hand side updated in parallel.
 constexpr int kFinishThreads = 128;
 
-__global__ void __launch_bounds__(kFinishThreads) finish_kernel(const double2 *H, const double2 *gv,
+__global__ void __launch_bounds__(kFinishThreads) finish_kernel(const float4 *H, const float4 *gv,
                                                                 const int *steps, float4 *ycoef, int m,
                                                                 const int *was_active) {
-    extern __shared__ __align__(16) unsigned char fsm[];
+    extern __shared__ __align__(16) float4 rhs[];              // m+1
+    __shared__ float4 ysh;
     const int c = blockIdx.x;
     if (!was_active[c]) return;
     const int kk = steps[c];
-    double2 *rhs = reinterpret_cast<double2 *>(fsm);              // m+1
-    const double2 *Hc = H + (long)c * (m + 1) * m;
-    const double2 *g = gv + (long)c * (m + 1);
+    const float4 *Hc = H + (long)c * (m + 1) * m;
+    const float4 *g = gv + (long)c * (m + 1);
     for (int i = threadIdx.x; i < kk; i += blockDim.x) rhs[i] = g[i];
     __syncthreads();
     for (int i = kk - 1; i >= 0; --i) {
-        const double2 d = Hc[i + (long)i * (m + 1)];
-        const double dd = d.x * d.x + d.y * d.y;
-        const double2 s = rhs[i];
-        const double2 yi = dd > 0.0 ? make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd)
-                                    : make_double2(0.0, 0.0);
-        for (int l = threadIdx.x; l < i; l += blockDim.x) {
-            const double2 t = cmul(Hc[l + (long)i * (m + 1)], yi);
-            rhs[l] = make_double2(rhs[l].x - t.x, rhs[l].y - t.y);
+        if (threadIdx.x == 0) {
+            const dfc d = dfc_load(*reinterpret_cast<const cdf *>(&Hc[i + (long)i * (m + 1)]));
+            const dfc sv = dfc_load(*reinterpret_cast<const cdf *>(&rhs[i]));
+            const df dd = dfc_abs2(d);
+            dfc yi{df{0.f, 0.f}, df{0.f, 0.f}};
+            if (dd.hi > 0.f) yi = dfc_scale(dfc_mul(sv, dfc_conj(d)), df_recip(dd));
+            const cdf yc = dfc_store(yi);
+            ysh = make_float4(yc.rh, yc.ih, yc.rl, yc.il);
+            ycoef[(long)c * (m + 1) + i] = ysh;
         }
-        if (threadIdx.x == 0) ycoef[(long)c * (m + 1) + i] = F64N::to_cdf(yi);
+        __syncthreads();
+        const dfc yi = dfc_load(*reinterpret_cast<const cdf *>(&ysh));
+        for (int l = threadIdx.x; l < i; l += blockDim.x) {
+            const dfc t = dfc_mul(dfc_load(*reinterpret_cast<const cdf *>(&Hc[l + (long)i * (m + 1)])), yi);
+            const dfc r = dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&rhs[l])), t);
+            *reinterpret_cast<cdf *>(&rhs[l]) = dfc_store(r);
+        }
         __syncthreads();
     }
 }
@@ -588,7 +586,9 @@ static int ensure_work(Plan *p, int m, int k, bool flex, bool host_io) {
     g->n = p->n;
     g->flex = flex;
     g->NB = kStepNB;
-    g->nblk = (int)((p->n + g->NB - 1) / g->NB);
+    g->nblk = (int)((p->n + g->NB - 1) / g->NB);               // update / scale / norm grid
+    const long nblk_dot = (p->n + kDotNE - 1) / kDotNE;
+    const long pstride = std::max((long)(m + 1) * nblk_dot, (long)g->nblk);
     const long n = p->n;
     size_t total = 0;
     bool ok = true;
@@ -603,14 +603,14 @@ static int ensure_work(Plan *p, int m, int k, bool flex, bool host_io) {
     alloc(&g->W, sizeof(float4) * k * n);
     alloc(&g->R, sizeof(float4) * k * n);
     alloc(&g->Vin, sizeof(float4) * k * n);
-    alloc(&g->H, sizeof(double2) * (size_t)k * (m + 1) * m);
-    alloc(&g->hacc, sizeof(double2) * (size_t)k * (m + 1));
-    alloc(&g->gv, sizeof(double2) * (size_t)k * (m + 1));
-    alloc(&g->sn, sizeof(double2) * (size_t)k * m);
+    alloc(&g->H, sizeof(float4) * (size_t)k * (m + 1) * m);
+    alloc(&g->hacc, sizeof(float4) * (size_t)k * (m + 1));
+    alloc(&g->gv, sizeof(float4) * (size_t)k * (m + 1));
+    alloc(&g->sn, sizeof(float4) * (size_t)k * m);
     alloc(&g->hco, sizeof(float4) * (size_t)k * (m + 1));
     alloc(&g->ycoef, sizeof(float4) * (size_t)k * (m + 1));
-    alloc(&g->part, sizeof(float4) * (size_t)k * (m + 1) * g->nblk);
-    alloc(&g->cs, sizeof(double) * (size_t)k * m);
+    alloc(&g->part, sizeof(float4) * (size_t)k * pstride);
+    alloc(&g->cs, sizeof(float2) * (size_t)k * m);
     alloc(&g->beta2, sizeof(double) * k);
     alloc(&g->vnorm, sizeof(double) * k);
     alloc(&g->inv_beta, sizeof(double) * k);
@@ -638,31 +638,30 @@ static int ensure_work(Plan *p, int m, int k, bool flex, bool host_io) {
 }
 
 // ||col||^2 of the k columns of x ([c][n] double-float) into g->beta2.
-static int norm2_cols(Plan *p, GmresWork *g, const float4 *x, int k, const int *active) {
-    dim3 grid(g->nblk, k);
-    dots_partial_kernel<<<grid, kVecThreads, g->NB * sizeof(float4), p->stream>>>(
-        x, 0, p->n, nullptr, 1, x, p->n, g->NB, g->nblk, g->m + 1, g->part, active);
-    count_launch(p);
-    dots_reduce_kernel<<<dim3(1, k), 32, 0, p->stream>>>(g->part, g->nblk, nullptr, 1, g->m + 1, nullptr, nullptr, 2,
-                                                          g->beta2, active);
-    count_launch(p);
+static int norm2_cols(Plan *p, GmresWork *g, const float4 *x, int k) {
+    const long pstride = std::max((long)(g->m + 1) * ((p->n + kDotNE - 1) / kDotNE), (long)g->nblk);
+    norm_partial_kernel<<<dim3(g->nblk, k), kVecThreads, 0, p->stream>>>(x, p->n, kStepNB, g->nblk, pstride,
+                                                                          g->part);
+    norm_final_kernel<<<k, 32, 0, p->stream>>>(g->part, g->nblk, pstride, g->beta2);
+    count_launch(p, 2);
     return check_cuda(p, cudaGetLastError(), "norm launch");
 }
 
 // One Arnoldi step for every active column, on p->stream (captured or not):
 // [block-Jacobi], the product, then the four fused Gram-Schmidt/Givens kernels.
-static int arnoldi_step(Plan *p, GmresWork *g, int inner) {
+static int arnoldi_step(Plan *p, GmresWork *g, int inner, int j) {
     const int m = g->m, k = g->k;
     const long n = p->n, bs_i = (long)k * n;
     cudaStream_t st = p->stream;
     int rc;
     const float4 *src = g->Vb;
     if (g->flex) {
-        rc = block_jacobi_run(p, g->Vb, FMT_CDF, n, g->Zb, FMT_CDF, n, k, g->d_j, bs_i, g->active);
+        rc = block_jacobi_run(p, g->Vb + (long)j * bs_i, FMT_CDF, n, g->Zb + (long)j * bs_i, FMT_CDF, n, k,
+                              nullptr, 0, g->active);
         if (rc != BTTB_OK) return rc;
         src = g->Zb;
     }
-    rc = matvec_run(p, src, FMT_CDF, n, g->W, FMT_CDF, n, k, inner, g->d_j, bs_i, nullptr, g->active);
+    rc = matvec_run(p, src + (long)j * bs_i, FMT_CDF, n, g->W, FMT_CDF, n, k, inner, nullptr, 0, nullptr, g->active);
     if (rc != BTTB_OK) return rc;
     StepArgs a{};
     a.Vb = g->Vb;
@@ -672,17 +671,18 @@ static int arnoldi_step(Plan *p, GmresWork *g, int inner) {
     a.bs_c = n;
     a.m = m;
     a.k = k;
-    a.nblk = g->nblk;
+    a.nblk_dot = (int)((n + kDotNE - 1) / kDotNE);
+    a.ich = (m + 1 + kDotIW - 1) / kDotIW;
+    a.nblk_vec = g->nblk;
     a.part = g->part;
+    a.pstride = std::max((long)(m + 1) * a.nblk_dot, (long)g->nblk);
     a.hco = g->hco;
     a.hacc = g->hacc;
-    a.beta2 = g->beta2;
     a.cnt_a = g->counters;
     a.cnt_b = g->counters + k;
     a.cnt_c = g->counters + 2 * k;
     a.cnt_d = g->counters + 3 * k;
     a.active = g->active;
-    a.d_j = g->d_j;
     a.d_any_step = g->d_any_step;
     a.H = g->H;
     a.gv = g->gv;
@@ -694,13 +694,22 @@ static int arnoldi_step(Plan *p, GmresWork *g, int inner) {
     a.mlimit = g->mlimit;
     a.target = g->target;
     a.err = p->d_err;
-    const dim3 grid(g->nblk, k);
+    const dim3 dgrid(a.nblk_dot, a.ich, k), vgrid(a.nblk_vec, k);
     const size_t hs_bytes = (size_t)(m + 1) * sizeof(float4);
-    step_dots_kernel<<<grid, kStepNB, 0, st>>>(a);
-    step_update_dots_kernel<<<grid, kStepNB, hs_bytes, st>>>(a);
-    step_update_norm_givens_kernel<<<grid, kStepNB, hs_bytes + (size_t)(3 * m + 2) * sizeof(double2), st>>>(a);
-    step_scale_advance_kernel<<<grid, kStepNB, 0, st>>>(a);
-    count_launch(p, 4);
+    const size_t upd_smem = hs_bytes + (size_t)(3 * m + 2) * sizeof(float4);
+    int tok;
+    for (int pass = 0; pass < 2; ++pass) {
+        tok = prof_begin(p, 3);
+        launch_pdl(step_dots_kernel, dgrid, dim3(kDotIW * 32), 0, st, a, pass, pass == 0 ? a.cnt_a : a.cnt_b, j);
+        prof_end(p, tok, 0.0);
+        tok = prof_begin(p, pass == 0 ? 4 : 5);
+        launch_pdl(step_update_kernel, vgrid, dim3(kStepNB), upd_smem, st, a, pass, j);
+        prof_end(p, tok, 0.0);
+    }
+    tok = prof_begin(p, 6);
+    launch_pdl(step_scale_kernel, vgrid, dim3(kStepNB), 0, st, a, j);
+    prof_end(p, tok, 0.0);
+    count_launch(p, 5);
     return check_cuda(p, cudaGetLastError(), "Arnoldi step launch");
 }
 
@@ -713,7 +722,7 @@ static int cycle_finish(Plan *p, GmresWork *g) {
                                                                                g->act_cycle);
     count_launch(p);
     update_kernel<<<dim3(vgrid, k), kVecThreads, (m + 1) * sizeof(float4), p->stream>>>(
-        g->flex ? g->Zb : g->Vb, bs_i, bs_c, nullptr, g->steps, g->ycoef, m + 1, g->X, n, 1.f, g->act_cycle);
+        g->flex ? g->Zb : g->Vb, bs_i, bs_c, g->steps, g->ycoef, m + 1, g->X, n, 1.f, g->act_cycle);
     count_launch(p);
     return check_cuda(p, cudaGetLastError(), "cycle finish launch");
 }
@@ -736,7 +745,7 @@ static int build_cycle_graph(Plan *p, GmresWork *g, int inner) {
     int rc = BTTB_OK;
     for (int step = 0; step < g->m && rc == BTTB_OK; ++step) {
         p->sink_step = step;
-        rc = arnoldi_step(p, g, inner);
+        rc = arnoldi_step(p, g, inner, step);
     }
     p->sink_step = g->m;
     if (rc == BTTB_OK) rc = cycle_finish(p, g);
@@ -802,7 +811,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
         fill_zero_kernel<<<1024, kVecThreads, 0, st>>>(g->X, (long)k * n);
         count_launch(p);
     }
-    if ((rc = norm2_cols(p, g, g->Vin, k, nullptr)) != BTTB_OK) return rc;
+    if ((rc = norm2_cols(p, g, g->Vin, k)) != BTTB_OK) return rc;
     std::vector<double> vn2(k), vnorm(k), b2(k), relres(k, 0.0), tgt(k);
     std::vector<int> status(k, BTTB_OK), total(k, 0), cycles(k, 0), act(k), mlim(k), stp(k, 0), bd(k, 0);
     e = cudaMemcpyAsync(vn2.data(), g->beta2, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
@@ -819,7 +828,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
         if ((rc = matvec_run(p, g->X, FMT_CDF, n, g->W, FMT_CDF, n, k, PREC_DF64)) != BTTB_OK) return rc;
         resid_kernel<<<1024, kVecThreads, 0, st>>>(g->Vin, g->W, g->R, (long)k * n);
         count_launch(p);
-        if ((rc = norm2_cols(p, g, g->R, k, nullptr)) != BTTB_OK) return rc;
+        if ((rc = norm2_cols(p, g, g->R, k)) != BTTB_OK) return rc;
         e = cudaMemcpyAsync(b2.data(), g->beta2, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&dev_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -862,9 +871,9 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
         cudaMemsetAsync(g->bdown, 0, sizeof(int) * k, st);
         cudaMemsetAsync(g->steps, 0, sizeof(int) * k, st);
         cudaMemsetAsync(g->d_any_step, 0, sizeof(int), st);
-        cycle_start_kernel<<<1, 256, 0, st>>>(g->beta2, g->gv, g->inv_beta, m, k, g->active, g->d_j);
+        cycle_start_kernel<<<1, 256, 0, st>>>(g->beta2, g->gv, g->inv_beta, m, k, g->active);
         count_launch(p);
-        scale_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(g->R, g->Vb, bs_i, bs_c, g->d_j, g->inv_beta, n,
+        scale_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(g->R, g->Vb, bs_i, bs_c, 0, g->inv_beta, n,
                                                              g->active);
         count_launch(p);
         if (use_graph) {
@@ -874,7 +883,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
             p->launches += g->launches_per_cycle;
         } else {
             for (int step = 0; step < m; ++step) {
-                if ((rc = arnoldi_step(p, g, inner)) != BTTB_OK) return rc;
+                if ((rc = arnoldi_step(p, g, inner, step)) != BTTB_OK) return rc;
                 e = cudaMemcpyAsync(g->h_any, g->d_any_step, sizeof(int), cudaMemcpyDeviceToHost, st);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(st);
                 if (e != cudaSuccess) return check_cuda(p, e, "Arnoldi step");

@@ -106,6 +106,24 @@ int prof_begin(Plan *p, int kid);
 void prof_end(Plan *p, int token, double bytes);
 inline void count_launch(Plan *p, int n = 1) { p->launches += n; }
 
+// Launch with the programmatic-stream-serialisation attribute: the kernel may be
+// scheduled while its predecessor drains; it waits on griddepcontrol.wait.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Thread-local error message helpers (bttb.cu).
 int set_error(Plan *p, int code, const std::string &msg);
 int check_cuda(Plan *p, cudaError_t e, const char *what);

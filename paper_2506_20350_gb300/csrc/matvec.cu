@@ -19,6 +19,7 @@
 
 #include "arith.cuh"
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace bttb {
 
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(kBjThreads) bj_apply_kernel(const float2 *rinv
     float2 *rsm = xs + (long)cpb * b;                         // b*b, row-major (when it fits)
     const float2 *rs = rinv_in_smem ? rsm : rinv;
     const int c = blockIdx.y;
+    pdl_wait();
     if (active && !active[c]) return;
     const int cell0 = blockIdx.x * cpb;
     const int nc = min(cpb, ncells - cell0);
@@ -130,9 +132,10 @@ static int bj_launch(Plan *p, const void *x, long ldx, void *z, long ldz, int nr
         if (e != cudaSuccess) return check_cuda(p, e, "block-Jacobi smem attribute");
     }
     dim3 grid((ncells + cpb - 1) / cpb, nrhs);
-    kern<<<grid, kBjThreads, smem, p->stream>>>(p->bj_inv, x, ldx, z, ldz, b, ncells, cpb, in_sel, in_sel_stride,
-                                                in_smem, active);
+    cudaError_t le = launch_pdl(kern, grid, dim3(kBjThreads), smem, p->stream, (const float2 *)p->bj_inv, x, ldx, z,
+                                ldz, b, ncells, cpb, in_sel, in_sel_stride, in_smem, active);
     count_launch(p);
+    if (le != cudaSuccess) return check_cuda(p, le, "block-Jacobi launch");
     return check_cuda(p, cudaGetLastError(), "block-Jacobi launch");
 }
 

@@ -351,7 +351,100 @@ static int launch_contract(Plan *p, const void *u, void *v, int k, const int *ac
     }
 }
 
+// ---------------------------------------------------------------------------
+// Many right-hand sides (binary32): the per-bin block product is a complex GEMM
+// V_k = G_k U_k with U_k of b x k.  CTA (tile, bin) stages the bin's spectrum
+// block (column-major, as stored) and a 64-column tile of U (column-major, as
+// stored) with two bulk copies, then thread (row p, column group g)
+// accumulates its row over the tile's columns of group g; the vector entry of
+// a column is a shared-memory broadcast.  Consecutive CTAs share a bin, so the
+// spectrum block is re-read from L2.
+// ---------------------------------------------------------------------------
+constexpr int kMultiTile = 64;
+
+template <int CPG>
+__global__ void __launch_bounds__(256) contract_multi_kernel(const float2 *g0, long gbs, const float2 *u, float2 *v,
+                                                              long ubs, int b, int k, int *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8);
+    float2 *gs = reinterpret_cast<float2 *>(smem + 128);
+    const uint32_t gbytes = round_up128((uint32_t)(b * b) * 8u);
+    float2 *us = reinterpret_cast<float2 *>(smem + 128 + gbytes);
+    const int bin = blockIdx.y, c0 = blockIdx.x * kMultiTile;
+    const int nc = min(kMultiTile, k - c0);
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t gb = round_up16((uint32_t)(b * b) * 8u);
+        const uint32_t ub = round_up16((uint32_t)(nc * b) * 8u);
+        mbar_arrive_expect_tx(bar, gb + ub);
+        bulk_g2s(gs, g0 + (long)bin * gbs, gb, bar, l2_policy_evict_last());
+        bulk_g2s(us, u + (long)bin * ubs + (long)c0 * b, ub, bar, l2_policy_evict_first());
+    }
+    const bool ok = mbar_wait_bounded(bar, 0, abort_flag);
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, DEVERR_TIMEOUT);
+            mbar_wait_drain(bar, 0);
+        }
+        return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rw = (b + 31) / 32;                 // row warps
+    const int cg = 8 / rw;                        // column groups
+    const int wr = warp % rw, wg = warp / rw;
+    const int p = wr * 32 + lane;
+    if (wg < cg && p < b) {
+        float2 acc[CPG];
+#pragma unroll
+        for (int j = 0; j < CPG; ++j) acc[j] = make_float2(0.f, 0.f);
+        const int cbase = wg * CPG;
+        for (int q = 0; q < b; ++q) {
+            const float2 gq = gs[q * b + p];
+#pragma unroll
+            for (int j = 0; j < CPG; ++j) {
+                const float2 x = us[(cbase + j) * b + q];     // broadcast within the warp
+                acc[j].x = fmaf(gq.x, x.x, acc[j].x);
+                acc[j].x = fmaf(-gq.y, x.y, acc[j].x);
+                acc[j].y = fmaf(gq.x, x.y, acc[j].y);
+                acc[j].y = fmaf(gq.y, x.x, acc[j].y);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CPG; ++j)
+            if (cbase + j < nc) v[(long)bin * ubs + (long)(c0 + cbase + j) * b + p] = acc[j];
+    }
+    pdl_trigger();
+}
+
+static int launch_contract_multi(Plan *p, const void *u, void *v, int k) {
+    const int b = p->b;
+    if (!p->ghat_hi) return set_error(p, BTTB_ERR_INVALID_ARG, "plan does not keep the binary32 spectrum");
+    const int rw = (b + 31) / 32, cg = 8 / rw;     // b <= 128: rw in 1..4, cg in {8, 4, 2}
+    const int cpg = kMultiTile / cg;                 // exactly covers the tile: 8, 16 or 32 columns
+    const size_t smem = 128 + round_up128((uint32_t)(b * b) * 8u) + round_up128((uint32_t)(kMultiTile * b) * 8u);
+    auto kern = cpg == 8 ? contract_multi_kernel<8> : (cpg == 16 ? contract_multi_kernel<16> : contract_multi_kernel<32>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return check_cuda(p, e, "multi-RHS smem attribute");
+    const dim3 grid((k + kMultiTile - 1) / kMultiTile, (unsigned)p->bins);
+    const int tok = prof_begin(p, BTTB_K_BLOCK_PRODUCT_PREC + BTTB_MV_FP32);
+    e = launch_pdl(kern, grid, dim3(256), smem, p->stream, (const float2 *)p->ghat_hi, p->gbs, (const float2 *)u,
+                   (float2 *)v, p->ubs, b, k, p->d_err);
+    count_launch(p);
+    prof_end(p, tok, (double)p->bins * ((double)b * b * 8 + 2.0 * k * b * 8));
+    if (e != cudaSuccess) return check_cuda(p, e, "multi-RHS launch");
+    return BTTB_OK;
+}
+
 int contract_launch(Plan *p, int prec, const void *u, void *v, int k, const int *active) {
+    // Many right-hand sides in binary32: a tiled per-bin GEMM instead of k/4 passes over the spectrum.
+    if (prec == PREC_F32 && k > 8 && p->b <= 128) return launch_contract_multi(p, u, v, k);
     switch (prec) {
         case PREC_F32: return launch_contract<F32>(p, u, v, k, active);
         case PREC_F64N: return launch_contract<F64N>(p, u, v, k, active);

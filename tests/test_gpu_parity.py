@@ -88,6 +88,43 @@ def test_product_random_generators(bt, nx, ny, b, k):
     _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP32).cpu().numpy(), ref, FP32_TOL, "binary32")
 
 
+@pytest.mark.parametrize("nx,ny,b,k", [
+    (5, 3, 7, 20),     # odd b, one 64-column tile (partial)
+    (4, 4, 12, 65),    # two tiles, the second with one column
+    (3, 3, 33, 130),   # three row warps' layout (rw = 2), three tiles
+    (3, 2, 96, 70),    # widest multi-RHS layout (rw = 3)
+])
+def test_multi_rhs_product_binary32(bt, nx, ny, b, k):
+    """k > 8 right-hand sides take the tiled per-bin GEMM (binary32)."""
+    gen = arrays.random_generator_blocks(nx, ny, b, seed=300 + b + k)
+    plan = bt.Plan(nx, ny, b, max_rhs=k)
+    plan.set_generators(gen)
+    x = _rand(np.random.default_rng(7), k, plan.n)
+    ref = oracle.matvec(gen, x.T).T
+    y = plan.matvec(_dev(x.astype(np.complex64)), prec=bt.BTTB_MV_FP32).cpu().numpy()
+    _check(y, ref, FP32_TOL, "multi-RHS binary32")
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64).cpu().numpy(), ref, FP64_TOL, "multi-RHS df64")
+
+
+def test_multi_rhs_solve_all_ports(bt):
+    """Every element's port excitation (the embedded-element-pattern workload), IR per column."""
+    nx, ny, b = 8, 6, 12
+    gen = arrays.generator_blocks(nx, ny, b, seed=31)
+    v = arrays.port_excitations(nx, ny, b).T.copy()          # 48 columns
+    plan = bt.Plan(nx, ny, b, max_rhs=v.shape[0])
+    plan.set_generators(gen)
+    sol, rc, res = plan.solve(_dev(v), tol=1e-8, restart=30, inner=bt.BTTB_MV_FP32)
+    assert rc == bt.BTTB_OK, bt.bttb_last_error()
+    rr = oracle.relres(gen, v.T, sol.cpu().numpy().T)
+    assert np.all(rr <= 1e-8), rr.max()
+    assert all(r.status == bt.BTTB_OK for r in res)
+    # each column agrees with its own single-column solve
+    for col in (0, 17, 47):
+        s1, _, _ = plan.solve(_dev(v[col:col + 1]), tol=1e-8, restart=30, inner=bt.BTTB_MV_FP32)
+        x1 = s1.cpu().numpy()[0]
+        assert np.linalg.norm(sol.cpu().numpy()[col] - x1) <= 1e-6 * np.linalg.norm(x1)
+
+
 def test_product_padded_leading_dimension_and_groups(bt):
     nx, ny, b, k = 6, 4, 10, 9          # 9 columns -> three passes of the block product
     gen = arrays.random_generator_blocks(nx, ny, b, seed=7)

@@ -231,6 +231,7 @@ def run_ours(args):
     I = torch.zeros_like(V)
     b64 = product_bytes(nx, ny, b, mx, my, "fp64")
     b32 = product_bytes(nx, ny, b, mx, my, "fp32")
+    torch.cuda.synchronize()          # inputs were built on the default stream; the plan runs on its own
 
     def solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_NONE, Vt=V, It=I, host_io=False, flags=0):
         with torch.cuda.stream(stream):
@@ -355,6 +356,7 @@ def run_ours(args):
         planm = bt.Plan(nx, ny, b, max_rhs=kall, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_FP32),
                         stream=stream)
         planm.set_generators(gen)
+        torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             planm.solve(vm, im, tol=tol, restart=restart, inner=bt.BTTB_MV_FP32, max_iters=2)   # graph + buffers
         torch.cuda.synchronize()
@@ -372,6 +374,46 @@ def run_ours(args):
                  "workspace_gb": planm.workspace_bytes() / 1e9}
         del vm, im
         planm.close()
+        torch.cuda.empty_cache()
+
+    # uneven batch: 64 independent arrays (nx, ny ~ U{8..40}, b in {24, 60, 96}, 1..16 port excitations)
+    uneven = None
+    if os.environ.get("BTTB_BENCH_SKIP_UNEVEN") is None:
+        specs = arrays.uneven_batch_specs()
+        batch = bt.Batch([(s.nx, s.ny, s.b, s.nrhs) for s in specs])
+        vs = []
+        for i, sp in enumerate(specs):
+            g = arrays.generator_blocks_torch(sp.nx, sp.ny, sp.b, sp.seed, device=dev)
+            batch.set_generators(i, g)
+            del g
+            cells = [(c % sp.nx, c // sp.nx) for c in range(sp.nrhs)]
+            vs.append(torch.from_numpy(arrays.port_excitations(sp.nx, sp.ny, sp.b, cells).T.copy()).to(dev))
+        widths = batch.autotune(reps=3)
+        batch.solve(vs, tol=tol, restart=restart, inner=bt.BTTB_MV_FP32, max_iters=2)     # graphs + buffers
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rcu, resu = batch.solve(vs, tol=tol, restart=restart, inner=bt.BTTB_MV_FP32)
+        torch.cuda.synchronize()
+        ut = time.perf_counter() - t0
+        # the same arrays one after another with plain FP64 GMRES
+        plans = [bt.bttb_batch_plan(batch.handle, i) for i in range(len(specs))]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(len(specs)):
+            out = torch.zeros_like(vs[i])
+            bt.bttb_gmres_solve(plans[i], vs[i], out, vs[i].shape[0], vs[i].shape[1],
+                                bt.gmres_opts(tol=tol, restart=restart, inner=bt.BTTB_MV_FP64))
+        torch.cuda.synchronize()
+        st = time.perf_counter() - t0
+        its = [r.iters for r in resu]
+        uneven = {"arrays": len(specs), "columns": len(resu), "solve_ms": ut * 1e3,
+                  "status_ok": sum(r.status == bt.BTTB_OK for r in resu), "iters_max": max(its),
+                  "iters_mean": float(np.mean(its)), "relres_true_max": max(r.relres_true for r in resu),
+                  "sequential_fp64_ms": st * 1e3, "speedup_vs_sequential_fp64": st / ut,
+                  "fft_chunk_widths": {str(w): widths.count(w) for w in sorted(set(widths))},
+                  "unknowns_total": int(sum(s.nx * s.ny * s.b * s.nrhs for s in specs))}
+        del vs
+        batch.close()
         torch.cuda.empty_cache()
 
     peak, peak_kind = measured_peaks()
@@ -417,6 +459,7 @@ def run_ours(args):
         "matvec": mv,
         "step_breakdown_host_driven": breakdown,
         "multi_rhs": multi,
+        "uneven_batch": uneven,
     }
     print(json.dumps(line), flush=True)
     barrier(world)

@@ -102,8 +102,10 @@ int bttb_plan_grid(bttb_plan plan, int *mx, int *my);
  *                p the observer basis (row), q the source basis (column).
  *   dtype      : storage type of gen.
  *   gen_is_host: nonzero if gen is a host pointer.
- * Synchronises the plan's stream.  The caller may free gen on return.
- * Returns BTTB_ERR_NONFINITE if gen holds NaN/Inf.
+ * Synchronises the plan's stream; with a device pointer it first waits for all
+ * work already queued on the device (gen may come from any stream).  The
+ * caller may free gen on return.  Returns BTTB_ERR_NONFINITE if gen holds
+ * NaN/Inf.
  */
 int bttb_set_generators(bttb_plan plan, const void *gen, bttb_dtype dtype, int gen_is_host);
 
@@ -225,6 +227,42 @@ int bttb_profile_read(bttb_plan plan, int which, bttb_kernel_stats *out);
  */
 int bttb_matvec_noalloc(int nx, int ny, int b, const void *gen, const void *x, void *y, int nrhs, long ld,
                         void *cuda_stream);
+
+/*
+ * Batches of independent arrays of uneven sizes.  Array i has nx[i] x ny[i]
+ * cells, b[i] bases per cell and up to nrhs[i] right-hand sides; it gets its
+ * own plan (created with prec_mask) on its own CUDA stream owned by the batch;
+ * the streams are blocking streams, ordered after work on the legacy default
+ * stream, and a batch solve first waits for all work queued on the device.
+ * A batch solve runs every array's GMRES concurrently: one host thread per
+ * array drives that array's captured restart cycles on its stream, so the GPU
+ * overlaps the arrays' kernels.  The paper solves one array at a time; the
+ * batch is this library's extension for many arrays.
+ */
+typedef struct bttb_batch_s *bttb_batch;
+int bttb_batch_create(bttb_batch *out, int count, const int *nx, const int *ny, const int *b, const int *nrhs,
+                      unsigned prec_mask);
+/* The plan of array `index` (owned by the batch; do not destroy it). */
+int bttb_batch_plan(bttb_batch batch, int index, bttb_plan *out);
+/* bttb_set_generators for array `index`. */
+int bttb_batch_set_generators(bttb_batch batch, int index, const void *gen, bttb_dtype dtype, int gen_is_host);
+/*
+ * Autotuner: for every distinct FFT grid and block size (mx, my, b) in the
+ * batch, time `reps` binary32 products with each FFT batch-chunk width in
+ * {2, 4, 8, 16, 32} on the array's stream and keep the fastest for every array
+ * of that shape.  chosen_out (host, count entries, may be NULL) receives the
+ * width per array.  Needs the generators of the arrays to tune.
+ */
+int bttb_batch_autotune(bttb_batch batch, int reps, int *chosen_out);
+/*
+ * Solve every array: V[i], I[i] are device complex128 multi-vectors of array i
+ * with nrhs[i] columns and column stride ld[i] (opts->host_io makes them host
+ * pointers).  out_host receives sum(nrhs) results, array by array.  Returns the
+ * worst status over the arrays; bttb_last_error names the first failing array.
+ */
+int bttb_batch_gmres_solve(bttb_batch batch, const void *const *V, void *const *I, const long *ld,
+                           const bttb_gmres_opts *opts, bttb_col_result *out_host);
+int bttb_batch_destroy(bttb_batch batch);
 
 /* Bytes of device memory the plan holds (spectrum copies and workspace). */
 size_t bttb_plan_workspace_bytes(bttb_plan plan);

@@ -31,6 +31,8 @@ BTTB_K_BLOCK_PRODUCT, BTTB_K_FFT, BTTB_K_ALL, BTTB_K_BLOCK_PRODUCT_PREC = 0, 1, 
 EXPORTS = ("bttb_plan_create", "bttb_plan_grid", "bttb_set_generators", "bttb_matvec",
            "bttb_gmres_solve", "bttb_block_jacobi_apply", "bttb_get_spectrum_bin",
            "bttb_profile", "bttb_profile_read", "bttb_matvec_noalloc",
+           "bttb_batch_create", "bttb_batch_plan", "bttb_batch_set_generators", "bttb_batch_autotune",
+           "bttb_batch_gmres_solve", "bttb_batch_destroy",
            "bttb_plan_workspace_bytes", "bttb_plan_destroy", "bttb_last_error")
 
 
@@ -79,6 +81,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bttb_profile.argtypes = [vp, ci]
     lib.bttb_profile_read.argtypes = [vp, ci, ctypes.POINTER(KernelStats)]
     lib.bttb_matvec_noalloc.argtypes = [ci, ci, ci, vp, vp, vp, ci, cl, vp]
+    pi = ctypes.POINTER(ci)
+    lib.bttb_batch_create.argtypes = [ctypes.POINTER(vp), ci, pi, pi, pi, pi, ctypes.c_uint]
+    lib.bttb_batch_plan.argtypes = [vp, ci, ctypes.POINTER(vp)]
+    lib.bttb_batch_set_generators.argtypes = [vp, ci, vp, ci, ci]
+    lib.bttb_batch_autotune.argtypes = [vp, ci, pi]
+    lib.bttb_batch_gmres_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(cl),
+                                           ctypes.POINTER(GmresOpts), ctypes.POINTER(ColResult)]
+    lib.bttb_batch_destroy.argtypes = [vp]
     lib.bttb_plan_workspace_bytes.argtypes = [vp]
     lib.bttb_plan_workspace_bytes.restype = ctypes.c_size_t
     lib.bttb_plan_destroy.argtypes = [vp]
@@ -179,6 +189,50 @@ def bttb_matvec_noalloc(nx: int, ny: int, b: int, gen, x, y, nrhs: int, ld: int,
                                               _stream_handle(stream)))
 
 
+def _ints(vals):
+    return (ctypes.c_int * len(vals))(*[int(v) for v in vals])
+
+
+def bttb_batch_create(nx, ny, b, nrhs, prec_mask: int = 0):
+    h = ctypes.c_void_p()
+    _check(load_library().bttb_batch_create(ctypes.byref(h), len(nx), _ints(nx), _ints(ny), _ints(b), _ints(nrhs),
+                                            prec_mask))
+    return h
+
+
+def bttb_batch_plan(batch, index: int):
+    h = ctypes.c_void_p()
+    _check(load_library().bttb_batch_plan(batch, index, ctypes.byref(h)))
+    return h
+
+
+def bttb_batch_set_generators(batch, index: int, gen) -> None:
+    bttb_set_generators(bttb_batch_plan(batch, index), gen)
+
+
+def bttb_batch_autotune(batch, count: int, reps: int = 5) -> list[int]:
+    out = (ctypes.c_int * count)()
+    _check(load_library().bttb_batch_autotune(batch, reps, out))
+    return list(out)
+
+
+def bttb_batch_gmres_solve(batch, Vs, Is, lds, opts: GmresOpts) -> tuple[int, list[ColResult]]:
+    n = len(Vs)
+    total = sum(v.shape[0] for v in Vs)
+    res = (ColResult * total)()
+    vp = (ctypes.c_void_p * n)(*[_ptr(v) for v in Vs])
+    ip = (ctypes.c_void_p * n)(*[_ptr(i) for i in Is])
+    ld = (ctypes.c_long * n)(*lds)
+    rc = load_library().bttb_batch_gmres_solve(batch, vp, ip, ld, ctypes.byref(opts), res)
+    _check(rc, None, soft_ok=True)
+    return rc, list(res)
+
+
+def bttb_batch_destroy(batch) -> None:
+    if batch:
+        _check(load_library().bttb_batch_destroy(batch))
+
+
 def bttb_plan_workspace_bytes(plan) -> int:
     return int(load_library().bttb_plan_workspace_bytes(plan))
 
@@ -203,6 +257,42 @@ def gmres_opts(tol=1e-8, restart=50, max_iters=5000, pc=BTTB_PC_NONE, inner=BTTB
         o.history = history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         o.history_len = history.shape[0]
     return o
+
+
+class Batch:
+    """Owner of a bttb_batch: independent arrays of uneven sizes solved concurrently."""
+
+    def __init__(self, specs, prec_mask=0):
+        """specs: sequence of (nx, ny, b, nrhs)."""
+        self.specs = [tuple(int(v) for v in s) for s in specs]
+        nx, ny, b, k = zip(*self.specs)
+        self.handle = bttb_batch_create(nx, ny, b, k, prec_mask)
+
+    def set_generators(self, index, gen):
+        bttb_batch_set_generators(self.handle, index, gen)
+
+    def autotune(self, reps=5):
+        return bttb_batch_autotune(self.handle, len(self.specs), reps)
+
+    def solve(self, Vs, Is=None, **kw):
+        """Vs[i]: (nrhs_i, N_i) complex128 device tensors; returns (Is, rc, results)."""
+        import torch
+        if Is is None:
+            Is = [torch.zeros_like(v) for v in Vs]
+        lds = [v.shape[1] for v in Vs]
+        rc, res = bttb_batch_gmres_solve(self.handle, Vs, Is, lds, gmres_opts(**kw))
+        return Is, rc, res
+
+    def close(self):
+        if getattr(self, "handle", None):
+            bttb_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

@@ -1,0 +1,175 @@
+// Batches of independent arrays of uneven sizes (nx, ny, b, number of
+// right-hand sides).  Every array has its own plan on its own CUDA stream;
+// a batch solve runs the arrays' restarted-GMRES drivers concurrently (one
+// host thread per array), so the GPU executes the arrays' captured cycle
+// graphs side by side.  An autotuner picks, per distinct (mx, my, b), the FFT
+// batch-chunk width by timing binary32 products on the plan's stream.
+#include <algorithm>
+#include <map>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "arith.cuh"
+#include "internal.h"
+
+struct bttb_batch_s {
+    int count = 0;
+    std::vector<bttb_plan> plans;
+    std::vector<cudaStream_t> streams;
+    std::vector<int> nrhs;
+};
+
+using namespace bttb;
+
+static int batch_release(bttb_batch b) {
+    if (!b) return BTTB_OK;
+    for (bttb_plan p : b->plans) bttb_plan_destroy(p);
+    for (cudaStream_t s : b->streams)
+        if (s) cudaStreamDestroy(s);
+    delete b;
+    return BTTB_OK;
+}
+
+extern "C" {
+
+int bttb_batch_create(bttb_batch *out, int count, const int *nx, const int *ny, const int *b, const int *nrhs,
+                      unsigned prec_mask) {
+    if (!out) return set_error(nullptr, BTTB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || count > 4096 || !nx || !ny || !b || !nrhs)
+        return set_error(nullptr, BTTB_ERR_INVALID_ARG, "need 1 <= count <= 4096 and size arrays");
+    bttb_batch h = new (std::nothrow) bttb_batch_s();
+    if (!h) return set_error(nullptr, BTTB_ERR_OOM, "host allocation failed");
+    h->count = count;
+    h->plans.assign(count, nullptr);
+    h->streams.assign(count, nullptr);
+    h->nrhs.assign(nrhs, nrhs + count);
+    for (int i = 0; i < count; ++i) {
+        // Blocking streams: work the caller queued on the legacy default stream (where
+        // frameworks usually build inputs) completes before the array's kernels run.
+        cudaError_t e = cudaStreamCreateWithFlags(&h->streams[i], cudaStreamDefault);
+        if (e != cudaSuccess) {
+            batch_release(h);
+            return check_cuda(nullptr, e, "batch stream");
+        }
+        const int rc = bttb_plan_create(&h->plans[i], nx[i], ny[i], b[i], nrhs[i], prec_mask, h->streams[i]);
+        if (rc != BTTB_OK) {
+            batch_release(h);
+            return rc;
+        }
+    }
+    *out = h;
+    return BTTB_OK;
+}
+
+int bttb_batch_plan(bttb_batch batch, int index, bttb_plan *out) {
+    if (!batch || !out || index < 0 || index >= batch->count)
+        return set_error(nullptr, BTTB_ERR_INVALID_ARG, "bad batch, index or out");
+    *out = batch->plans[index];
+    return BTTB_OK;
+}
+
+int bttb_batch_set_generators(bttb_batch batch, int index, const void *gen, bttb_dtype dtype, int gen_is_host) {
+    if (!batch || index < 0 || index >= batch->count)
+        return set_error(nullptr, BTTB_ERR_INVALID_ARG, "bad batch or index");
+    return bttb_set_generators(batch->plans[index], gen, dtype, gen_is_host);
+}
+
+int bttb_batch_autotune(bttb_batch batch, int reps, int *chosen_out) {
+    if (!batch) return set_error(nullptr, BTTB_ERR_INVALID_ARG, "batch is NULL");
+    if (reps < 1) reps = 1;
+    std::map<std::tuple<int, int, int>, int> best;
+    const int candidates[5] = {2, 4, 8, 16, 32};
+    for (int i = 0; i < batch->count; ++i) {
+        Plan &p = batch->plans[i]->p;
+        if (!p.have_gen || !p.ghat_hi) continue;
+        const auto key = std::make_tuple(p.mx, p.my, p.b);
+        if (best.count(key)) continue;
+        void *x = nullptr, *y = nullptr;
+        cudaError_t e = cudaMalloc(&x, p.n * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc(&y, p.n * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, p.n * sizeof(float2), p.stream);
+        if (e != cudaSuccess) {
+            cudaFree(x);
+            cudaFree(y);
+            return check_cuda(&p, e, "autotune buffers");
+        }
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best_ms = 1e30f;
+        int best_p = p.fft_pmax;
+        for (int cand : candidates) {
+            p.fft_pmax = cand;
+            matvec_run(&p, x, FMT_C64, p.n, y, FMT_C64, p.n, 1, PREC_F32);        // warm
+            cudaEventRecord(e0, p.stream);
+            for (int r = 0; r < reps; ++r) matvec_run(&p, x, FMT_C64, p.n, y, FMT_C64, p.n, 1, PREC_F32);
+            cudaEventRecord(e1, p.stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_p = cand;
+            }
+        }
+        p.fft_pmax = best_p;
+        best[key] = best_p;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(x);
+        cudaFree(y);
+    }
+    for (int i = 0; i < batch->count; ++i) {
+        Plan &p = batch->plans[i]->p;
+        const auto it = best.find(std::make_tuple(p.mx, p.my, p.b));
+        if (it != best.end()) p.fft_pmax = it->second;
+        if (chosen_out) chosen_out[i] = p.fft_pmax;
+    }
+    return BTTB_OK;
+}
+
+int bttb_batch_gmres_solve(bttb_batch batch, const void *const *V, void *const *I, const long *ld,
+                           const bttb_gmres_opts *opts, bttb_col_result *out_host) {
+    if (!batch || !V || !I || !ld || !opts) return set_error(nullptr, BTTB_ERR_INVALID_ARG, "NULL argument");
+    const int n = batch->count;
+    std::vector<int> rcs(n, BTTB_OK);
+    std::vector<std::string> msgs(n);
+    std::vector<long> off(n + 1, 0);
+    for (int i = 0; i < n; ++i) off[i + 1] = off[i] + batch->nrhs[i];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    // Inputs may come from any stream: let everything already queued finish first.
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return check_cuda(nullptr, e, "batch solve: device synchronise");
+    std::vector<std::thread> th;
+    th.reserve(n);
+    for (int i = 0; i < n; ++i) {
+        th.emplace_back([&, i]() {
+            cudaSetDevice(dev);
+            bttb_gmres_opts o = *opts;
+            o.history = nullptr;
+            o.history_len = 0;
+            rcs[i] = bttb_gmres_solve(batch->plans[i], V[i], I[i], batch->nrhs[i], ld[i], &o,
+                                      out_host ? out_host + off[i] : nullptr);
+            if (rcs[i] < 0) msgs[i] = bttb_last_error(batch->plans[i]);
+        });
+    }
+    for (auto &t : th) t.join();
+    int worst = BTTB_OK;
+    for (int i = 0; i < n; ++i) {
+        if (rcs[i] < 0 && (worst >= 0 || rcs[i] < worst)) {
+            worst = rcs[i];
+            set_error(nullptr, rcs[i], "array " + std::to_string(i) + ": " + msgs[i]);
+        } else if (worst >= 0 && rcs[i] > worst) {
+            worst = rcs[i];
+        }
+    }
+    return worst;
+}
+
+int bttb_batch_destroy(bttb_batch batch) { return batch_release(batch); }
+
+}  // extern "C"

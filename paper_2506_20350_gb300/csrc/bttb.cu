@@ -10,10 +10,6 @@
 #include "internal.h"
 #include "ptx.cuh"
 
-struct bttb_plan_s {
-    bttb::Plan p;
-};
-
 namespace bttb {
 
 static thread_local std::string g_last_error = "no error";
@@ -186,6 +182,11 @@ int bttb_set_generators(bttb_plan plan, const void *gen, bttb_dtype dtype, int g
     if (dtype != BTTB_C64 && dtype != BTTB_C128) return set_error(nullptr, BTTB_ERR_INVALID_ARG, "bad dtype");
     Plan &p = plan->p;
     p.have_gen = false;
+    if (!gen_is_host) {
+        // A device generator buffer may have been produced on any stream.
+        cudaError_t e0 = cudaDeviceSynchronize();
+        if (e0 != cudaSuccess) return check_cuda(&p, e0, "set_generators: device synchronise");
+    }
     cudaMemsetAsync(p.d_err, 0, sizeof(int), p.stream);
     int rc = spectrum_compute(&p, gen, dtype, gen_is_host);
     if (rc != BTTB_OK) return rc;

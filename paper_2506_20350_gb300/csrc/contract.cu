@@ -297,7 +297,7 @@ static int launch_contract_impl(Plan *p, const void *u, void *v, int k, const in
     const size_t smem = 256 + (size_t)a.st_bytes * kConsumerWarps * kWarpStages;
 
     auto kern = contract_kernel<A, KC, R, VEC>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
     if (e != cudaSuccess) return check_cuda(p, e, "contract smem attribute");
     const long warps_needed = a.nbins;
     int grid = (int)((warps_needed + kConsumerWarps - 1) / kConsumerWarps);
@@ -430,7 +430,7 @@ static int launch_contract_multi(Plan *p, const void *u, void *v, int k) {
     const int cpg = kMultiTile / cg;                 // exactly covers the tile: 8, 16 or 32 columns
     const size_t smem = 128 + round_up128((uint32_t)(b * b) * 8u) + round_up128((uint32_t)(kMultiTile * b) * 8u);
     auto kern = cpg == 8 ? contract_multi_kernel<8> : (cpg == 16 ? contract_multi_kernel<16> : contract_multi_kernel<32>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
     if (e != cudaSuccess) return check_cuda(p, e, "multi-RHS smem attribute");
     const dim3 grid((k + kMultiTile - 1) / kMultiTile, (unsigned)p->bins);
     const int tok = prof_begin(p, BTTB_K_BLOCK_PRODUCT_PREC + BTTB_MV_FP32);

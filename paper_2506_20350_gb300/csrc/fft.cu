@@ -251,7 +251,7 @@ static int launch_one(Plan *p, const FftPass &a) {
     size_t smem = ((size_t)a.M + 8 + 2 * (size_t)a.M * a.P) * sizeof(C);
     auto kern = fft_pass_kernel<A, INF, OUTF, INV>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
         if (e != cudaSuccess) return check_cuda(p, e, "fft smem attribute");
     }
     dim3 grid(a.O, (a.pdim + a.P - 1) / a.P, a.ncols);
@@ -284,9 +284,9 @@ static int dispatch_fmt(Plan *p, const FftPass &a, int infmt, int outfmt, bool i
     }
 }
 
-static int choose_P(int M, int pdim, size_t elem) {
+static int choose_P(int M, int pdim, size_t elem, int pmax) {
     int P = 1;
-    while (P < 16 && P < pdim) P <<= 1;
+    while (P < pmax && P < pdim) P <<= 1;
     while (P > 1 && ((size_t)M + 8 + 2 * (size_t)M * P) * elem > 96 * 1024) P >>= 1;
     return P;
 }
@@ -297,7 +297,7 @@ int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool in
     a.nst = f.nst;
     for (int i = 0; i < f.nst; ++i) a.radix[i] = f.radix[i];
     size_t elem = prec == PREC_F32 ? 8 : 16;
-    a.P = choose_P(a.M, a.pdim, elem);
+    a.P = choose_P(a.M, a.pdim, elem, p->fft_pmax);
     a.log2P = 0;
     while ((1 << a.log2P) < a.P) ++a.log2P;
     if (a.O <= 0 || a.ncols <= 0 || a.pdim <= 0) return BTTB_OK;

@@ -62,6 +62,7 @@ struct Plan {
     int dev = 0, nsm = 0;
     size_t smem_optin = 0;
     FftPlan fx, fy;
+    int fft_pmax = 16;            // widest batch chunk of an FFT pass (power of two; autotuned in batches)
 
     // Spectrum copies, scaled by 1/(mx*my).  Bin k holds its b x b block
     // column-major (entry (p, q) at q*b + p) at offset k*gbs elements.
@@ -153,3 +154,8 @@ int gmres_solve(Plan *p, const void *V, void *I, int nrhs, long ld, const bttb_g
 void gmres_free(Plan *p);
 
 }  // namespace bttb
+
+// The opaque handle of the C ABI wraps a plan.
+struct bttb_plan_s {
+    bttb::Plan p;
+};

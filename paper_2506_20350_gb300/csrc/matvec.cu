@@ -128,7 +128,7 @@ static int bj_launch(Plan *p, const void *x, long ldx, void *z, long ldz, int nr
     const size_t smem = xs_bytes + (in_smem ? r_bytes : 0);
     auto kern = bj_apply_kernel<INF, OUTF>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
         if (e != cudaSuccess) return check_cuda(p, e, "block-Jacobi smem attribute");
     }
     dim3 grid((ncells + cpb - 1) / cpb, nrhs);

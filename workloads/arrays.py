@@ -58,6 +58,23 @@ def generator_blocks(nx: int, ny: int, b: int, seed: int) -> np.ndarray:
     return gen
 
 
+def generator_blocks_torch(nx: int, ny: int, b: int, seed: int, device="cuda"):
+    """The synthetic generators of ``generator_blocks`` synthesised with torch
+    (binary64) on ``device``: same centroids, same formula, for large batches
+    where numpy synthesis would dominate.  Returns a complex128 tensor."""
+    import torch
+    c = torch.from_numpy(centroids(b, seed)).to(device)
+    ii = torch.arange(-(nx - 1), nx, dtype=torch.float64, device=device)
+    jj = torch.arange(-(ny - 1), ny, dtype=torch.float64, device=device)
+    dx = c[None, None, :, 0, None] + CELL * ii[None, :, None, None] - c[None, None, None, :, 0]
+    dy = c[None, None, :, 1, None] + CELL * jj[:, None, None, None] - c[None, None, None, :, 1]
+    r = torch.clamp(torch.sqrt(dx * dx + dy * dy), min=R_MIN)
+    gen = torch.polar(1.0 / (4.0 * np.pi * r), -K0 * r)
+    idx = torch.arange(b, device=device)
+    gen[ny - 1, nx - 1, idx, idx] += SELF_TERM
+    return gen.contiguous()
+
+
 def random_generator_blocks(nx: int, ny: int, b: int, seed: int,
                             diag_shift: complex = 0.0) -> np.ndarray:
     """Non-reciprocal complex Gaussian generators (T[-i,-j] != T[i,j]^T).

@@ -61,7 +61,9 @@ typedef enum {
 
 typedef enum {
     BTTB_PC_NONE = 0,
-    BTTB_PC_BLOCK_JACOBI = 1 /* P_K of Sec. III-B: LU of T[0,0] applied to every cell */
+    BTTB_PC_BLOCK_JACOBI = 1, /* P_K of Sec. III-B: LU of T[0,0] applied to every cell */
+    BTTB_PC_LEARNED = 2       /* P_K^{-1} r + f(r), f the learned Fourier-domain
+                                 correction attached with bttb_plan_set_learned      */
 } bttb_precond;
 
 enum {
@@ -263,6 +265,58 @@ int bttb_batch_autotune(bttb_batch batch, int reps, int *chosen_out);
 int bttb_batch_gmres_solve(bttb_batch batch, const void *const *V, void *const *I, const long *ld,
                            const bttb_gmres_opts *opts, bttb_col_result *out_host);
 int bttb_batch_destroy(bttb_batch batch);
+
+/*
+ * Learned Fourier-domain correction to the block-Jacobi preconditioner P_K of
+ * Sec. III-B.  The paper stops at P_K and the row preconditioner P_Z and notes
+ * (Sec. V) that coupling more neighbouring elements may help; this object adds
+ * a trained correction that sees the whole array through the 2-level DFT of
+ * App. B.  For a column r:
+ *   r^   = FFT2(pad r)/s, s = sqrt(mx*my)          (Eq. (xc2), App. B)
+ *   h_k  = B_k r^_k                 per bin k, B_k complex rank x b
+ *   g    = h + conv3(relu(conv2(relu(conv1(h)))))  3x3 circular convolutions over
+ *          the (ky, kx) grid; h read as 2*rank real channels (2r = Re, 2r+1 = Im);
+ *          conv1: 2*rank -> channels, conv2: channels -> channels,
+ *          conv3: channels -> 2*rank, each with a bias
+ *   z^_k = A_k g_k                  per bin k, A_k complex b x rank
+ *   f(r) = crop(IFFT2_unnormalised(z^))/s
+ *   M(r) = P_K^{-1} r + f(r)
+ * Parameters are one binary32 vector (bttb_learned_param_count entries) in the
+ * order B [bin][r][p] (re, im), A [bin][p][r] (re, im), W1 [co][ci][3][3], c1,
+ * W2, c2, W3, c3; bin = ky*mx + kx.  Every kernel reads a bfloat16 copy of
+ * them and accumulates in binary32.  Training minimises
+ *   L = (1/n) sum_c ||M(r_c) - e_c||^2 / ||e_c||^2
+ * over pairs (r_c, e_c) with Z e_c = r_c, by Adam on the binary32 master copy.
+ * The object belongs to one plan (which needs the FP32 spectrum and a regular
+ * T[0,0]); destroy it before the plan.
+ *   rank in {8, 16, 24, 32}; channels in {16, 32, 64}; 1 <= max_cols <= 256
+ *   (largest ncols of any later call, and largest nrhs of a BTTB_PC_LEARNED
+ *   solve).  Weights are initialised from `seed` (small A, B: f starts near 0).
+ */
+typedef struct bttb_learned_s *bttb_learned;
+int bttb_learned_create(bttb_learned *out, bttb_plan plan, int rank, int channels, int max_cols,
+                        unsigned long long seed);
+/* Number of binary32 parameters. */
+long bttb_learned_param_count(bttb_learned l);
+/* Copy the binary32 parameters to (to_host != 0) or from a HOST array;
+ * synchronises the plan's stream.  Loading refreshes the bfloat16 copy. */
+int bttb_learned_params(bttb_learned l, float *host, int to_host);
+/* z[:, c] = M(r[:, c]) for c < ncols: device multi-vectors of type dtype,
+ * column stride ld >= N.  Stream-ordered, no synchronisation. */
+int bttb_learned_apply(bttb_learned l, const void *r, void *z, int ncols, long ld, bttb_dtype dtype);
+/* Loss and gradient for pairs (r, e): device complex64 multi-vectors with
+ * column stride ld.  grad_host (HOST, param_count floats, may be NULL)
+ * receives dL/dtheta (complex parameters: dL/dRe, dL/dIm); loss_host (may be
+ * NULL) the loss.  Either output synchronises the plan's stream. */
+int bttb_learned_gradients(bttb_learned l, const void *r, const void *e, int ncols, long ld, float *grad_host,
+                           double *loss_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * minibatch (r, e), laid out as for bttb_learned_gradients. */
+int bttb_learned_train_step(bttb_learned l, const void *r, const void *e, int ncols, long ld, float lr,
+                            double *loss_host);
+/* Attach (or, with l == NULL, detach) the object used by BTTB_PC_LEARNED. */
+int bttb_plan_set_learned(bttb_plan plan, bttb_learned l);
+int bttb_learned_destroy(bttb_learned l);
 
 /* Bytes of device memory the plan holds (spectrum copies and workspace). */
 size_t bttb_plan_workspace_bytes(bttb_plan plan);

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libbttb.so")
 
 BTTB_C64, BTTB_C128 = 0, 1
 BTTB_MV_FP64, BTTB_MV_FP32, BTTB_MV_FP64_NATIVE = 0, 1, 2
-BTTB_PC_NONE, BTTB_PC_BLOCK_JACOBI = 0, 1
+BTTB_PC_NONE, BTTB_PC_BLOCK_JACOBI, BTTB_PC_LEARNED = 0, 1, 2
 BTTB_GMRES_NO_GRAPH = 1
 BTTB_OK, BTTB_NOT_CONVERGED, BTTB_BREAKDOWN = 0, 1, 2
 BTTB_ERR_INVALID_ARG, BTTB_ERR_CUDA, BTTB_ERR_OOM = -1, -2, -3
@@ -33,6 +33,8 @@ EXPORTS = ("bttb_plan_create", "bttb_plan_grid", "bttb_set_generators", "bttb_ma
            "bttb_profile", "bttb_profile_read", "bttb_matvec_noalloc",
            "bttb_batch_create", "bttb_batch_plan", "bttb_batch_set_generators", "bttb_batch_autotune",
            "bttb_batch_gmres_solve", "bttb_batch_destroy",
+           "bttb_learned_create", "bttb_learned_param_count", "bttb_learned_params", "bttb_learned_apply",
+           "bttb_learned_gradients", "bttb_learned_train_step", "bttb_plan_set_learned", "bttb_learned_destroy",
            "bttb_plan_workspace_bytes", "bttb_plan_destroy", "bttb_last_error")
 
 
@@ -89,14 +91,23 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bttb_batch_gmres_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(cl),
                                            ctypes.POINTER(GmresOpts), ctypes.POINTER(ColResult)]
     lib.bttb_batch_destroy.argtypes = [vp]
+    lib.bttb_learned_create.argtypes = [ctypes.POINTER(vp), vp, ci, ci, ci, ctypes.c_ulonglong]
+    lib.bttb_learned_param_count.argtypes = [vp]
+    lib.bttb_learned_params.argtypes = [vp, vp, ci]
+    lib.bttb_learned_apply.argtypes = [vp, vp, vp, ci, cl, ci]
+    lib.bttb_learned_gradients.argtypes = [vp, vp, vp, ci, cl, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.bttb_learned_train_step.argtypes = [vp, vp, vp, ci, cl, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    lib.bttb_plan_set_learned.argtypes = [vp, vp]
+    lib.bttb_learned_destroy.argtypes = [vp]
     lib.bttb_plan_workspace_bytes.argtypes = [vp]
     lib.bttb_plan_workspace_bytes.restype = ctypes.c_size_t
     lib.bttb_plan_destroy.argtypes = [vp]
     lib.bttb_last_error.argtypes = [vp]
     lib.bttb_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("bttb_plan_workspace_bytes", "bttb_last_error"):
+        if name not in ("bttb_plan_workspace_bytes", "bttb_last_error", "bttb_learned_param_count"):
             getattr(lib, name).restype = ci
+    lib.bttb_learned_param_count.restype = cl
     _lib = lib
     return lib
 
@@ -233,6 +244,48 @@ def bttb_batch_destroy(batch) -> None:
         _check(load_library().bttb_batch_destroy(batch))
 
 
+def bttb_learned_create(plan, rank: int = 16, channels: int = 64, max_cols: int = 64, seed: int = 0):
+    h = ctypes.c_void_p()
+    _check(load_library().bttb_learned_create(ctypes.byref(h), plan, rank, channels, max_cols, seed), plan)
+    return h
+
+
+def bttb_learned_param_count(learned) -> int:
+    return int(load_library().bttb_learned_param_count(learned))
+
+
+def bttb_learned_params(learned, host_array, to_host: bool) -> None:
+    """host_array: C-contiguous float32 numpy array of param_count entries."""
+    _check(load_library().bttb_learned_params(learned, _ptr(host_array), int(bool(to_host))))
+
+
+def bttb_learned_apply(learned, r, z, ncols: int, ld: int, dtype: int) -> None:
+    _check(load_library().bttb_learned_apply(learned, _ptr(r), _ptr(z), ncols, ld, dtype))
+
+
+def bttb_learned_gradients(learned, r, e, ncols: int, ld: int, grad_host=None) -> float:
+    loss = ctypes.c_double(0.0)
+    g = _ptr(grad_host) if grad_host is not None else None
+    _check(load_library().bttb_learned_gradients(learned, _ptr(r), _ptr(e), ncols, ld, g, ctypes.byref(loss)))
+    return loss.value
+
+
+def bttb_learned_train_step(learned, r, e, ncols: int, ld: int, lr: float, want_loss: bool = True):
+    loss = ctypes.c_double(0.0)
+    _check(load_library().bttb_learned_train_step(learned, _ptr(r), _ptr(e), ncols, ld, lr,
+                                                  ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def bttb_plan_set_learned(plan, learned) -> None:
+    _check(load_library().bttb_plan_set_learned(plan, learned), plan)
+
+
+def bttb_learned_destroy(learned) -> None:
+    if learned:
+        _check(load_library().bttb_learned_destroy(learned))
+
+
 def bttb_plan_workspace_bytes(plan) -> int:
     return int(load_library().bttb_plan_workspace_bytes(plan))
 
@@ -344,6 +397,94 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             bttb_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Learned:
+    """Owner of a bttb_learned object (the learned correction of a plan).
+
+    Parameters as a dict of numpy arrays with the shapes of the C layout:
+    B (bins, rank, b) complex, A (bins, b, rank) complex, W1 (ch, 2*rank, 3, 3),
+    c1 (ch,), W2 (ch, ch, 3, 3), c2 (ch,), W3 (2*rank, ch, 3, 3), c3 (2*rank,).
+    """
+
+    def __init__(self, plan: "Plan", rank=16, channels=64, max_cols=64, seed=0):
+        self.plan, self.rank, self.channels, self.max_cols = plan, rank, channels, max_cols
+        self.bins = plan.mx * plan.my
+        self.handle = bttb_learned_create(plan.handle, rank, channels, max_cols, seed)
+        self.count = bttb_learned_param_count(self.handle)
+
+    def _shapes(self):
+        R, C, b, bins = self.rank, self.channels, self.plan.b, self.bins
+        return [("B", (bins, R, b), True), ("A", (bins, b, R), True), ("W1", (C, 2 * R, 3, 3), False),
+                ("c1", (C,), False), ("W2", (C, C, 3, 3), False), ("c2", (C,), False),
+                ("W3", (2 * R, C, 3, 3), False), ("c3", (2 * R,), False)]
+
+    def unflatten(self, flat):
+        import numpy as np
+        out, o = {}, 0
+        for name, shape, cplx in self._shapes():
+            cnt = int(np.prod(shape)) * (2 if cplx else 1)
+            v = flat[o:o + cnt]
+            o += cnt
+            out[name] = (v[0::2] + 1j * v[1::2]).reshape(shape) if cplx else v.reshape(shape).copy()
+        return out
+
+    def flatten(self, params):
+        import numpy as np
+        parts = []
+        for name, shape, cplx in self._shapes():
+            v = np.asarray(params[name]).reshape(-1)
+            if cplx:
+                w = np.empty(2 * v.size, dtype=np.float32)
+                w[0::2], w[1::2] = v.real, v.imag
+                parts.append(w)
+            else:
+                parts.append(v.astype(np.float32))
+        return np.ascontiguousarray(np.concatenate(parts))
+
+    def get_params(self):
+        import numpy as np
+        flat = np.empty(self.count, dtype=np.float32)
+        bttb_learned_params(self.handle, flat, True)
+        return self.unflatten(flat)
+
+    def set_params(self, params):
+        flat = self.flatten(params)
+        assert flat.size == self.count
+        bttb_learned_params(self.handle, flat, False)
+
+    def apply(self, r):
+        """M(r) for (k, N) device columns (complex64 or complex128)."""
+        import torch
+        rs = r.reshape(-1, self.plan.n)
+        z = torch.empty_like(rs)
+        dt = BTTB_C128 if rs.dtype == torch.complex128 else BTTB_C64
+        bttb_learned_apply(self.handle, rs, z, rs.shape[0], self.plan.n, dt)
+        return z.reshape(r.shape)
+
+    def gradients(self, r, e):
+        """(loss, grads dict) for complex64 device pairs (k, N)."""
+        import numpy as np
+        g = np.empty(self.count, dtype=np.float32)
+        loss = bttb_learned_gradients(self.handle, r, e, r.shape[0], self.plan.n, g)
+        return loss, self.unflatten(g)
+
+    def train_step(self, r, e, lr=1e-3, want_loss=True):
+        return bttb_learned_train_step(self.handle, r, e, r.shape[0], self.plan.n, lr, want_loss)
+
+    def attach(self):
+        bttb_plan_set_learned(self.plan.handle, self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            bttb_learned_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -254,10 +254,13 @@ int bttb_gmres_solve(bttb_plan plan, const void *V, void *I, int nrhs, long ld, 
     if (!V || !I || ld < p.n) return set_error(&p, BTTB_ERR_INVALID_ARG, "bad V, I or ld");
     if (!(opts->tol > 0.0) || opts->restart < 1 || opts->restart > 200 || opts->max_iters < 0)
         return set_error(&p, BTTB_ERR_INVALID_ARG, "need tol > 0, 1 <= restart <= 200, max_iters >= 0");
-    if (opts->pc != BTTB_PC_NONE && opts->pc != BTTB_PC_BLOCK_JACOBI)
+    if (opts->pc != BTTB_PC_NONE && opts->pc != BTTB_PC_BLOCK_JACOBI && opts->pc != BTTB_PC_LEARNED)
         return set_error(&p, BTTB_ERR_INVALID_ARG, "unknown preconditioner");
-    if (opts->pc == BTTB_PC_BLOCK_JACOBI && !p.bj_ready)
+    if (opts->pc != BTTB_PC_NONE && !p.bj_ready)
         return set_error(&p, BTTB_ERR_SINGULAR, "T[0,0] is singular: no block-Jacobi preconditioner");
+    if (opts->pc == BTTB_PC_LEARNED && (!p.learned || nrhs > learned_max_cols(p.learned)))
+        return set_error(&p, BTTB_ERR_INVALID_ARG,
+                         "BTTB_PC_LEARNED needs an attached learned object with max_cols >= nrhs");
     if (!prec_enabled(p, opts->inner)) return set_error(&p, BTTB_ERR_INVALID_ARG, "inner precision not enabled");
     if (!prec_enabled(p, BTTB_MV_FP64))
         return set_error(&p, BTTB_ERR_INVALID_ARG, "GMRES needs the FP64 (double-float) spectrum for its residuals");

@@ -26,7 +26,8 @@ namespace bttb {
 struct GmresWork {
     int m = 0, k = 0;
     long n = 0;
-    bool flex = false;
+    bool flex = false;            // Zb allocated
+    int pc = BTTB_PC_NONE;        // preconditioner of the current solve
     int NB = 0, nblk = 0;
     float4 *X = nullptr, *Vb = nullptr, *Zb = nullptr, *W = nullptr, *R = nullptr, *Vin = nullptr;
     // Hessenberg [c][(m+1)*m] column-major, accumulated CGS coefficients [c][m+1],
@@ -47,6 +48,7 @@ struct GmresWork {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t cycle_exec = nullptr;
     int graph_inner = -1;
+    int graph_pc = -1;
     bool graph_prof = false;
     long launches_per_cycle = 0;
     std::vector<Plan::GraphRec> grecs;
@@ -655,9 +657,13 @@ static int arnoldi_step(Plan *p, GmresWork *g, int inner, int j) {
     cudaStream_t st = p->stream;
     int rc;
     const float4 *src = g->Vb;
-    if (g->flex) {
+    if (g->pc == BTTB_PC_BLOCK_JACOBI) {
         rc = block_jacobi_run(p, g->Vb + (long)j * bs_i, FMT_CDF, n, g->Zb + (long)j * bs_i, FMT_CDF, n, k,
                               nullptr, 0, g->active);
+        if (rc != BTTB_OK) return rc;
+        src = g->Zb;
+    } else if (g->pc == BTTB_PC_LEARNED) {
+        rc = learned_apply_run(p, g->Vb + (long)j * bs_i, FMT_CDF, n, g->Zb + (long)j * bs_i, FMT_CDF, n, k);
         if (rc != BTTB_OK) return rc;
         src = g->Zb;
     }
@@ -722,7 +728,7 @@ static int cycle_finish(Plan *p, GmresWork *g) {
                                                                                g->act_cycle);
     count_launch(p);
     update_kernel<<<dim3(vgrid, k), kVecThreads, (m + 1) * sizeof(float4), p->stream>>>(
-        g->flex ? g->Zb : g->Vb, bs_i, bs_c, g->steps, g->ycoef, m + 1, g->X, n, 1.f, g->act_cycle);
+        g->pc != BTTB_PC_NONE ? g->Zb : g->Vb, bs_i, bs_c, g->steps, g->ycoef, m + 1, g->X, n, 1.f, g->act_cycle);
     count_launch(p);
     return check_cuda(p, cudaGetLastError(), "cycle finish launch");
 }
@@ -764,6 +770,7 @@ static int build_cycle_graph(Plan *p, GmresWork *g, int inner) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return check_cuda(p, e, "graph instantiate");
     g->graph_inner = inner;
+    g->graph_pc = g->pc;
     g->graph_prof = p->prof;
     return BTTB_OK;
 }
@@ -771,12 +778,13 @@ static int build_cycle_graph(Plan *p, GmresWork *g, int inner) {
 int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmres_opts *o,
                 bttb_col_result *out) {
     const int m = o->restart;
-    const bool flex = o->pc == BTTB_PC_BLOCK_JACOBI;
+    const bool flex = o->pc != BTTB_PC_NONE;
     const int inner = o->inner;
     const bool use_graph = !(o->flags & BTTB_GMRES_NO_GRAPH);
     int rc = ensure_work(p, m, k, flex, o->host_io != 0);
     if (rc != BTTB_OK) return rc;
     GmresWork *g = p->gw;
+    g->pc = o->pc;
     const long n = p->n;
     const long bs_i = (long)k * n, bs_c = n;    // basis layout [i][c][n]
     cudaStream_t st = p->stream;
@@ -877,7 +885,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
                                                              g->active);
         count_launch(p);
         if (use_graph) {
-            if (!g->cycle_exec || g->graph_inner != inner || g->graph_prof != p->prof)
+            if (!g->cycle_exec || g->graph_inner != inner || g->graph_pc != g->pc || g->graph_prof != p->prof)
                 if ((rc = build_cycle_graph(p, g, inner)) != BTTB_OK) return rc;
             if ((e = cudaGraphLaunch(g->cycle_exec, st)) != cudaSuccess) return check_cuda(p, e, "graph launch");
             p->launches += g->launches_per_cycle;

@@ -52,6 +52,7 @@ struct FftPass {
 enum Prec { PREC_DF64 = BTTB_MV_FP64, PREC_F32 = BTTB_MV_FP32, PREC_F64N = BTTB_MV_FP64_NATIVE };
 
 struct GmresWork;
+struct Learned;
 
 struct Plan {
     int nx = 0, ny = 0, b = 0, mx = 0, my = 0, max_rhs = 0;
@@ -82,6 +83,7 @@ struct Plan {
     size_t ws_bytes = 0;
 
     GmresWork *gw = nullptr;
+    Learned *learned = nullptr;   // attached learned preconditioner (learned.cu), not owned
     int *d_err = nullptr;         // device error word
     size_t bytes_held = 0;
 
@@ -152,6 +154,10 @@ int block_jacobi_setup(Plan *p, const double2 *t00_host);
 int gmres_solve(Plan *p, const void *V, void *I, int nrhs, long ld, const bttb_gmres_opts *o,
                 bttb_col_result *out);
 void gmres_free(Plan *p);
+
+// learned.cu: z = P_K^{-1} x + f(x) with the plan's attached learned correction.
+int learned_apply_run(Plan *p, const void *x, int xfmt, long ldx, void *z, int zfmt, long ldz, int nc);
+int learned_max_cols(const Learned *L);
 
 }  // namespace bttb
 

@@ -289,7 +289,7 @@ int bttb_batch_destroy(bttb_batch batch);
  * over pairs (r_c, e_c) with Z e_c = r_c, by Adam on the binary32 master copy.
  * The object belongs to one plan (which needs the FP32 spectrum and a regular
  * T[0,0]); destroy it before the plan.
- *   rank in {8, 16, 24, 32}; channels in {16, 32, 64}; 1 <= max_cols <= 256
+ *   rank in {8, 16, 32}; channels in {16, 32, 64}; 1 <= max_cols <= 256
  *   (largest ncols of any later call, and largest nrhs of a BTTB_PC_LEARNED
  *   solve).  Weights are initialised from `seed` (small A, B: f starts near 0).
  */

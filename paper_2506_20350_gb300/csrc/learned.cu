@@ -47,47 +47,67 @@ __device__ __forceinline__ float bf(const __nv_bfloat16 *w, long i) { return __b
 constexpr int kEncCols = 16;
 
 // hc[c][bin][2r, 2r+1] = scale * sum_p B[bin][r][p] rh[bin][c][p]
+// Shared layouts keep a warp's reads on distinct banks: B as [p][r] with row
+// stride R+1, the staged columns with row stride b+1.
 __global__ void __launch_bounds__(256) lp_encode_kernel(const __nv_bfloat16 *Bw, const float2 *rh, long ubs, float *hc,
                                                         int nc, int b, int R, long bins, float scale) {
     extern __shared__ __align__(16) float2 sm2[];
-    float2 *Bs = sm2;                    // R*b
-    float2 *xs = sm2 + (long)R * b;      // kEncCols*b
+    const int bst = R + 1, xst = b + 1;
+    float2 *Bs = sm2;                    // b*bst
+    float2 *xs = sm2 + (long)b * bst;    // kEncCols*xst
     const long bin = blockIdx.x;
     const int c0 = blockIdx.y * kEncCols;
     const int ncb = min(kEncCols, nc - c0);
     for (int i = threadIdx.x; i < R * b; i += blockDim.x) {
         const long o = (bin * R * b + i) * 2;
-        Bs[i] = make_float2(bf(Bw, o), bf(Bw, o + 1));
+        const int r = i / b, q = i - r * b;
+        Bs[q * bst + r] = make_float2(bf(Bw, o), bf(Bw, o + 1));
     }
-    for (int i = threadIdx.x; i < ncb * b; i += blockDim.x) xs[i] = rh[bin * ubs + (long)(c0 + i / b) * b + i % b];
+    for (int i = threadIdx.x; i < ncb * b; i += blockDim.x) {
+        const int cl = i / b;
+        xs[cl * xst + (i - cl * b)] = rh[bin * ubs + (long)c0 * b + i];
+    }
     __syncthreads();
     for (int t = threadIdx.x; t < ncb * R; t += blockDim.x) {
         const int cl = t / R, r = t % R;
-        float ar = 0.f, ai = 0.f;
-        for (int q = 0; q < b; ++q) {
-            const float2 w = Bs[r * b + q], x = xs[cl * b + q];
+        float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+        const float2 *xr = xs + cl * xst;
+        int q = 0;
+        for (; q + 1 < b; q += 2) {
+            const float2 w = Bs[q * bst + r], x = xr[q];
+            const float2 w2 = Bs[(q + 1) * bst + r], x2 = xr[q + 1];
+            ar = fmaf(w.x, x.x, fmaf(-w.y, x.y, ar));
+            ai = fmaf(w.x, x.y, fmaf(w.y, x.x, ai));
+            br = fmaf(w2.x, x2.x, fmaf(-w2.y, x2.y, br));
+            bi = fmaf(w2.x, x2.y, fmaf(w2.y, x2.x, bi));
+        }
+        if (q < b) {
+            const float2 w = Bs[q * bst + r], x = xr[q];
             ar = fmaf(w.x, x.x, fmaf(-w.y, x.y, ar));
             ai = fmaf(w.x, x.y, fmaf(w.y, x.x, ai));
         }
         float *o = hc + ((long)(c0 + cl) * bins + bin) * 2 * R + 2 * r;
-        o[0] = ar * scale;
-        o[1] = ai * scale;
+        o[0] = (ar + br) * scale;
+        o[1] = (ai + bi) * scale;
     }
 }
 
-// zh[bin][c][p] = scale * sum_r A[bin][p][r] g[c][bin][r], g = hc + a3 (as complex)
+// zh[bin][c][p] = scale * sum_r A[bin][p][r] g[c][bin][r], g = hc + a3 (as complex).
+// A staged as [r][p] with row stride b+1.
 __global__ void __launch_bounds__(256) lp_decode_kernel(const __nv_bfloat16 *Aw, const float *hc, const float *a3,
                                                         float2 *zh, long ubs, int nc, int b, int R, long bins,
                                                         float scale) {
     extern __shared__ __align__(16) float2 sm2[];
-    float2 *As = sm2;                    // b*R
-    float2 *gs = sm2 + (long)b * R;      // kEncCols*R
+    const int ast = b + 1;
+    float2 *As = sm2;                    // R*ast
+    float2 *gs = sm2 + (long)R * ast;    // kEncCols*R
     const long bin = blockIdx.x;
     const int c0 = blockIdx.y * kEncCols;
     const int ncb = min(kEncCols, nc - c0);
     for (int i = threadIdx.x; i < b * R; i += blockDim.x) {
         const long o = (bin * b * R + i) * 2;
-        As[i] = make_float2(bf(Aw, o), bf(Aw, o + 1));
+        const int pr = i / R, r = i - pr * R;
+        As[r * ast + pr] = make_float2(bf(Aw, o), bf(Aw, o + 1));
     }
     for (int i = threadIdx.x; i < ncb * R; i += blockDim.x) {
         const long o = ((long)(c0 + i / R) * bins + bin) * 2 * R + 2 * (i % R);
@@ -98,7 +118,7 @@ __global__ void __launch_bounds__(256) lp_decode_kernel(const __nv_bfloat16 *Aw,
         const int cl = t / b, pr = t % b;
         float ar = 0.f, ai = 0.f;
         for (int r = 0; r < R; ++r) {
-            const float2 w = As[pr * R + r], g = gs[cl * R + r];
+            const float2 w = As[r * ast + pr], g = gs[cl * R + r];
             ar = fmaf(w.x, g.x, fmaf(-w.y, g.y, ar));
             ai = fmaf(w.x, g.y, fmaf(w.y, g.x, ai));
         }
@@ -118,101 +138,238 @@ __global__ void lp_wt_kernel(const __nv_bfloat16 *W, float *Wt, int Co, int Ci, 
     }
 }
 
-// out[n][co] = (bias ? bias[co] : 0) + sum_{ci, tap} Wt[(ci*9+tap)*Co + co] * in(neighbour(n, tap))[ci],
-// in = relu(X) when relu_in; the result is multiplied by (mask[n][co] > 0) when mask is given.
+// Circular 3x3 convolution over the (ky, kx) grid of every column:
+//   out[n][co] = bias[co] + sum_{tap, ci} Wt[(ci*9 + tap)*CO + co] * in(nb(n, tap))[ci],
+// nb(n, tap) the neighbour (y + tap/3 - 1, x + tap%3 - 1) mod (my, mx) of position n
+// in its column, in = relu(X) when relu_in; the result is zeroed where
+// mask[n][co] <= 0 when a mask is given (the ReLU derivative of the backward pass).
+// Persistent CTAs of 256 threads hold the CI*9*CO weights in shared memory and
+// walk tiles of TP = 4096/CO positions.  For each tile a table of the 9 x TP
+// neighbour rows is built once (double-buffered: the next tile's table is
+// built while the current one is used); per tap the TP neighbour rows (CI
+// floats each) are copied in with 16-byte cp.async, double-buffered across
+// taps.  A thread owns 4 positions (strided by TP/4) x 4 output channels.
+template <int CO>
 __global__ void __launch_bounds__(256) lp_conv_kernel(const float *X, int Ci, int relu_in, const float *Wt,
-                                                      const float *bias, float *out, int Co, long npos, int my,
-                                                      int mx, long bins, const float *mask) {
-    extern __shared__ __align__(16) float wsm[];        // Ci*9*Co
-    for (int i = threadIdx.x; i < Ci * 9 * Co; i += blockDim.x) wsm[i] = Wt[i];
-    __syncthreads();
-    const int P = blockDim.x / Co;
-    const int pl = threadIdx.x / Co, co = threadIdx.x % Co;
-    if (pl >= P) return;
-    for (long n = (long)blockIdx.x * P + pl; n < npos; n += (long)gridDim.x * P) {
-        const long c = n / bins, pos = n % bins;
-        const int y = (int)(pos / mx), x = (int)(pos % mx);
-        float acc = bias ? bias[co] : 0.f;
-#pragma unroll 1
-        for (int tap = 0; tap < 9; ++tap) {
-            const int yy = (y + tap / 3 - 1 + my) % my, xx = (x + tap % 3 - 1 + mx) % mx;
-            const float *xr = X + (c * bins + (long)yy * mx + xx) * Ci;
-            const float *wr = wsm + (long)tap * Co + co;
-#pragma unroll 8
-            for (int ci = 0; ci < Ci; ++ci) {
-                float v = xr[ci];
-                if (relu_in) v = fmaxf(v, 0.f);
-                acc = fmaf(wr[(long)ci * 9 * Co], v, acc);
+                                                      const float *bias, float *out, long npos, int my, int mx,
+                                                      long bins, const float *mask) {
+    constexpr int TP = 4096 / CO;
+    constexpr int CG = CO / 4;
+    constexpr int PS = TP / 4;                 // position stride of a thread's 4 positions
+    extern __shared__ __align__(16) float lsm[];
+    float *ws = lsm;                           // Ci*9*CO
+    const int xstride = Ci + 4;                // floats per staged row (keeps 16-byte alignment)
+    float *xs0 = ws + (long)Ci * 9 * CO;       // 2 buffers of TP*xstride
+    int *nbr0 = reinterpret_cast<int *>(xs0 + 2 * TP * xstride);   // 2 tables of 9*TP rows
+    const long ntiles = (npos + TP - 1) / TP;
+    if ((long)blockIdx.x >= ntiles) return;
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(Wt);
+        float4 *dst = reinterpret_cast<float4 *>(ws);
+        for (int i = threadIdx.x; i < Ci * 9 * CO / 4; i += blockDim.x) dst[i] = src[i];
+    }
+    // neighbour rows of tile t (row = c*bins + yy*mx + xx, -1 past the end)
+    auto build_table = [&](long t, int *tab) {
+        for (int pl = threadIdx.x; pl < TP; pl += blockDim.x) {
+            const long n = t * TP + pl;
+            if (n < npos) {
+                const long c = n / bins;
+                const int pos = (int)(n - c * bins);
+                const int y = pos / mx, x = pos - y * mx;
+                const int ym = y == 0 ? my - 1 : y - 1, yp = y == my - 1 ? 0 : y + 1;
+                const int xm = x == 0 ? mx - 1 : x - 1, xp = x == mx - 1 ? 0 : x + 1;
+                const int base = (int)(c * bins);
+                const int ys[3] = {ym, y, yp}, xs3[3] = {xm, x, xp};
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) tab[tap * TP + pl] = base + ys[tap / 3] * mx + xs3[tap % 3];
+            } else {
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) tab[tap * TP + pl] = -1;
             }
         }
-        if (mask && !(mask[n * Co + co] > 0.f)) acc = 0.f;
-        out[n * Co + co] = acc;
+    };
+    const int cshift = 31 - __clz(Ci / 4);     // Ci/4 is a power of two
+    const int cmask = Ci / 4 - 1;
+    auto stage = [&](const int *tab, int tap, float *dst) {
+        for (int i = threadIdx.x; i < TP * (Ci / 4); i += blockDim.x) {
+            const int pl = i >> cshift, ch = i & cmask;
+            const int row = tab[tap * TP + pl];
+            float *d = dst + pl * xstride + ch * 4;
+            if (row >= 0) cp_async16(d, X + (long)row * Ci + ch * 4);
+            else *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cp_async_commit();
+    };
+    const int cg = threadIdx.x % CG, pg = threadIdx.x / CG;
+    float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (bias) bv = *reinterpret_cast<const float4 *>(bias + cg * 4);
+    int buf = 0, tb = 0;
+    build_table(blockIdx.x, nbr0);
+    __syncthreads();
+    stage(nbr0, 0, xs0);
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long tn = t + gridDim.x;
+        int *tab = nbr0 + tb * 9 * TP, *tabn = nbr0 + (tb ^ 1) * 9 * TP;
+        if (tn < ntiles) build_table(tn, tabn);       // read first at tap 8, after two barriers
+        float acc[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[j][k] = 0.f;
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+            if (tap < 8) stage(tab, tap + 1, xs0 + (buf ^ 1) * TP * xstride);
+            else if (tn < ntiles) stage(tabn, 0, xs0 + (buf ^ 1) * TP * xstride);
+            else cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            const float *xr = xs0 + buf * TP * xstride + pg * xstride;
+            const float *wr = ws + tap * CO + cg * 4;
+#pragma unroll 2
+            for (int ci = 0; ci < Ci; ci += 4) {
+                float4 xv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    xv[j] = *reinterpret_cast<const float4 *>(xr + j * PS * xstride + ci);
+                    if (relu_in) {
+                        xv[j].x = fmaxf(xv[j].x, 0.f);
+                        xv[j].y = fmaxf(xv[j].y, 0.f);
+                        xv[j].z = fmaxf(xv[j].z, 0.f);
+                        xv[j].w = fmaxf(xv[j].w, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const float4 w = *reinterpret_cast<const float4 *>(wr + (long)(ci + cc) * 9 * CO);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float v = cc == 0 ? xv[j].x : cc == 1 ? xv[j].y : cc == 2 ? xv[j].z : xv[j].w;
+                        acc[j][0] = fmaf(v, w.x, acc[j][0]);
+                        acc[j][1] = fmaf(v, w.y, acc[j][1]);
+                        acc[j][2] = fmaf(v, w.z, acc[j][2]);
+                        acc[j][3] = fmaf(v, w.w, acc[j][3]);
+                    }
+                }
+            }
+            __syncthreads();
+            buf ^= 1;
+        }
+        tb ^= 1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long n = t * TP + pg + j * PS;
+            if (n >= npos) continue;
+            float4 o = make_float4(acc[j][0] + bv.x, acc[j][1] + bv.y, acc[j][2] + bv.z, acc[j][3] + bv.w);
+            if (mask) {
+                const float4 mv = *reinterpret_cast<const float4 *>(mask + n * CO + cg * 4);
+                if (!(mv.x > 0.f)) o.x = 0.f;
+                if (!(mv.y > 0.f)) o.y = 0.f;
+                if (!(mv.z > 0.f)) o.z = 0.f;
+                if (!(mv.w > 0.f)) o.w = 0.f;
+            }
+            *reinterpret_cast<float4 *>(out + n * CO + cg * 4) = o;
+        }
     }
+    cp_async_wait<0>();
 }
 
-// Partial weight gradients of one convolution over a chunk of positions:
-// wpart[chunk][co][k], k = ci*9 + tap for k < Ci*9 and k = Ci*9 for the bias:
-//   sum_n dA[n][co] * in(neighbour(n, tap))[ci]   (in = relu(X) when relu_in).
-constexpr int kWgChunk = 512;
-constexpr int kWgStep = 32;
+// Partial weight gradients of one convolution over a chunk of positions, one tap
+// per CTA row (blockIdx.y):
+//   wpart[chunk][co][ci*9 + tap] = sum_{n in chunk} dA[n][co] * in(nb(n, tap))[ci]
+//   wpart[chunk][co][Ci*9]       = sum_{n in chunk} dA[n][co]        (bias, tap 0 only)
+// in = relu(X) when relu_in.  Ci*Co/16 threads, each owning 4 output x 4 input
+// channels; tiles of kWgTile positions (input rows of the tap and dA rows) are
+// copied in with cp.async, double-buffered.
+constexpr int kWgTile = 64;
+constexpr int kWgChunks = 96;       // position chunks (x 9 taps) of a weight-gradient launch
 
 __global__ void __launch_bounds__(256) lp_wgrad_kernel(const float *X, int Ci, int relu_in, const float *dA, int Co,
-                                                       long npos, int my, int mx, long bins, float *wpart) {
-    __shared__ float das[kWgStep][64];
-    __shared__ float xcs[kWgStep][64];
-    const int K = Ci * 9 + 1;
-    const int chunk = blockIdx.x, ktile = blockIdx.y * 64;
-    const int TCO = Co / 16;                          // co per thread (Co = 64 -> 4, 32 -> 2)
-    const int tco = threadIdx.x / 16, tk = threadIdx.x % 16;
+                                                       long npos, long chunk_len, int my, int mx, long bins,
+                                                       float *wpart) {
+    extern __shared__ __align__(16) float gsm[];
+    const int xs_stride = Ci + 4, ds_stride = Co + 4;
+    const int buf_floats = kWgTile * (xs_stride + ds_stride);
+    const int chunk = blockIdx.x, tap = blockIdx.y;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int cig = threadIdx.x % (Ci / 4), cog = threadIdx.x / (Ci / 4);
+    const long n0 = (long)chunk * chunk_len;
+    const long n1 = min(npos, n0 + chunk_len);
+    const int xch = Ci / 4, dch = Co / 4;
+    auto stage = [&](long nb, float *dst) {
+        float *xs = dst, *ds = dst + kWgTile * xs_stride;
+        for (int i = threadIdx.x; i < kWgTile * (xch + dch); i += blockDim.x) {
+            const int pl = i / (xch + dch), q = i - pl * (xch + dch);
+            const long n = nb + pl;
+            float *d = q < xch ? xs + pl * xs_stride + q * 4 : ds + pl * ds_stride + (q - xch) * 4;
+            if (n < n1) {
+                if (q < xch) {
+                    const long c = n / bins;
+                    const int pos = (int)(n - c * bins);
+                    const int y = pos / mx, x = pos - y * mx;
+                    int yy = y + dy, xx = x + dx;
+                    yy += yy < 0 ? my : 0;
+                    yy -= yy >= my ? my : 0;
+                    xx += xx < 0 ? mx : 0;
+                    xx -= xx >= mx ? mx : 0;
+                    cp_async16(d, X + (c * bins + (long)yy * mx + xx) * Ci + q * 4);
+                } else {
+                    cp_async16(d, dA + n * Co + (q - xch) * 4);
+                }
+            } else {
+                *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        cp_async_commit();
+    };
     float acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[a][k] = 0.f;
-    const long n0 = (long)chunk * kWgChunk;
-    for (int s = 0; s < kWgChunk; s += kWgStep) {
+    float bacc[4] = {0.f, 0.f, 0.f, 0.f};
+    const bool do_bias = tap == 0 && cig == 0;
+    int buf = 0;
+    if (n0 < n1) stage(n0, gsm);
+    for (long nb = n0; nb < n1; nb += kWgTile) {
+        if (nb + kWgTile < n1) stage(nb + kWgTile, gsm + (buf ^ 1) * buf_floats);
+        else cp_async_commit();
+        cp_async_wait<1>();
         __syncthreads();
-        for (int i = threadIdx.x; i < kWgStep * 64; i += blockDim.x) {
-            const int np = i / 64, j = i % 64;
-            const long n = n0 + s + np;
-            // dA rows (Co values, zero beyond)
-            das[np][j] = (n < npos && j < Co) ? dA[n * Co + j] : 0.f;
-            // columns of the unfolded input for this k tile
-            const int k = ktile + j;
-            float v = 0.f;
-            if (n < npos && k < K) {
-                if (k == Ci * 9) {
-                    v = 1.f;
-                } else {
-                    const int ci = k / 9, tap = k % 9;
-                    const long c = n / bins, pos = n % bins;
-                    const int y = (int)(pos / mx), x = (int)(pos % mx);
-                    const int yy = (y + tap / 3 - 1 + my) % my, xx = (x + tap % 3 - 1 + mx) % mx;
-                    v = X[(c * bins + (long)yy * mx + xx) * Ci + ci];
-                    if (relu_in) v = fmaxf(v, 0.f);
-                }
+        const float *xs = gsm + buf * buf_floats;
+        const float *ds = xs + kWgTile * xs_stride;
+#pragma unroll 4
+        for (int pl = 0; pl < kWgTile; ++pl) {
+            float4 xv = *reinterpret_cast<const float4 *>(xs + pl * xs_stride + cig * 4);
+            const float4 dv = *reinterpret_cast<const float4 *>(ds + pl * ds_stride + cog * 4);
+            if (relu_in) {
+                xv.x = fmaxf(xv.x, 0.f);
+                xv.y = fmaxf(xv.y, 0.f);
+                xv.z = fmaxf(xv.z, 0.f);
+                xv.w = fmaxf(xv.w, 0.f);
             }
-            xcs[np][j] = v;
-        }
-        __syncthreads();
-        for (int np = 0; np < kWgStep; ++np) {
+            const float d4[4] = {dv.x, dv.y, dv.z, dv.w};
+            const float x4[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                if (a < TCO) {
-                    const float d = das[np][tco * TCO + a];
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) acc[a][k] = fmaf(d, xcs[np][tk * 4 + k], acc[a][k]);
-                }
+                for (int k = 0; k < 4; ++k) acc[a][k] = fmaf(d4[a], x4[k], acc[a][k]);
+            if (do_bias) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) bacc[a] += d4[a];
             }
         }
+        __syncthreads();
+        buf ^= 1;
     }
+    cp_async_wait<0>();
+    const int K = Ci * 9 + 1;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a) {
+        float *row = wpart + ((long)chunk * Co + cog * 4 + a) * K;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int co = tco * TCO + a, kk = ktile + tk * 4 + k;
-            if (a < TCO && kk < K) wpart[((long)chunk * Co + co) * K + kk] = acc[a][k];
-        }
+        for (int k = 0; k < 4; ++k) row[(cig * 4 + k) * 9 + tap] = acc[a][k];
+        if (do_bias) row[Ci * 9] = bacc[a];
+    }
 }
 
 // grad[oW + co*Ci*9 + k] = sum_chunks wpart (k < Ci*9); grad[oc + co] = bias column
@@ -433,19 +590,28 @@ static int fft_inv(Plan *p, Learned *L, const float2 *in, int nc, void *out, int
     return fft_pass_launch(p, e, PREC_F32, FMT_C64, outfmt, true);
 }
 
+template <int CO>
+static int conv_launch_co(Plan *p, Learned *L, const float *X, int Ci, int relu_in, const float *bias, float *out,
+                          int nc, const float *mask) {
+    constexpr int TP = 4096 / CO;
+    const size_t smem = ((size_t)Ci * 9 * CO + 2 * (size_t)TP * (Ci + 4) + 2 * 9 * (size_t)TP) * sizeof(float);
+    cudaFuncSetAttribute(lp_conv_kernel<CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
+    const long npos = (long)nc * L->bins;
+    const long ntiles = (npos + TP - 1) / TP;
+    const long blocks = std::min<long>(ntiles, p->nsm);
+    lp_conv_kernel<CO><<<(unsigned)blocks, 256, smem, p->stream>>>(X, Ci, relu_in, L->wt, bias, out, npos, L->my,
+                                                                   L->mx, L->bins, mask);
+    return BTTB_OK;
+}
+
 static int conv_launch(Plan *p, Learned *L, const float *X, int Ci, int relu_in, const __nv_bfloat16 *W,
                        const float *bias, float *out, int Co, int nc, int flip, const float *mask) {
     // flip = 1: data gradient (input channels Co of W, output channels Ci of W)
     const int wCo = flip ? Ci : Co, wCi = flip ? Co : Ci;
     lp_wt_kernel<<<64, 256, 0, p->stream>>>(W, L->wt, wCo, wCi, flip);
-    const size_t smem = (size_t)Ci * 9 * Co * sizeof(float);
-    cudaFuncSetAttribute(lp_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
-    const long npos = (long)nc * L->bins;
-    const int P = 256 / Co;
-    long blocks = (npos + P - 1) / P;
-    if (blocks > (long)p->nsm * 8) blocks = (long)p->nsm * 8;
-    lp_conv_kernel<<<(unsigned)blocks, 256, smem, p->stream>>>(X, Ci, relu_in, L->wt, bias, out, Co, npos, L->my, L->mx,
-                                                               L->bins, mask);
+    if (Co == 64) conv_launch_co<64>(p, L, X, Ci, relu_in, bias, out, nc, mask);
+    else if (Co == 32) conv_launch_co<32>(p, L, X, Ci, relu_in, bias, out, nc, mask);
+    else conv_launch_co<16>(p, L, X, Ci, relu_in, bias, out, nc, mask);
     count_launch(p, 2);
     return check_cuda(p, cudaGetLastError(), "learned conv launch");
 }
@@ -453,11 +619,15 @@ static int conv_launch(Plan *p, Learned *L, const float *X, int Ci, int relu_in,
 static int wgrad_launch(Plan *p, Learned *L, const float *X, int Ci, int relu_in, const float *dA, int Co, int nc,
                         float *gW, float *gc) {
     const long npos = (long)nc * L->bins;
-    const int nchunks = (int)((npos + kWgChunk - 1) / kWgChunk);
+    const int nchunks = (int)std::min<long>(kWgChunks, (npos + kWgTile - 1) / kWgTile);
+    const long chunk_len = ((npos + nchunks - 1) / nchunks + kWgTile - 1) / kWgTile * kWgTile;
+    const int nch = (int)((npos + chunk_len - 1) / chunk_len);
+    const size_t smem = 2 * (size_t)kWgTile * (Ci + Co + 8) * sizeof(float);
+    cudaFuncSetAttribute(lp_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
+    lp_wgrad_kernel<<<dim3(nch, 9), Ci * Co / 16, smem, p->stream>>>(X, Ci, relu_in, dA, Co, npos, chunk_len, L->my,
+                                                                      L->mx, L->bins, L->wpart);
     const int K = Ci * 9 + 1;
-    const dim3 grid(nchunks, (K + 63) / 64);
-    lp_wgrad_kernel<<<grid, 256, 0, p->stream>>>(X, Ci, relu_in, dA, Co, npos, L->my, L->mx, L->bins, L->wpart);
-    lp_wgrad_reduce_kernel<<<(Co * K + 255) / 256, 256, 0, p->stream>>>(L->wpart, nchunks, Co, Ci, gW, gc);
+    lp_wgrad_reduce_kernel<<<(Co * K + 255) / 256, 256, 0, p->stream>>>(L->wpart, nch, Co, Ci, gW, gc);
     count_launch(p, 2);
     return check_cuda(p, cudaGetLastError(), "learned weight-gradient launch");
 }
@@ -472,7 +642,7 @@ static int learned_forward(Learned *L, const void *r, int rfmt, long ld, int nc)
     const dim3 eg((unsigned)L->bins, (nc + kEncCols - 1) / kEncCols);
     cudaFuncSetAttribute(lp_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
     cudaFuncSetAttribute(lp_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
-    lp_encode_kernel<<<eg, 256, (size_t)(R * b + kEncCols * b) * sizeof(float2), p->stream>>>(
+    lp_encode_kernel<<<eg, 256, (size_t)(b * (R + 1) + kEncCols * (b + 1)) * sizeof(float2), p->stream>>>(
         wB, L->rh, L->ubs, L->hc, nc, b, R, L->bins, L->scale);
     count_launch(p);
     if ((rc = conv_launch(p, L, L->hc, 2 * R, 0, L->wbf + L->oW1, L->master + L->oc1, L->a1, C, nc, 0, nullptr)))
@@ -480,7 +650,7 @@ static int learned_forward(Learned *L, const void *r, int rfmt, long ld, int nc)
     if ((rc = conv_launch(p, L, L->a1, C, 1, L->wbf + L->oW2, L->master + L->oc2, L->a2, C, nc, 0, nullptr))) return rc;
     if ((rc = conv_launch(p, L, L->a2, C, 1, L->wbf + L->oW3, L->master + L->oc3, L->a3, 2 * R, nc, 0, nullptr)))
         return rc;
-    lp_decode_kernel<<<eg, 256, (size_t)(b * R + kEncCols * R) * sizeof(float2), p->stream>>>(
+    lp_decode_kernel<<<eg, 256, (size_t)(R * (b + 1) + kEncCols * R) * sizeof(float2), p->stream>>>(
         wA, L->hc, L->a3, L->zh, L->ubs, nc, b, R, L->bins, L->scale);
     count_launch(p);
     return fft_inv(p, L, L->zh, nc, L->zs, FMT_C64, L->n);
@@ -572,10 +742,10 @@ int bttb_learned_create(bttb_learned *out, bttb_plan plan, int rank, int channel
                         unsigned long long seed) {
     if (!out || !plan) return set_error(nullptr, BTTB_ERR_INVALID_ARG, "out or plan is NULL");
     *out = nullptr;
-    if (rank < 8 || rank > 32 || rank % 8 != 0 || (channels != 16 && channels != 32 && channels != 64) ||
+    if ((rank != 8 && rank != 16 && rank != 32) || (channels != 16 && channels != 32 && channels != 64) ||
         max_cols < 1 || max_cols > 256)
         return set_error(nullptr, BTTB_ERR_INVALID_ARG,
-                         "need rank in {8, 16, 24, 32}, channels in {16, 32, 64}, 1 <= max_cols <= 256");
+                         "need rank in {8, 16, 32}, channels in {16, 32, 64}, 1 <= max_cols <= 256");
     Plan &p = plan->p;
     if (!p.ghat_hi) return set_error(&p, BTTB_ERR_INVALID_ARG, "the plan needs the binary32 spectrum copy");
     Learned *L = new (std::nothrow) Learned();
@@ -630,9 +800,8 @@ int bttb_learned_create(bttb_learned *out, bttb_plan plan, int rank, int channel
     alloc(&L->dx, sizeof(float) * pos * std::max(C, 2 * R));
     alloc(&L->dh, sizeof(float) * pos * C);
     alloc(&L->wt, sizeof(float) * (size_t)std::max(C, 2 * R) * 9 * C);
-    const long nchunks = (pos + kWgChunk - 1) / kWgChunk;
     const long mc = std::max(C, 2 * R);
-    L->wpart_len = nchunks * mc * (mc * 9 + 1);
+    L->wpart_len = (long)kWgChunks * mc * (mc * 9 + 1);
     alloc(&L->wpart, sizeof(float) * L->wpart_len);
     alloc(&L->colred, sizeof(float) * 2 * nc);
     if (!ok) {

@@ -77,14 +77,18 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
 // ---------------------------------------------------------------------------
 constexpr int kBjThreads = 256;
 
+// R_0^{-1} is stored column-major (entry (p, q) at q*b + p), so the threads of a
+// warp, which own consecutive output rows p, read consecutive words.  A thread
+// computes two outputs at a time (rows of two cells) for independent FMA chains.
 template <int INF, int OUTF>
 __global__ void __launch_bounds__(kBjThreads) bj_apply_kernel(const float2 *rinv, const void *x, long ldx, void *z,
                                                                long ldz, int b, int ncells, int cpb,
                                                                const int *in_sel, long in_sel_stride,
                                                                int rinv_in_smem, const int *active) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *xs = reinterpret_cast<float2 *>(smem_raw);       // cpb*b
-    float2 *rsm = xs + (long)cpb * b;                         // b*b, row-major (when it fits)
+    const int xst = b + 1;                                    // padded row stride of the staged cells
+    float2 *xs = reinterpret_cast<float2 *>(smem_raw);       // cpb*xst
+    float2 *rsm = xs + (long)cpb * xst;                       // b*b, column-major (when it fits)
     const float2 *rs = rinv_in_smem ? rsm : rinv;
     const int c = blockIdx.y;
     pdl_wait();
@@ -95,23 +99,35 @@ __global__ void __launch_bounds__(kBjThreads) bj_apply_kernel(const float2 *rinv
         for (int i = threadIdx.x; i < b * b; i += blockDim.x) rsm[i] = rinv[i];
     long xoff = (long)c * ldx + (long)cell0 * b;
     if (in_sel) xoff += (long)(*in_sel) * in_sel_stride;
-    for (int i = threadIdx.x; i < nc * b; i += blockDim.x) xs[i] = load_vec<F32, INF>(x, xoff + i);
+    for (int i = threadIdx.x; i < nc * b; i += blockDim.x) {
+        const int cl = i / b;
+        xs[cl * xst + (i - cl * b)] = load_vec<F32, INF>(x, xoff + i);
+    }
     __syncthreads();
     long zoff = (long)c * ldz + (long)cell0 * b;
     if (in_sel) zoff += (long)(*in_sel) * in_sel_stride;       // same selected column slot on output
-    for (int o = threadIdx.x; o < nc * b; o += blockDim.x) {
-        const int cl = o / b, pr = o % b;
-        const float2 *row = rs + (long)pr * b;
-        const float2 *xv = xs + (long)cl * b;
-        float2 acc = make_float2(0.f, 0.f);
+    const int total = nc * b;
+    for (int o = threadIdx.x; o < total; o += 2 * blockDim.x) {
+        const int o2 = o + blockDim.x;
+        const bool two = o2 < total;
+        const int cl = o / b, pr = o - cl * b;
+        const int cl2 = two ? o2 / b : cl, pr2 = two ? o2 - cl2 * b : pr;
+        const float2 *xv = xs + (long)cl * xst, *xv2 = xs + (long)cl2 * xst;
+        float2 a = make_float2(0.f, 0.f), a2 = make_float2(0.f, 0.f);
         for (int q = 0; q < b; ++q) {
-            float2 g = row[q], u = xv[q];
-            acc.x = fmaf(g.x, u.x, acc.x);
-            acc.x = fmaf(-g.y, u.y, acc.x);
-            acc.y = fmaf(g.x, u.y, acc.y);
-            acc.y = fmaf(g.y, u.x, acc.y);
+            const float2 g = rs[(long)q * b + pr], g2 = rs[(long)q * b + pr2];
+            const float2 u = xv[q], u2 = xv2[q];
+            a.x = fmaf(g.x, u.x, a.x);
+            a.x = fmaf(-g.y, u.y, a.x);
+            a.y = fmaf(g.x, u.y, a.y);
+            a.y = fmaf(g.y, u.x, a.y);
+            a2.x = fmaf(g2.x, u2.x, a2.x);
+            a2.x = fmaf(-g2.y, u2.y, a2.x);
+            a2.y = fmaf(g2.x, u2.y, a2.y);
+            a2.y = fmaf(g2.y, u2.x, a2.y);
         }
-        store_vec<F32, OUTF>(z, zoff + o, acc);
+        store_vec<F32, OUTF>(z, zoff + o, a);
+        if (two) store_vec<F32, OUTF>(z, zoff + o2, a2);
     }
 }
 
@@ -122,7 +138,7 @@ static int bj_launch(Plan *p, const void *x, long ldx, void *z, long ldz, int nr
     int cpb = (8 * 1024) / b;                                  // cells per CTA
     if (cpb < 1) cpb = 1;
     if (cpb > ncells) cpb = ncells;
-    const size_t xs_bytes = (size_t)cpb * b * sizeof(float2);
+    const size_t xs_bytes = (size_t)cpb * (b + 1) * sizeof(float2);
     const size_t r_bytes = (size_t)b * b * sizeof(float2);
     const int in_smem = (xs_bytes + r_bytes <= 160 * 1024) ? 1 : 0;
     const size_t smem = xs_bytes + (in_smem ? r_bytes : 0);
@@ -217,7 +233,7 @@ int block_jacobi_setup(Plan *p, const double2 *t00) {
             col[2 * i] = (sr * dr + si * di) / dd;
             col[2 * i + 1] = (si * dr - sr * di) / dd;
         }
-        for (int i = 0; i < b; ++i) inv[(long)i * b + e] = make_float2((float)col[2 * i], (float)col[2 * i + 1]);
+        for (int i = 0; i < b; ++i) inv[(long)e * b + i] = make_float2((float)col[2 * i], (float)col[2 * i + 1]);
     }
     if (!p->bj_inv) {
         cudaError_t e = cudaMalloc(&p->bj_inv, (size_t)b * b * sizeof(float2));

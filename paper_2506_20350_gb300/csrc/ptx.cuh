@@ -103,6 +103,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 // Programmatic dependent launch: let the next kernel in the stream be scheduled
 // now, and wait until the kernels this one depends on have completed (both are
 // no-ops for a kernel launched without the programmatic attribute).
+// 16-byte asynchronous global -> shared copy (L2 only), commit and wait.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 

@@ -159,7 +159,7 @@ def test_adam_step_updates_master_and_lowers_loss(bt):
 def test_invalid_arguments(bt):
     plan = bt.Plan(4, 4, 12, max_rhs=2)
     with pytest.raises(bt.BttbError):
-        bt.Learned(plan, rank=12, channels=64, max_cols=2)     # rank not a multiple of 8
+        bt.Learned(plan, rank=12, channels=64, max_cols=2)     # rank not in {8, 16, 32}
     with pytest.raises(bt.BttbError):
         bt.Learned(plan, rank=16, channels=48, max_cols=2)
     plan.set_generators(arrays.generator_blocks(4, 4, 12, seed=0))

@@ -17,6 +17,13 @@ Reported:
   e2e          the same step through the C ABI with host buffers (H2D of V,
                D2H of I inside the timed region).
   cpu_baseline the CPU oracle's O(N^2) product timed on the host cores.
+  multi_rhs    all 900 port excitations of the same array in one batched solve.
+  uneven_batch 64 independent arrays of uneven size solved concurrently.
+  learned_preconditioner
+               the 40 x 40, b = 96 array: training of the learned correction
+               on 2000 plain-solver pairs, then 50 held-out excitations with
+               plain GMRES, block-Jacobi FGMRES and learned FGMRES.
+  (BTTB_BENCH_SKIP_MULTI / _UNEVEN / _LEARNED leave a leg out.)
 
 ``--impl reference`` times the CPU oracle as it stands on this workload:
 each step is one brute-force product (a bounded sample of the solve).
@@ -152,7 +159,9 @@ def product_bytes(nx, ny, b, mx, my, prec):
 def traffic_from_profiles(kernel_key: str):
     """ncu DRAM bytes per launch recorded in profiles/, if the kernel source is unchanged."""
     src = os.path.join(ROOT, "paper_2506_20350_gb300", "csrc", "contract.cu")
-    digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    # digest of the code lines only: comment edits keep the capture valid
+    code = [ln for ln in open(src).read().splitlines() if not ln.strip().startswith("//")]
+    digest = hashlib.sha1("\n".join(code).encode()).hexdigest()[:12]
     path = os.path.join(ROOT, "profiles", "contract_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -207,6 +216,113 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def learned_leg(dev, stream):
+    """The learned Fourier-domain preconditioner on the 40x40, b=96 array: 2000
+    (residual, exact correction) pairs from 500 seeded random port excitations
+    (plain-solver iterates after 0, 10, 40 and 80 steps; exact solutions to
+    1e-10), GPU training, then 50 held-out excitations solved to 1e-8 by plain
+    GMRES, block-Jacobi FGMRES and learned FGMRES."""
+    import torch
+
+    import paper_2506_20350_gb300 as bt
+    from workloads import arrays
+
+    c = arrays.CONFIGS["learned"]
+    nx, ny, b, tol = c["nx"], c["ny"], c["b"], c["tol"]
+    ntr_rhs, snaps, chunk = c["ntrain"] // 4, (0, 10, 40, 80), 50
+    t_all = time.perf_counter()
+    plan = bt.Plan(nx, ny, b, max_rhs=64, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_FP32), stream=stream)
+    g = arrays.generator_blocks_torch(nx, ny, b, c["seed"], device=dev)
+    plan.set_generators(g)
+    del g
+    n = plan.n
+    t0 = time.perf_counter()
+    rs, es = [], []
+    with torch.cuda.stream(stream):
+        vtr = arrays.random_port_excitations(nx, ny, b, ntr_rhs, seed=c["seed"])
+        for c0 in range(0, ntr_rhs, chunk):
+            V = torch.from_numpy(vtr[:, c0:c0 + chunk].T.copy()).to(dev)
+            xs, rc, _ = plan.solve(V, tol=1e-10, restart=50, max_iters=4000, pc=bt.BTTB_PC_BLOCK_JACOBI,
+                                   inner=bt.BTTB_MV_FP32)
+            for j in snaps:
+                xj = torch.zeros_like(V) if j == 0 else plan.solve(V, tol=1e-14, restart=50, max_iters=j)[0]
+                r = V - plan.matvec(xj)
+                nr = torch.linalg.vector_norm(r, dim=1, keepdim=True)
+                rs.append((r / nr).to(torch.complex64))
+                es.append(((xs - xj) / nr).to(torch.complex64))
+        rtr, etr = torch.cat(rs).contiguous(), torch.cat(es).contiguous()
+        del rs, es, vtr
+    torch.cuda.synchronize()
+    pairs_s = time.perf_counter() - t0
+    npairs = rtr.shape[0]
+    lrn = bt.Learned(plan, rank=16, channels=64, max_cols=64, seed=c["seed"])
+    Vte = torch.from_numpy(arrays.random_port_excitations(nx, ny, b, c["ntest"], seed=c["test_seed"]).T.copy()).to(dev)
+    steps, batch, lr = 1500, 64, 1e-3
+    gen_t = torch.Generator().manual_seed(c["seed"])
+    with torch.cuda.stream(stream):
+        loss0 = lrn.gradients(rtr[:64], etr[:64])[0]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s_ in range(steps):
+            idx = torch.randperm(npairs, generator=gen_t)[:batch].to(dev)
+            lrn.train_step(rtr[idx].contiguous(), etr[idx].contiguous(), lr=lr, want_loss=False)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        loss1 = lrn.gradients(rtr[:64], etr[:64])[0]
+        # held-out loss on the test excitations' first residuals (r = V, exact correction Z^-1 V)
+        xs_te, _, _ = plan.solve(Vte, tol=1e-10, restart=50, max_iters=4000, pc=bt.BTTB_PC_BLOCK_JACOBI,
+                                 inner=bt.BTTB_MV_FP32)
+        nr = torch.linalg.vector_norm(Vte, dim=1, keepdim=True)
+        rte = (Vte / nr).to(torch.complex64).contiguous()
+        ete = (xs_te / nr).to(torch.complex64).contiguous()
+        lrn2 = lrn.gradients(rte, ete)[0]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lrn.apply(rte)
+        ev0.record(stream)
+        for _ in range(10):
+            lrn.apply(rte)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = ev0.elapsed_time(ev1) / 10
+    del rtr, etr
+    lrn.attach()
+    res = {}
+    for name, pc, inner in (("plain_fp64", bt.BTTB_PC_NONE, bt.BTTB_MV_FP64),
+                            ("plain_ir", bt.BTTB_PC_NONE, bt.BTTB_MV_FP32),
+                            ("block_jacobi_fp64", bt.BTTB_PC_BLOCK_JACOBI, bt.BTTB_MV_FP64),
+                            ("block_jacobi_ir", bt.BTTB_PC_BLOCK_JACOBI, bt.BTTB_MV_FP32),
+                            ("learned_fp64", bt.BTTB_PC_LEARNED, bt.BTTB_MV_FP64),
+                            ("learned_ir", bt.BTTB_PC_LEARNED, bt.BTTB_MV_FP32)):
+        with torch.cuda.stream(stream):
+            plan.solve(Vte, tol=tol, restart=50, max_iters=2, pc=pc, inner=inner)     # graph + buffers
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            _, rc, rr = plan.solve(Vte, tol=tol, restart=50, max_iters=5000, pc=pc, inner=inner)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        its = [x.iters for x in rr]
+        res[name] = {"solve_ms": dt * 1e3, "status_ok": sum(x.status == bt.BTTB_OK for x in rr),
+                     "iters_mean": float(np.mean(its)), "iters_max": max(its),
+                     "relres_true_max": max(x.relres_true for x in rr)}
+    base = res["plain_fp64"]["solve_ms"]
+    for v in res.values():
+        v["speedup_vs_plain_fp64"] = base / v["solve_ms"]
+    bt.bttb_plan_set_learned(plan.handle, None)
+    out = {"workload": f"{nx}x{ny} b={b}, N={n}, grid {plan.mx}x{plan.my}; {c['ntest']} held-out random "
+                       f"port excitations (seed {c['test_seed']}) to {tol:g}",
+           "network": "per-bin rank-16 complex encode/decode + 3 circular 3x3 convs (32->64->64->32 ch), "
+                      "bf16 weights, fp32 accumulate",
+           "params": lrn.count, "training_pairs": npairs, "pairs_s": pairs_s,
+           "train_steps": steps, "batch": batch, "lr": lr, "train_s": train_s,
+           "train_ms_per_step": train_s * 1e3 / steps, "loss_train_before": loss0, "loss_train_after": loss1,
+           "loss_heldout_first_residual": lrn2, "apply_ms_50_columns": apply_ms,
+           "solves": res, "leg_s": time.perf_counter() - t_all}
+    lrn.close()
+    plan.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -259,7 +375,9 @@ def run_ours(args):
     ev0.record(stream)
     total_bytes, iters, cycles, relres = 0.0, [], [], []
     for _ in range(args.steps):
+        torch.cuda.nvtx.range_push("ir_step")
         r = solve()
+        torch.cuda.nvtx.range_pop()
         total_bytes += step_bytes(r, bt.BTTB_MV_FP32)
         iters.append(r.iters)
         cycles.append(r.cycles)
@@ -416,6 +534,11 @@ def run_ours(args):
         batch.close()
         torch.cuda.empty_cache()
 
+    learned = None
+    if os.environ.get("BTTB_BENCH_SKIP_LEARNED") is None:
+        learned = learned_leg(dev, stream)
+        torch.cuda.empty_cache()
+
     peak, peak_kind = measured_peaks()
     ach32 = st32.bytes / (st32.ms / 1e3) / 1e9 if st32.ms > 0 else 0.0
     ach64 = st64.bytes / (st64.ms / 1e3) / 1e9 if st64.ms > 0 else 0.0
@@ -460,6 +583,7 @@ def run_ours(args):
         "step_breakdown_host_driven": breakdown,
         "multi_rhs": multi,
         "uneven_batch": uneven,
+        "learned_preconditioner": learned,
     }
     print(json.dumps(line), flush=True)
     barrier(world)

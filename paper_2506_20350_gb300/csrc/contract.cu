@@ -4,19 +4,22 @@
 //
 // This kernel streams the whole spectrum once per product and is bound by HBM
 // bandwidth.  Design:
-//  - persistent CTAs (one per SM); bins are dealt out round-robin and a CTA
-//    walks the column chunks of each of its bins in order;
-//  - one producer warp issues bulk asynchronous copies (cp.async.bulk with an
-//    evict-first L2 policy) of the spectrum chunk -- one plane for binary32 and
-//    binary64, the hi and lo planes for double-float -- plus the bin's
-//    transformed vectors into a ring of shared-memory stages guarded by
-//    mbarrier transaction counts;
-//  - eight consumer warps: thread (p, g) owns output row p and the g-th slice
-//    of the chunk's columns; the spectrum is stored column-major per bin, so a
-//    warp reads consecutive rows of one column (conflict-free) and the vector
-//    entry is a broadcast;
-//  - double-float accumulation is compensated (Dot2); the G partial sums of a
-//    row are combined through shared memory at the end of each bin.
+//  - persistent CTAs (one per SM) of eight warps; bins are dealt out
+//    round-robin over CTAs, then over the CTA's warps, and one warp owns one
+//    bin at a time (lane l accumulates rows l*R .. l*R+R-1 over all columns),
+//    so a bin needs no cross-warp reduction and no barrier;
+//  - each warp streams its bins' column chunks through a private ring of
+//    shared-memory stages: lane 0 issues bulk asynchronous copies
+//    (cp.async.bulk, evict-first L2 policy for the spectrum) of the spectrum
+//    chunk -- one plane for binary32 and binary64, the hi and lo planes for
+//    double-float -- plus the bin's transformed vectors, one mbarrier per stage
+//    counting the bytes in;
+//  - the spectrum is stored column-major per bin, so a lane reads R
+//    consecutive rows of one column (a 16-byte vector for R = 2) and the
+//    vector entry is a broadcast;
+//  - double-float accumulation is compensated (Dot2); every mbarrier wait is
+//    bounded by the global timer and reports a timeout instead of hanging.
+// A second kernel (contract_multi_kernel, below) covers many right-hand sides.
 #include <cstdio>
 
 #include "arith.cuh"

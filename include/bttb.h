@@ -142,8 +142,16 @@ typedef struct {
 /* Each restart cycle (m Arnoldi steps, back substitution, update) runs as one
  * CUDA graph replayed per cycle; finished columns make the remaining kernels of
  * the cycle exit at once.  BTTB_GMRES_NO_GRAPH launches the same kernels from
- * the host instead, with one host synchronisation per step. */
-enum { BTTB_GMRES_NO_GRAPH = 1 };
+ * the host instead, with one host synchronisation per step.
+ *
+ * BTTB_GMRES_GLOBAL (nrhs > 1): the global GMRES of Sec. III-C, Eq. (ZIVvec):
+ * one Krylov space for vec(I) of the system (I (x) Z) vec(I) = vec(V), with
+ * Frobenius inner products, instead of one Krylov space per column.  Every
+ * column stays in the space until all columns meet tol (each cycle targets a
+ * Frobenius residual of tol * min_c ||V_c||); every column reports the same
+ * iteration count and its own true residual.  Default: one space per column,
+ * converged columns masked. */
+enum { BTTB_GMRES_NO_GRAPH = 1, BTTB_GMRES_GLOBAL = 2 };
 
 typedef struct {
     int status;          /* BTTB_OK, BTTB_NOT_CONVERGED or BTTB_BREAKDOWN          */

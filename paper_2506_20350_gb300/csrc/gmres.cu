@@ -24,8 +24,12 @@
 namespace bttb {
 
 struct GmresWork {
-    int m = 0, k = 0;
-    long n = 0;
+    int m = 0, k = 0;             // Krylov dimension, Krylov columns
+    long n = 0;                   // Krylov vector length
+    int kp = 0;                   // product columns (k, or the k user columns of one global Krylov column)
+    long np = 0;                  // product vector length (N)
+    bool glob = false;            // global GMRES: one Krylov column over all kp user columns
+    int *act_prod = nullptr;      // per product column copy of the global column's active flag
     bool flex = false;            // Zb allocated
     int pc = BTTB_PC_NONE;        // preconditioner of the current solve
     int NB = 0, nblk = 0;
@@ -175,6 +179,11 @@ __global__ void resid_kernel(const float4 *vin, const float4 *zx, float4 *r, lon
 }
 
 // Start of a cycle: g = (beta0, 0, ...), inv_beta = 1/beta0, j = 0.
+// Global GMRES: every product column follows the one Krylov column's flag.
+__global__ void bcast_active_kernel(const int *active, int *act_prod, int kp) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kp; i += gridDim.x * blockDim.x) act_prod[i] = active[0];
+}
+
 __global__ void cycle_start_kernel(const double *beta2, float4 *gv, double *inv_beta, int m, int k,
                                    const int *active) {
     for (int c = threadIdx.x; c < k; c += blockDim.x) {
@@ -567,7 +576,7 @@ static void free_work(GmresWork *g) {
     cudaFree(g->part); cudaFree(g->cs); cudaFree(g->beta2); cudaFree(g->vnorm); cudaFree(g->inv_beta);
     cudaFree(g->target); cudaFree(g->active); cudaFree(g->steps); cudaFree(g->bdown); cudaFree(g->mlimit);
     cudaFree(g->d_j); cudaFree(g->d_any); cudaFree(g->io); cudaFree(g->act_cycle);
-    cudaFree(g->counters); cudaFree(g->d_any_step);
+    cudaFree(g->counters); cudaFree(g->d_any_step); cudaFree(g->act_prod);
     cudaFreeHost(g->h_any);
     delete g;
 }
@@ -578,20 +587,30 @@ void gmres_free(Plan *p) {
     p->gw = nullptr;
 }
 
-static int ensure_work(Plan *p, int m, int k, bool flex, bool host_io) {
+static long norm_pstride(int m, long len) {
+    return std::max((long)(m + 1) * ((len + kDotNE - 1) / kDotNE), (len + kStepNB - 1) / kStepNB);
+}
+
+// Workspace for k Krylov columns of length n; the product sees kp columns of
+// length np (kp = k, np = n, or one global column: k = 1, n = kp * np).
+static int ensure_work(Plan *p, int m, int k, long nv, int kp, bool flex, bool host_io) {
     GmresWork *g = p->gw;
-    if (g && g->m == m && g->k == k && (g->flex || !flex) && (!host_io || g->io)) return BTTB_OK;
+    if (g && g->m == m && g->k == k && g->n == nv && g->kp == kp && (g->flex || !flex) && (!host_io || g->io))
+        return BTTB_OK;
     gmres_free(p);
     g = new GmresWork();
     g->m = m;
     g->k = k;
-    g->n = p->n;
+    g->n = nv;
+    g->kp = kp;
+    g->np = p->n;
+    g->glob = (k == 1 && kp > 1);
     g->flex = flex;
     g->NB = kStepNB;
-    g->nblk = (int)((p->n + g->NB - 1) / g->NB);               // update / scale / norm grid
-    const long nblk_dot = (p->n + kDotNE - 1) / kDotNE;
-    const long pstride = std::max((long)(m + 1) * nblk_dot, (long)g->nblk);
-    const long n = p->n;
+    g->nblk = (int)((nv + g->NB - 1) / g->NB);                 // update / scale / norm grid
+    const long pstride = std::max(norm_pstride(m, nv) * k, norm_pstride(m, p->n) * kp);
+    const long n = nv;
+    const int ks = std::max(k, kp);                             // per-column scalars (user norms need kp)
     size_t total = 0;
     bool ok = true;
     auto alloc = [&](auto **ptr, size_t bytes) {
@@ -611,9 +630,10 @@ static int ensure_work(Plan *p, int m, int k, bool flex, bool host_io) {
     alloc(&g->sn, sizeof(float4) * (size_t)k * m);
     alloc(&g->hco, sizeof(float4) * (size_t)k * (m + 1));
     alloc(&g->ycoef, sizeof(float4) * (size_t)k * (m + 1));
-    alloc(&g->part, sizeof(float4) * (size_t)k * pstride);
+    alloc(&g->part, sizeof(float4) * (size_t)pstride);
     alloc(&g->cs, sizeof(float2) * (size_t)k * m);
-    alloc(&g->beta2, sizeof(double) * k);
+    alloc(&g->beta2, sizeof(double) * ks);
+    alloc(&g->act_prod, sizeof(int) * kp);
     alloc(&g->vnorm, sizeof(double) * k);
     alloc(&g->inv_beta, sizeof(double) * k);
     alloc(&g->target, sizeof(double) * k);
@@ -639,12 +659,12 @@ static int ensure_work(Plan *p, int m, int k, bool flex, bool host_io) {
     return BTTB_OK;
 }
 
-// ||col||^2 of the k columns of x ([c][n] double-float) into g->beta2.
-static int norm2_cols(Plan *p, GmresWork *g, const float4 *x, int k) {
-    const long pstride = std::max((long)(g->m + 1) * ((p->n + kDotNE - 1) / kDotNE), (long)g->nblk);
-    norm_partial_kernel<<<dim3(g->nblk, k), kVecThreads, 0, p->stream>>>(x, p->n, kStepNB, g->nblk, pstride,
-                                                                          g->part);
-    norm_final_kernel<<<k, 32, 0, p->stream>>>(g->part, g->nblk, pstride, g->beta2);
+// ||col||^2 of the ncols columns of x ([c][len] double-float) into g->beta2.
+static int norm2_cols(Plan *p, GmresWork *g, const float4 *x, int ncols, long len) {
+    const long pstride = norm_pstride(g->m, len);
+    const int nblk = (int)((len + kStepNB - 1) / kStepNB);
+    norm_partial_kernel<<<dim3(nblk, ncols), kVecThreads, 0, p->stream>>>(x, len, kStepNB, nblk, pstride, g->part);
+    norm_final_kernel<<<ncols, 32, 0, p->stream>>>(g->part, nblk, pstride, g->beta2);
     count_launch(p, 2);
     return check_cuda(p, cudaGetLastError(), "norm launch");
 }
@@ -652,22 +672,28 @@ static int norm2_cols(Plan *p, GmresWork *g, const float4 *x, int k) {
 // One Arnoldi step for every active column, on p->stream (captured or not):
 // [block-Jacobi], the product, then the four fused Gram-Schmidt/Givens kernels.
 static int arnoldi_step(Plan *p, GmresWork *g, int inner, int j) {
-    const int m = g->m, k = g->k;
-    const long n = p->n, bs_i = (long)k * n;
+    const int m = g->m, k = g->k, kp = g->kp;
+    const long n = g->n, np = g->np, bs_i = (long)k * n;
     cudaStream_t st = p->stream;
     int rc;
     const float4 *src = g->Vb;
+    const int *pact = g->active;                 // product-column flags
+    if (g->glob) {
+        bcast_active_kernel<<<(kp + 255) / 256, 256, 0, st>>>(g->active, g->act_prod, kp);
+        count_launch(p);
+        pact = g->act_prod;
+    }
     if (g->pc == BTTB_PC_BLOCK_JACOBI) {
-        rc = block_jacobi_run(p, g->Vb + (long)j * bs_i, FMT_CDF, n, g->Zb + (long)j * bs_i, FMT_CDF, n, k,
-                              nullptr, 0, g->active);
+        rc = block_jacobi_run(p, g->Vb + (long)j * bs_i, FMT_CDF, np, g->Zb + (long)j * bs_i, FMT_CDF, np, kp,
+                              nullptr, 0, pact);
         if (rc != BTTB_OK) return rc;
         src = g->Zb;
     } else if (g->pc == BTTB_PC_LEARNED) {
-        rc = learned_apply_run(p, g->Vb + (long)j * bs_i, FMT_CDF, n, g->Zb + (long)j * bs_i, FMT_CDF, n, k);
+        rc = learned_apply_run(p, g->Vb + (long)j * bs_i, FMT_CDF, np, g->Zb + (long)j * bs_i, FMT_CDF, np, kp);
         if (rc != BTTB_OK) return rc;
         src = g->Zb;
     }
-    rc = matvec_run(p, src + (long)j * bs_i, FMT_CDF, n, g->W, FMT_CDF, n, k, inner, nullptr, 0, nullptr, g->active);
+    rc = matvec_run(p, src + (long)j * bs_i, FMT_CDF, np, g->W, FMT_CDF, np, kp, inner, nullptr, 0, nullptr, pact);
     if (rc != BTTB_OK) return rc;
     StepArgs a{};
     a.Vb = g->Vb;
@@ -722,7 +748,7 @@ static int arnoldi_step(Plan *p, GmresWork *g, int inner, int j) {
 // Back substitution and x += (preconditioned) basis * y for the columns of this cycle.
 static int cycle_finish(Plan *p, GmresWork *g) {
     const int m = g->m, k = g->k;
-    const long n = p->n, bs_i = (long)k * n, bs_c = n;
+    const long n = g->n, bs_i = (long)k * n, bs_c = n;
     const int vgrid = (int)std::min<long>((n + kVecThreads - 1) / kVecThreads, 1024);
     finish_kernel<<<k, kFinishThreads, (m + 1) * sizeof(double2), p->stream>>>(g->H, g->gv, g->steps, g->ycoef, m,
                                                                                g->act_cycle);
@@ -781,15 +807,20 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
     const bool flex = o->pc != BTTB_PC_NONE;
     const int inner = o->inner;
     const bool use_graph = !(o->flags & BTTB_GMRES_NO_GRAPH);
-    int rc = ensure_work(p, m, k, flex, o->host_io != 0);
+    // Global GMRES (Sec. III-C, Eq. (ZIVvec)): one Krylov space for vec(I), Frobenius inner products.
+    const bool glob = (o->flags & BTTB_GMRES_GLOBAL) && k > 1;
+    const long n = p->n;                         // user / product vector length
+    const int kg = glob ? 1 : k;                 // Krylov columns
+    const long nv = glob ? (long)k * n : n;      // Krylov vector length
+    int rc = ensure_work(p, m, kg, nv, k, flex, o->host_io != 0);
     if (rc != BTTB_OK) return rc;
     GmresWork *g = p->gw;
     g->pc = o->pc;
-    const long n = p->n;
-    const long bs_i = (long)k * n, bs_c = n;    // basis layout [i][c][n]
+    const long bs_i = (long)kg * nv, bs_c = nv;  // basis layout [i][c][nv]
     cudaStream_t st = p->stream;
     cudaError_t e;
     const int vgrid = (int)std::min<long>((n + kVecThreads - 1) / kVecThreads, 1024);
+    const int kgrid = (int)std::min<long>((nv + kVecThreads - 1) / kVecThreads, 1024);
 
     // Inputs: V -> Vin (double-float), I (x0) -> X
     const double2 *Vd = reinterpret_cast<const double2 *>(V);
@@ -819,70 +850,113 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
         fill_zero_kernel<<<1024, kVecThreads, 0, st>>>(g->X, (long)k * n);
         count_launch(p);
     }
-    if ((rc = norm2_cols(p, g, g->Vin, k)) != BTTB_OK) return rc;
-    std::vector<double> vn2(k), vnorm(k), b2(k), relres(k, 0.0), tgt(k);
-    std::vector<int> status(k, BTTB_OK), total(k, 0), cycles(k, 0), act(k), mlim(k), stp(k, 0), bd(k, 0);
+    if ((rc = norm2_cols(p, g, g->Vin, k, n)) != BTTB_OK) return rc;
+    std::vector<double> vn2(k), vnorm(k), b2(k), relres(k, 0.0), tgt(kg);
+    std::vector<int> status(k, BTTB_OK), cycles(k, 0);
+    std::vector<int> total(kg, 0), act(kg), mlim(kg), stp(kg, 0), bd(kg, 0);   // per Krylov column
     e = cudaMemcpyAsync(vn2.data(), g->beta2, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return check_cuda(p, e, "norm of V");
-    for (int c = 0; c < k; ++c) vnorm[c] = std::sqrt(vn2[c]);
+    double vmin = INFINITY;
+    for (int c = 0; c < k; ++c) {
+        vnorm[c] = std::sqrt(vn2[c]);
+        if (vnorm[c] > 0.0) vmin = std::min(vmin, vnorm[c]);
+    }
     std::vector<char> done(k, 0);
     int hist_n = 0;
     const int max_iters = o->max_iters;
     int dev_err = 0;
 
     for (int cycle = 0;; ++cycle) {
-        // True residual with the FP64 product.
+        // True residual with the FP64 product, per user column.
         if ((rc = matvec_run(p, g->X, FMT_CDF, n, g->W, FMT_CDF, n, k, PREC_DF64)) != BTTB_OK) return rc;
         resid_kernel<<<1024, kVecThreads, 0, st>>>(g->Vin, g->W, g->R, (long)k * n);
         count_launch(p);
-        if ((rc = norm2_cols(p, g, g->R, k)) != BTTB_OK) return rc;
+        if ((rc = norm2_cols(p, g, g->R, k, n)) != BTTB_OK) return rc;
         e = cudaMemcpyAsync(b2.data(), g->beta2, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&dev_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return check_cuda(p, e, "residual norm");
         if (dev_err & DEVERR_TIMEOUT) return set_error(p, BTTB_ERR_TIMEOUT, "a device pipeline wait timed out");
         bool any = false;
-        for (int c = 0; c < k; ++c) {
-            if (done[c]) { act[c] = 0; continue; }
-            relres[c] = vnorm[c] > 0.0 ? std::sqrt(b2[c]) / vnorm[c] : 0.0;
-            if (!std::isfinite(relres[c])) {
-                status[c] = BTTB_ERR_NONFINITE;
-                done[c] = 1;
-            } else if (relres[c] <= o->tol || vnorm[c] == 0.0) {
-                status[c] = BTTB_OK;
-                done[c] = 1;
-            } else if (total[c] >= max_iters) {
-                status[c] = BTTB_NOT_CONVERGED;
-                done[c] = 1;
-            } else if (cycle > 0 && bd[c] && stp[c] == 0) {
-                status[c] = BTTB_BREAKDOWN;
-                done[c] = 1;
+        if (!glob) {
+            for (int c = 0; c < k; ++c) {
+                if (done[c]) { act[c] = 0; continue; }
+                relres[c] = vnorm[c] > 0.0 ? std::sqrt(b2[c]) / vnorm[c] : 0.0;
+                if (!std::isfinite(relres[c])) {
+                    status[c] = BTTB_ERR_NONFINITE;
+                    done[c] = 1;
+                } else if (relres[c] <= o->tol || vnorm[c] == 0.0) {
+                    status[c] = BTTB_OK;
+                    done[c] = 1;
+                } else if (total[c] >= max_iters) {
+                    status[c] = BTTB_NOT_CONVERGED;
+                    done[c] = 1;
+                } else if (cycle > 0 && bd[c] && stp[c] == 0) {
+                    status[c] = BTTB_BREAKDOWN;
+                    done[c] = 1;
+                }
+                act[c] = done[c] ? 0 : 1;
+                if (act[c]) {
+                    any = true;
+                    mlim[c] = std::min(m, max_iters - total[c]);
+                    const double b0 = std::sqrt(b2[c]);
+                    double t = 0.9 * o->tol * vnorm[c];
+                    if (inner == BTTB_MV_FP32) t = std::max(t, 1e-5 * b0);
+                    tgt[c] = t;
+                    cycles[c] += 1;
+                }
             }
-            act[c] = done[c] ? 0 : 1;
-            if (act[c]) {
+        } else {
+            // Every column stays in the one Krylov space until all meet tol; the cycle's target on the
+            // Frobenius norm, tol * min_c ||V_c||, bounds every column's residual by tol ||V_c||.
+            double f2 = 0.0;
+            bool all_ok = true, bad = false;
+            for (int c = 0; c < k; ++c) {
+                relres[c] = vnorm[c] > 0.0 ? std::sqrt(b2[c]) / vnorm[c] : 0.0;
+                if (!std::isfinite(relres[c])) bad = true;
+                if (!(relres[c] <= o->tol) && vnorm[c] != 0.0) all_ok = false;
+                f2 += b2[c];
+            }
+            int fin = -1;                                 // status for every column when the solve ends
+            if (bad) fin = BTTB_ERR_NONFINITE;
+            else if (all_ok) fin = BTTB_OK;
+            else if (total[0] >= max_iters) fin = BTTB_NOT_CONVERGED;
+            else if (cycle > 0 && bd[0] && stp[0] == 0) fin = BTTB_BREAKDOWN;
+            if (fin != -1) {
+                for (int c = 0; c < k; ++c) {
+                    status[c] = fin;
+                    if ((fin == BTTB_NOT_CONVERGED || fin == BTTB_BREAKDOWN) && relres[c] <= o->tol)
+                        status[c] = BTTB_OK;
+                    if (fin == BTTB_ERR_NONFINITE && std::isfinite(relres[c])) status[c] = BTTB_NOT_CONVERGED;
+                }
+                act[0] = 0;
+            } else {
                 any = true;
-                mlim[c] = std::min(m, max_iters - total[c]);
-                const double b0 = std::sqrt(b2[c]);
-                double t = 0.9 * o->tol * vnorm[c];
-                if (inner == BTTB_MV_FP32) t = std::max(t, 1e-5 * b0);
-                tgt[c] = t;
-                cycles[c] += 1;
+                act[0] = 1;
+                mlim[0] = std::min(m, max_iters - total[0]);
+                double t = 0.9 * o->tol * (std::isfinite(vmin) ? vmin : 0.0);
+                if (inner == BTTB_MV_FP32) t = std::max(t, 1e-5 * std::sqrt(f2));
+                tgt[0] = t;
+                for (int c = 0; c < k; ++c) cycles[c] += 1;
+                e = cudaMemcpyAsync(g->beta2, &f2, sizeof(double), cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);     // f2 is a host stack value
+                if (e != cudaSuccess) return check_cuda(p, e, "Frobenius norm");
             }
         }
         if (o->history && hist_n < o->history_len) o->history[hist_n++] = relres[0];
         if (!any) break;
-        cudaMemcpyAsync(g->active, act.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(g->act_cycle, act.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(g->mlimit, mlim.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(g->target, tgt.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st);
-        cudaMemsetAsync(g->bdown, 0, sizeof(int) * k, st);
-        cudaMemsetAsync(g->steps, 0, sizeof(int) * k, st);
+        cudaMemcpyAsync(g->active, act.data(), sizeof(int) * kg, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(g->act_cycle, act.data(), sizeof(int) * kg, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(g->mlimit, mlim.data(), sizeof(int) * kg, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(g->target, tgt.data(), sizeof(double) * kg, cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(g->bdown, 0, sizeof(int) * kg, st);
+        cudaMemsetAsync(g->steps, 0, sizeof(int) * kg, st);
         cudaMemsetAsync(g->d_any_step, 0, sizeof(int), st);
-        cycle_start_kernel<<<1, 256, 0, st>>>(g->beta2, g->gv, g->inv_beta, m, k, g->active);
+        cycle_start_kernel<<<1, 256, 0, st>>>(g->beta2, g->gv, g->inv_beta, m, kg, g->active);
         count_launch(p);
-        scale_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(g->R, g->Vb, bs_i, bs_c, 0, g->inv_beta, n,
-                                                             g->active);
+        scale_kernel<<<dim3(kgrid, kg), kVecThreads, 0, st>>>(g->R, g->Vb, bs_i, bs_c, 0, g->inv_beta, nv,
+                                                              g->active);
         count_launch(p);
         if (use_graph) {
             if (!g->cycle_exec || g->graph_inner != inner || g->graph_pc != g->pc || g->graph_prof != p->prof)
@@ -899,12 +973,12 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
             }
             if ((rc = cycle_finish(p, g)) != BTTB_OK) return rc;
         }
-        e = cudaMemcpyAsync(stp.data(), g->steps, sizeof(int) * k, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(bd.data(), g->bdown, sizeof(int) * k, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(stp.data(), g->steps, sizeof(int) * kg, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bd.data(), g->bdown, sizeof(int) * kg, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return check_cuda(p, e, "cycle end");
         int maxsteps = 0;
-        for (int c = 0; c < k; ++c)
+        for (int c = 0; c < kg; ++c)
             if (act[c]) {
                 total[c] += stp[c];
                 maxsteps = std::max(maxsteps, stp[c]);
@@ -945,7 +1019,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
     for (int c = 0; c < k; ++c) {
         if (out) {
             out[c].status = status[c];
-            out[c].iters = total[c];
+            out[c].iters = total[glob ? 0 : c];
             out[c].cycles = cycles[c];
             out[c].relres_true = relres[c];
         }

@@ -56,7 +56,12 @@ typedef enum { BTTB_C64 = 0, BTTB_C128 = 1 } bttb_dtype;
 typedef enum {
     BTTB_MV_FP64 = 0,        /* double-float spectrum (hi+lo planes) and arithmetic  */
     BTTB_MV_FP32 = 1,        /* binary32 spectrum (the hi plane) and arithmetic      */
-    BTTB_MV_FP64_NATIVE = 2  /* binary64 spectrum copy, binary64 (DFMA) arithmetic   */
+    BTTB_MV_FP64_NATIVE = 2, /* binary64 spectrum copy, binary64 (DFMA) arithmetic   */
+    BTTB_MV_TC_3XTF32 = 3    /* binary32 FFT passes; with >= 16 columns and b <= 64 the
+                                per-bin GEMM runs on the tensor cores in 3xTF32 (TF32
+                                head + tail of each factor, binary32 accumulation:
+                                binary32-level accuracy), otherwise as BTTB_MV_FP32.
+                                Reads the binary32 spectrum (hi plane).               */
 } bttb_mv_prec;
 
 typedef enum {
@@ -127,9 +132,9 @@ typedef struct {
     int max_iters;       /* total Arnoldi steps per column                         */
     bttb_precond pc;     /* right preconditioner (the residual stays the true one) */
     bttb_mv_prec inner;  /* precision of the products inside a restart cycle:
-                            FP64 = plain GMRES; FP32 = GMRES-IR (each cycle's
-                            starting residual is recomputed with the FP64 product,
-                            Arnoldi/Givens stay FP64)                             */
+                            FP64 = plain GMRES; FP32 or TC_3XTF32 = GMRES-IR (each
+                            cycle's starting residual is recomputed with the FP64
+                            product, Arnoldi/Givens stay FP64)                    */
     int use_x0;          /* nonzero: I holds the initial guess on entry            */
     int host_io;         /* nonzero: V and I are HOST pointers (complex128); the
                             library copies them in and out on the plan's stream  */
@@ -191,7 +196,9 @@ int bttb_get_spectrum_bin(bttb_plan plan, int ky, int kx, double *out_host);
  * Kernel timing.  While enabled, the plan brackets every launch of the block
  * product and of the FFT passes with CUDA events on its stream and counts
  * every kernel it launches.  bttb_profile(plan, 1) clears and starts,
- * bttb_profile(plan, 0) stops.  bttb_profile_read synchronises the stream and
+ * bttb_profile(plan, 0) stops.  Inside captured GMRES cycles level 1 times only
+ * the block product; bttb_profile(plan, 2) times every kernel that has a kind
+ * (the extra event nodes serialise the graph, so level 2 is for breakdowns).  bttb_profile_read synchronises the stream and
  * fills *out for `which`:
  *   BTTB_K_BLOCK_PRODUCT, BTTB_K_FFT: summed event time (ms), launches, and
  *     algorithmic bytes (the bytes the operation must move: spectrum planes
@@ -258,8 +265,8 @@ int bttb_batch_plan(bttb_batch batch, int index, bttb_plan *out);
 int bttb_batch_set_generators(bttb_batch batch, int index, const void *gen, bttb_dtype dtype, int gen_is_host);
 /*
  * Autotuner: for every distinct FFT grid and block size (mx, my, b) in the
- * batch, time `reps` binary32 products with each FFT batch-chunk width in
- * {2, 4, 8, 16, 32} on the array's stream and keep the fastest for every array
+ * batch, time `reps` one-column binary32 products with each FFT batch-chunk
+ * width in {2, 4, 8, 16, 32, 64} on the array's stream and keep the fastest for every array
  * of that shape.  chosen_out (host, count entries, may be NULL) receives the
  * width per array.  Needs the generators of the arrays to tune.
  */
@@ -325,6 +332,16 @@ int bttb_learned_train_step(bttb_learned l, const void *r, const void *e, int nc
 /* Attach (or, with l == NULL, detach) the object used by BTTB_PC_LEARNED. */
 int bttb_plan_set_learned(bttb_plan plan, bttb_learned l);
 int bttb_learned_destroy(bttb_learned l);
+
+/*
+ * Autotuner for one plan: times `reps` binary32 products of `nrhs` columns
+ * with each FFT batch-chunk width in {2, 4, 8, 16, 32, 64} on the plan's
+ * stream and keeps the fastest for every later call of the plan (all
+ * precisions; the width only changes the launch shape, not the result).
+ * chosen_out (host, may be NULL) receives it.  Needs the generators; frees
+ * the plan's GMRES workspace (it is rebuilt on the next solve).
+ */
+int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out);
 
 /* Bytes of device memory the plan holds (spectrum copies and workspace). */
 size_t bttb_plan_workspace_bytes(bttb_plan plan);

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbttb.so")
 
 BTTB_C64, BTTB_C128 = 0, 1
-BTTB_MV_FP64, BTTB_MV_FP32, BTTB_MV_FP64_NATIVE = 0, 1, 2
+BTTB_MV_FP64, BTTB_MV_FP32, BTTB_MV_FP64_NATIVE, BTTB_MV_TC_3XTF32 = 0, 1, 2, 3
 BTTB_PC_NONE, BTTB_PC_BLOCK_JACOBI, BTTB_PC_LEARNED = 0, 1, 2
 BTTB_GMRES_NO_GRAPH, BTTB_GMRES_GLOBAL = 1, 2
 BTTB_OK, BTTB_NOT_CONVERGED, BTTB_BREAKDOWN = 0, 1, 2
@@ -35,7 +35,7 @@ EXPORTS = ("bttb_plan_create", "bttb_plan_grid", "bttb_set_generators", "bttb_ma
            "bttb_batch_gmres_solve", "bttb_batch_destroy",
            "bttb_learned_create", "bttb_learned_param_count", "bttb_learned_params", "bttb_learned_apply",
            "bttb_learned_gradients", "bttb_learned_train_step", "bttb_plan_set_learned", "bttb_learned_destroy",
-           "bttb_plan_workspace_bytes", "bttb_plan_destroy", "bttb_last_error")
+           "bttb_plan_autotune", "bttb_plan_workspace_bytes", "bttb_plan_destroy", "bttb_last_error")
 
 
 class BttbError(RuntimeError):
@@ -99,6 +99,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bttb_learned_train_step.argtypes = [vp, vp, vp, ci, cl, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
     lib.bttb_plan_set_learned.argtypes = [vp, vp]
     lib.bttb_learned_destroy.argtypes = [vp]
+    lib.bttb_plan_autotune.argtypes = [vp, ci, ci, pi]
     lib.bttb_plan_workspace_bytes.argtypes = [vp]
     lib.bttb_plan_workspace_bytes.restype = ctypes.c_size_t
     lib.bttb_plan_destroy.argtypes = [vp]
@@ -184,8 +185,9 @@ def bttb_get_spectrum_bin(plan, ky: int, kx: int, b: int):
     return out
 
 
-def bttb_profile(plan, enable: bool) -> None:
-    _check(load_library().bttb_profile(plan, int(bool(enable))), plan)
+def bttb_profile(plan, enable) -> None:
+    """enable: False/0 off, True/1 on, 2 also times every kernel inside captured GMRES cycles."""
+    _check(load_library().bttb_profile(plan, int(enable)), plan)
 
 
 def bttb_profile_read(plan, which: int) -> KernelStats:
@@ -284,6 +286,13 @@ def bttb_plan_set_learned(plan, learned) -> None:
 def bttb_learned_destroy(learned) -> None:
     if learned:
         _check(load_library().bttb_learned_destroy(learned))
+
+
+def bttb_plan_autotune(plan, nrhs: int = 1, reps: int = 5) -> int:
+    """FFT batch-chunk width chosen for products of nrhs columns."""
+    out = ctypes.c_int(0)
+    _check(load_library().bttb_plan_autotune(plan, nrhs, reps, ctypes.byref(out)), plan)
+    return out.value
 
 
 def bttb_plan_workspace_bytes(plan) -> int:
@@ -390,6 +399,9 @@ class Plan:
 
     def spectrum_bin(self, ky, kx):
         return bttb_get_spectrum_bin(self.handle, ky, kx, self.b)
+
+    def autotune(self, nrhs=1, reps=5):
+        return bttb_plan_autotune(self.handle, nrhs, reps)
 
     def workspace_bytes(self):
         return bttb_plan_workspace_bytes(self.handle)

@@ -3,7 +3,8 @@
 // a batch solve runs the arrays' restarted-GMRES drivers concurrently (one
 // host thread per array), so the GPU executes the arrays' captured cycle
 // graphs side by side.  An autotuner picks, per distinct (mx, my, b), the FFT
-// batch-chunk width by timing binary32 products on the plan's stream.
+// batch-chunk width by timing binary32 products on the plan's stream (the
+// same tuner serves single plans through bttb_plan_autotune).
 #include <algorithm>
 #include <map>
 #include <string>
@@ -77,55 +78,81 @@ int bttb_batch_set_generators(bttb_batch batch, int index, const void *gen, bttb
     return bttb_set_generators(batch->plans[index], gen, dtype, gen_is_host);
 }
 
+// Times `reps` binary32 products of `nrhs` columns with each FFT batch-chunk
+// width and leaves the fastest in p.fft_pmax; returns it (or a negative status).
+static int autotune_plan(Plan &p, int nrhs, int reps) {
+    const int candidates[6] = {2, 4, 8, 16, 32, 64};
+    void *x = nullptr, *y = nullptr;
+    const size_t bytes = (size_t)nrhs * p.n * sizeof(float2);
+    cudaError_t e = cudaMalloc(&x, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&y, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, bytes, p.stream);
+    if (e != cudaSuccess) {
+        cudaFree(x);
+        cudaFree(y);
+        return check_cuda(&p, e, "autotune buffers");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    int best_p = p.fft_pmax;
+    for (int cand : candidates) {
+        p.fft_pmax = cand;
+        matvec_run(&p, x, FMT_C64, p.n, y, FMT_C64, p.n, nrhs, PREC_F32);        // warm
+        cudaEventRecord(e0, p.stream);
+        for (int r = 0; r < reps; ++r) matvec_run(&p, x, FMT_C64, p.n, y, FMT_C64, p.n, nrhs, PREC_F32);
+        cudaEventRecord(e1, p.stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_p = cand;
+        }
+    }
+    p.fft_pmax = best_p;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(&p, e, "autotune");
+    return best_p;
+}
+
+int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out) {
+    if (!plan) return set_error(nullptr, BTTB_ERR_INVALID_ARG, "plan is NULL");
+    Plan &p = plan->p;
+    if (!p.have_gen || !p.ghat_hi) return set_error(&p, BTTB_ERR_NO_GENERATORS, "autotune needs the binary32 spectrum");
+    if (nrhs < 1 || nrhs > p.max_rhs) return set_error(&p, BTTB_ERR_INVALID_ARG, "nrhs out of range [1, max_rhs]");
+    const int r = autotune_plan(p, nrhs, reps < 1 ? 1 : reps);
+    if (r < 0) return r;
+    if (chosen_out) *chosen_out = r;
+    gmres_free(&p);                          // captured cycles keep the old launch shapes
+    return BTTB_OK;
+}
+
 int bttb_batch_autotune(bttb_batch batch, int reps, int *chosen_out) {
     if (!batch) return set_error(nullptr, BTTB_ERR_INVALID_ARG, "batch is NULL");
     if (reps < 1) reps = 1;
     std::map<std::tuple<int, int, int>, int> best;
-    const int candidates[5] = {2, 4, 8, 16, 32};
     for (int i = 0; i < batch->count; ++i) {
         Plan &p = batch->plans[i]->p;
         if (!p.have_gen || !p.ghat_hi) continue;
         const auto key = std::make_tuple(p.mx, p.my, p.b);
         if (best.count(key)) continue;
-        void *x = nullptr, *y = nullptr;
-        cudaError_t e = cudaMalloc(&x, p.n * sizeof(float2));
-        if (e == cudaSuccess) e = cudaMalloc(&y, p.n * sizeof(float2));
-        if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, p.n * sizeof(float2), p.stream);
-        if (e != cudaSuccess) {
-            cudaFree(x);
-            cudaFree(y);
-            return check_cuda(&p, e, "autotune buffers");
-        }
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        float best_ms = 1e30f;
-        int best_p = p.fft_pmax;
-        for (int cand : candidates) {
-            p.fft_pmax = cand;
-            matvec_run(&p, x, FMT_C64, p.n, y, FMT_C64, p.n, 1, PREC_F32);        // warm
-            cudaEventRecord(e0, p.stream);
-            for (int r = 0; r < reps; ++r) matvec_run(&p, x, FMT_C64, p.n, y, FMT_C64, p.n, 1, PREC_F32);
-            cudaEventRecord(e1, p.stream);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_p = cand;
-            }
-        }
-        p.fft_pmax = best_p;
-        best[key] = best_p;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cudaFree(x);
-        cudaFree(y);
+        const int r = autotune_plan(p, 1, reps);
+        if (r < 0) return r;
+        best[key] = r;
     }
     for (int i = 0; i < batch->count; ++i) {
         Plan &p = batch->plans[i]->p;
         const auto it = best.find(std::make_tuple(p.mx, p.my, p.b));
-        if (it != best.end()) p.fft_pmax = it->second;
+        if (it != best.end() && it->second != p.fft_pmax) {
+            p.fft_pmax = it->second;
+            gmres_free(&p);
+        }
         if (chosen_out) chosen_out[i] = p.fft_pmax;
     }
     return BTTB_OK;

@@ -30,7 +30,7 @@ constexpr int kSinkToken = 1 << 30;
 int prof_begin(Plan *p, int kid) {
     if (!p->prof) return -1;
     if (p->sink) {
-        if (kid < BTTB_K_BLOCK_PRODUCT_PREC) return -1;      // in graphs only the block product is timed
+        if (kid < BTTB_K_BLOCK_PRODUCT_PREC && p->prof < 2) return -1;   // level 1: only the block product in graphs
         Plan::GraphRec r{nullptr, nullptr, kid, 0.0, p->sink_step};
         if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess) return -1;
         // External: captured as an event-record node that timestamps every replay
@@ -70,6 +70,7 @@ static bool prec_enabled(const Plan &p, int prec) {
         case BTTB_MV_FP64: return p.ghat_hi && p.ghat_lo;
         case BTTB_MV_FP32: return p.ghat_hi != nullptr;
         case BTTB_MV_FP64_NATIVE: return p.ghat_f64 != nullptr;
+        case BTTB_MV_TC_3XTF32: return p.ghat_hi != nullptr;
         default: return false;
     }
 }
@@ -107,7 +108,8 @@ int bttb_plan_create(bttb_plan *out, int nx, int ny, int b, int max_rhs, unsigne
         return set_error(nullptr, BTTB_ERR_INVALID_ARG,
                          "sizes must satisfy 1 <= nx, ny <= 1024, 1 <= b <= 256, 1 <= max_rhs <= 4096");
     if (prec_mask == 0) prec_mask = (1u << BTTB_MV_FP64) | (1u << BTTB_MV_FP32);
-    if (prec_mask & ~((1u << BTTB_MV_FP64) | (1u << BTTB_MV_FP32) | (1u << BTTB_MV_FP64_NATIVE)))
+    if (prec_mask & ~((1u << BTTB_MV_FP64) | (1u << BTTB_MV_FP32) | (1u << BTTB_MV_FP64_NATIVE) |
+                      (1u << BTTB_MV_TC_3XTF32)))
         return set_error(nullptr, BTTB_ERR_INVALID_ARG, "unknown bit in prec_mask");
     bttb_plan h = new (std::nothrow) bttb_plan_s();
     if (!h) return set_error(nullptr, BTTB_ERR_OOM, "host allocation failed");
@@ -153,7 +155,7 @@ int bttb_plan_create(bttb_plan *out, int nx, int ny, int b, int max_rhs, unsigne
         p.bytes_held += bytes;
         return BTTB_OK;
     };
-    if (prec_mask & ((1u << BTTB_MV_FP64) | (1u << BTTB_MV_FP32)))
+    if (prec_mask & ((1u << BTTB_MV_FP64) | (1u << BTTB_MV_FP32) | (1u << BTTB_MV_TC_3XTF32)))
         if ((rc = alloc((void **)&p.ghat_hi, gplane * sizeof(float2), "spectrum hi plane")) != BTTB_OK) return bail(rc);
     if (prec_mask & (1u << BTTB_MV_FP64))
         if ((rc = alloc((void **)&p.ghat_lo, gplane * sizeof(float2), "spectrum lo plane")) != BTTB_OK) return bail(rc);
@@ -308,7 +310,7 @@ int bttb_profile(bttb_plan plan, int enable) {
         p.launches = 0;
         for (int i = 0; i < Plan::kMaxKid; ++i) p.acc_ms[i] = p.acc_bytes[i] = 0.0, p.acc_n[i] = 0;
     }
-    p.prof = enable != 0;
+    p.prof = enable < 0 ? 0 : (enable > 2 ? 2 : enable);
     return BTTB_OK;
 }
 

@@ -445,7 +445,172 @@ static int launch_contract_multi(Plan *p, const void *u, void *v, int k) {
     return BTTB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Many right-hand sides on the tensor cores (3xTF32).  The complex per-bin GEMM
+// V_k = G_k U_k is one real GEMM: the 2b x 2b embedding [Gr -Gi; Gi Gr] times
+// [Ur; Ui] (2b x k).  Every factor x is split into a TF32 head and a TF32 tail,
+// x = hi + lo, and C += hi*lo' + lo*hi' + hi*hi' accumulates in binary32, which
+// keeps binary32-level accuracy (the lo*lo' term is below binary32 rounding).
+// CTA (64-column tile, bin), b <= 64: the embedding (up to 128 x 128, zero
+// padded) and the real tile [Ur; Ui] are built in shared memory, row strides
+// = 4 (mod 32) words so that the fragment loads are conflict-free; 8 warps in a
+// 4 x 2 grid of 32 x 32 output blocks issue warp-level mma.sync m16n8k8 with
+// TF32 inputs; the result is staged in shared memory and written back as
+// complex columns.
+// ---------------------------------------------------------------------------
+constexpr int kTcTile = 64;
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Row stride (floats) of the staged real operands: >= kp, = 4 (mod 32).
+__host__ __device__ constexpr int tc_stride(int kp) { return ((kp + 27) / 32) * 32 + 4; }
+
+__global__ void __launch_bounds__(256) contract_tc_kernel(const float2 *__restrict__ G, long gbs,
+                                                          const float2 *__restrict__ U, float2 *__restrict__ V,
+                                                          long ubs, int b, int k) {
+    extern __shared__ __align__(16) float tcs[];
+    const int twob = 2 * b;
+    const int kp = (twob + 7) / 8 * 8;                   // K padded to the MMA depth
+    const int st = tc_stride(kp);
+    float *As = tcs;                                      // 128 rows x st (row r, column q')
+    float *Bs = tcs + 128 * st;                           // kTcTile rows (columns n) x st (index q')
+    const long bin = blockIdx.y;
+    const int c0 = blockIdx.x * kTcTile;
+    const int ncb = min(kTcTile, k - c0);
+    pdl_wait();
+    // zero the padding, then scatter the embedding and the tile
+    for (int i = threadIdx.x; i < 128 * st; i += blockDim.x) {
+        const int r = i / st, q = i - r * st;
+        if (r >= twob || q >= twob) As[i] = 0.f;
+    }
+    for (int i = threadIdx.x; i < kTcTile * st; i += blockDim.x) {
+        const int n = i / st, q = i - n * st;
+        if (n >= ncb || q >= twob) Bs[i] = 0.f;
+    }
+    const float2 *gsrc = G + bin * gbs;
+    for (int i = threadIdx.x; i < b * b; i += blockDim.x) {
+        const int q = i / b, pr = i - q * b;              // column-major: entry (pr, q)
+        const float2 g = gsrc[i];
+        As[pr * st + q] = g.x;
+        As[pr * st + q + b] = -g.y;
+        As[(pr + b) * st + q] = g.y;
+        As[(pr + b) * st + q + b] = g.x;
+    }
+    const float2 *usrc = U + bin * ubs + (long)c0 * b;
+    for (int i = threadIdx.x; i < ncb * b; i += blockDim.x) {
+        const int n = i / b, q = i - n * b;
+        const float2 u = usrc[i];
+        Bs[n * st + q] = u.x;
+        Bs[n * st + q + b] = u.y;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int wm = warp >> 1, wn = warp & 1;
+    float acc[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+    const bool live = wm * 32 < twob;                     // warps whose rows are all padding skip the MMAs
+    if (live) {
+        for (int kb = 0; kb < kp; kb += 8) {
+            uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const float *ar = As + (wm * 32 + mt * 16 + gid) * st + kb + tig;
+                split_tf32(ar[0], ah[mt][0], al[mt][0]);
+                split_tf32(ar[8 * st], ah[mt][1], al[mt][1]);
+                split_tf32(ar[4], ah[mt][2], al[mt][2]);
+                split_tf32(ar[8 * st + 4], ah[mt][3], al[mt][3]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const float *br = Bs + (wn * 32 + nt * 8 + gid) * st + kb + tig;
+                split_tf32(br[0], bh[nt][0], bl[nt][0]);
+                split_tf32(br[4], bh[nt][1], bl[nt][1]);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    mma_tf32(acc[mt][nt], ah[mt], bl[nt]);
+                    mma_tf32(acc[mt][nt], al[mt], bh[nt]);
+                    mma_tf32(acc[mt][nt], ah[mt], bh[nt]);
+                }
+        }
+    }
+    __syncthreads();                                      // operands consumed: reuse the space for C
+    float *Cs = tcs;                                      // kTcTile columns x (2b + 1)
+    const int cst = twob + 1;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int r = wm * 32 + mt * 16 + gid, n = wn * 32 + nt * 8 + 2 * tig;
+            if (r < twob) {
+                Cs[n * cst + r] = acc[mt][nt][0];
+                Cs[(n + 1) * cst + r] = acc[mt][nt][1];
+            }
+            if (r + 8 < twob) {
+                Cs[n * cst + r + 8] = acc[mt][nt][2];
+                Cs[(n + 1) * cst + r + 8] = acc[mt][nt][3];
+            }
+        }
+    __syncthreads();
+    pdl_trigger();
+    float2 *vdst = V + bin * ubs + (long)c0 * b;
+    for (int i = threadIdx.x; i < ncb * b; i += blockDim.x) {
+        const int n = i / b, pr = i - n * b;
+        vdst[i] = make_float2(Cs[n * cst + pr], Cs[n * cst + pr + b]);
+    }
+}
+
+static size_t contract_tc_smem(int b) {
+    const int kp = (2 * b + 7) / 8 * 8;
+    return (size_t)(128 + kTcTile) * tc_stride(kp) * sizeof(float);
+}
+
+static int launch_contract_tc(Plan *p, const void *u, void *v, int k) {
+    const int b = p->b;
+    if (!p->ghat_hi) return set_error(p, BTTB_ERR_INVALID_ARG, "plan does not keep the binary32 spectrum");
+    const size_t smem = contract_tc_smem(b);
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)p->smem_optin);
+    if (e != cudaSuccess) return check_cuda(p, e, "tensor-core product smem attribute");
+    const dim3 grid((k + kTcTile - 1) / kTcTile, (unsigned)p->bins);
+    const int tok = prof_begin(p, BTTB_K_BLOCK_PRODUCT_PREC + BTTB_MV_TC_3XTF32);
+    e = launch_pdl(contract_tc_kernel, grid, dim3(256), smem, p->stream, (const float2 *)p->ghat_hi, p->gbs,
+                   (const float2 *)u, (float2 *)v, p->ubs, b, k);
+    count_launch(p);
+    prof_end(p, tok, (double)p->bins * ((double)b * b * 8 + 2.0 * k * b * 8));
+    if (e != cudaSuccess) return check_cuda(p, e, "tensor-core product launch");
+    return BTTB_OK;
+}
+
 int contract_launch(Plan *p, int prec, const void *u, void *v, int k, const int *active) {
+    // Tensor cores for a real per-bin GEMM (many columns, b <= 64); a GEMV (few columns) has no reuse.
+    if (prec == PREC_TC) {
+        if (k >= kTcMinCols && p->b <= 64) return launch_contract_tc(p, u, v, k);
+        prec = PREC_F32;
+    }
     // Many right-hand sides in binary32: a tiled per-bin GEMM instead of k/4 passes over the spectrum.
     if (prec == PREC_F32 && k > 8 && p->b <= 128) return launch_contract_multi(p, u, v, k);
     switch (prec) {

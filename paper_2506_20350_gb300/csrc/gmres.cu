@@ -53,7 +53,7 @@ struct GmresWork {
     cudaGraphExec_t cycle_exec = nullptr;
     int graph_inner = -1;
     int graph_pc = -1;
-    bool graph_prof = false;
+    int graph_prof = 0;
     long launches_per_cycle = 0;
     std::vector<Plan::GraphRec> grecs;
 };
@@ -197,17 +197,32 @@ __global__ void cycle_start_kernel(const double *beta2, float4 *gv, double *inv_
     }
 }
 
-// One Givens step of column c by one warp, in double-float.  The lanes stage
-// the Hessenberg column and the earlier rotations in shared memory (`wsm`,
-// 3m+2 float4), lane 0 applies the rotations in order.  Returns (on every
-// lane) whether the column continues.
+// Shuffle a double-float complex value (8 floats) within the warp.
+__device__ __forceinline__ dfc shfl_up_dfc(dfc v, int d) {
+    return dfc{df{__shfl_up_sync(0xffffffffu, v.re.hi, d), __shfl_up_sync(0xffffffffu, v.re.lo, d)},
+               df{__shfl_up_sync(0xffffffffu, v.im.hi, d), __shfl_up_sync(0xffffffffu, v.im.lo, d)}};
+}
+__device__ __forceinline__ dfc shfl_dfc(dfc v, int src) {
+    return dfc{df{__shfl_sync(0xffffffffu, v.re.hi, src), __shfl_sync(0xffffffffu, v.re.lo, src)},
+               df{__shfl_sync(0xffffffffu, v.im.hi, src), __shfl_sync(0xffffffffu, v.im.lo, src)}};
+}
+
+// One Givens step of column c by one warp, in double-float.  The earlier
+// rotations G_0 .. G_{j-1} act on the new Hessenberg column h as
+//   out_i = c_i t_i + s_i h_{i+1},   t_{i+1} = -conj(s_i) t_i + c_i h_{i+1},
+// t_0 = h_0, out_j = t_j: an affine recurrence for t, so the warp composes the
+// maps t -> alpha t + beta with a prefix scan (each lane first composes its own
+// run of consecutive rotations) instead of applying them one after another.
+// Lane 0 then forms the new rotation.  Returns (on every lane) whether the
+// column continues.  Scratch `wsm`: 4m+4 float4.
 __device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const float4 *hacc, double beta2,
                              float2 *cs, float4 *sn, float4 *gv, int *active, int *steps, int *bdown,
                              const int *mlimit, const double *target, double *inv_beta, int *err) {
     const int lane = threadIdx.x & 31;
     float4 *hcol = wsm;                                         // m+1 entries
     float4 *snw = hcol + (m + 1);                               // m entries
-    float2 *csw = reinterpret_cast<float2 *>(snw + m);          // m entries
+    float2 *csw = reinterpret_cast<float2 *>(snw + m);          // m entries (m float4 reserved)
+    float4 *hout = snw + 2 * m;                                 // m+1 entries
     float4 *Hc = H + (long)c * (m + 1) * m;
     const float4 *ha = hacc + (long)c * (m + 1);
     float zn2 = 0.f;
@@ -223,6 +238,46 @@ __device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const 
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) zn2 += __shfl_xor_sync(0xffffffffu, zn2, off);
     __syncwarp();
+    if (j > 0) {
+        const int per = (j + 31) / 32;                          // rotations per lane
+        const int i0 = min(lane * per, j), i1 = min(i0 + per, j);
+        const dfc zero{df{0.f, 0.f}, df{0.f, 0.f}};
+        dfc al{df{1.f, 0.f}, df{0.f, 0.f}}, be = zero;          // composition of this lane's maps
+        for (int i = i0; i < i1; ++i) {
+            const dfc si = dfc_load(*reinterpret_cast<const cdf *>(&snw[i]));
+            const df ci{csw[i].x, csw[i].y};
+            const dfc hn = dfc_load(*reinterpret_cast<const cdf *>(&hcol[i + 1]));
+            const dfc ai = dfc_neg(dfc_conj(si));
+            be = dfc_add(dfc_mul(ai, be), dfc_scale(hn, ci));
+            al = dfc_mul(ai, al);
+        }
+        // inclusive scan over lanes: lane L holds the maps of lanes 0..L composed
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const dfc ao = shfl_up_dfc(al, d), bo = shfl_up_dfc(be, d);
+            if (lane >= d) {
+                be = dfc_add(dfc_mul(al, bo), be);
+                al = dfc_mul(al, ao);
+            }
+        }
+        // t at the start of this lane's run: the exclusive prefix applied to h_0
+        dfc ea = shfl_up_dfc(al, 1), eb = shfl_up_dfc(be, 1);
+        const dfc h0 = dfc_load(*reinterpret_cast<const cdf *>(&hcol[0]));
+        dfc t = lane == 0 ? h0 : dfc_add(dfc_mul(ea, h0), eb);
+        for (int i = i0; i < i1; ++i) {
+            const dfc si = dfc_load(*reinterpret_cast<const cdf *>(&snw[i]));
+            const df ci{csw[i].x, csw[i].y};
+            const dfc hn = dfc_load(*reinterpret_cast<const cdf *>(&hcol[i + 1]));
+            *reinterpret_cast<cdf *>(&hout[i]) = dfc_store(dfc_add(dfc_scale(t, ci), dfc_mul(si, hn)));
+            t = dfc_add(dfc_mul(dfc_neg(dfc_conj(si)), t), dfc_scale(hn, ci));
+        }
+        // t_j from the full composition (lane 31)
+        const dfc ta = shfl_dfc(al, 31), tb = shfl_dfc(be, 31);
+        __syncwarp();
+        for (int i = lane; i < j; i += 32) hcol[i] = hout[i];
+        if (lane == 0) *reinterpret_cast<cdf *>(&hcol[j]) = dfc_store(dfc_add(dfc_mul(ta, h0), tb));
+        __syncwarp();
+    }
     int cont = 0;
     if (lane == 0) {
         const df beta = df_sqrt(df_from_double(fmax(beta2, 0.0)));
@@ -231,17 +286,6 @@ __device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const 
             atomicOr(err, DEVERR_NONFINITE);
             active[c] = 0;
         } else {
-            for (int i = 0; i < j; ++i) {
-                const dfc a0 = dfc_load(*reinterpret_cast<const cdf *>(&hcol[i]));
-                const dfc a1 = dfc_load(*reinterpret_cast<const cdf *>(&hcol[i + 1]));
-                const dfc si = dfc_load(*reinterpret_cast<const cdf *>(&snw[i]));
-                const df ci{csw[i].x, csw[i].y};
-                // (a0, a1) <- (c a0 + s a1, -conj(s) a0 + c a1)
-                const dfc n0 = dfc_add(dfc_scale(a0, ci), dfc_mul(si, a1));
-                const dfc n1 = dfc_sub(dfc_scale(a1, ci), dfc_mul(dfc_conj(si), a0));
-                *reinterpret_cast<cdf *>(&hcol[i]) = dfc_store(n0);
-                *reinterpret_cast<cdf *>(&hcol[i + 1]) = dfc_store(n1);
-            }
             const dfc a = dfc_load(*reinterpret_cast<const cdf *>(&hcol[j]));
             const df aa2 = dfc_abs2(a);
             const df rho = df_sqrt(df_add(aa2, df_mul(beta, beta)));
@@ -305,20 +349,24 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter, int total) {
     return s_last != 0;
 }
 
-// Gram-Schmidt dots: CTA (blk, ich, c) covers entries [blk*kDotNE, +kDotNE) of
-// column c; warp w takes basis vector i = ich*kDotIW + w.  CTAs whose vectors
-// are all beyond j exit without arriving; the last of the rest sums the
-// partials in block order: mode 0 sets hco = hacc = h, mode 1 sets hco = h and
-// adds h to hacc.
-constexpr int kDotNE = 1024;
+// Gram-Schmidt dots: the grid is sized for step j (static in the captured
+// graph): warp t of the launch takes work item t = (basis vector i, chunk of
+// kDotNE entries), i = t / nblk_dot, so the warps of a CTA read consecutive
+// chunks of one vector; a lane issues all of its loads before it accumulates.
+// Every CTA of an active column arrives on the column's counter; the last one
+// sums the partials in chunk order: mode 0 sets hco = hacc = h, mode 1 sets
+// hco = h and adds h to hacc.
+constexpr int kDotNE = 256;
 constexpr int kDotIW = 8;
+constexpr int kDotPL = kDotNE / 32;         // entries per lane
 
 struct StepArgs {
     const float4 *Vb;      // basis [i][c][n]
     float4 *W;             // [c][n]
     long n, bs_i, bs_c;
     int m, k;
-    int nblk_dot, ich;     // dots grid
+    int dot_sub;           // kDotNE-entry pieces per dots chunk (1, more for very long vectors)
+    int nblk_dot, ich;     // dots: chunks per vector; CTAs of the launch
     int nblk_vec;          // update / scale grid (kStepNB entries per CTA)
     float4 *part;          // [c][m+1][nblk_dot] (dots), reused as [c][nblk_vec] (norm)
     long pstride;          // (m+1)*max(nblk_dot, nblk_vec) per column
@@ -341,70 +389,73 @@ struct StepArgs {
 // accuracy); pass 1 is double-float throughout.
 __global__ void __launch_bounds__(kDotIW * 32) step_dots_kernel(const StepArgs a, int mode, unsigned *counter,
                                                                  int j) {
-    const int blk = blockIdx.x, c = blockIdx.z;
+    const int c = blockIdx.y;
     pdl_wait();
     if (!a.active[c]) return;
     const int cnt = j + 1;
-    const int nich = (cnt + kDotIW - 1) / kDotIW;
-    if ((int)blockIdx.y >= nich) return;                  // no vector of this CTA is in use
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.y * kDotIW + warp;
-    const long n0 = (long)blk * kDotNE;
-    const int len = (int)min((long)kDotNE, a.n - n0);
+    const long t = (long)blockIdx.x * kDotIW + warp;
+    const int i = (int)(t / a.nblk_dot), blk = (int)(t - (long)i * a.nblk_dot);
     float4 *part = a.part + (long)c * a.pstride;
-    if (i < cnt && mode == 0) {
-        const float4 *bv = a.Vb + (long)i * a.bs_i + (long)c * a.bs_c + n0;
-        const float4 *xv = a.W + (long)c * a.n + n0;
-        float re = 0.f, im = 0.f, re1 = 0.f, im1 = 0.f;
-#pragma unroll 8
-        for (int e = lane; e < len; e += 64) {
-            const float4 v = bv[e], x = xv[e];
-            re = fmaf(v.x, x.x, fmaf(v.y, x.y, re));
-            im = fmaf(v.x, x.y, fmaf(-v.y, x.x, im));
-            if (e + 32 < len) {
-                const float4 v2 = bv[e + 32], x2 = xv[e + 32];
-                re1 = fmaf(v2.x, x2.x, fmaf(v2.y, x2.y, re1));
-                im1 = fmaf(v2.x, x2.y, fmaf(-v2.y, x2.x, im1));
-            }
-        }
-        re += re1;
-        im += im1;
+    if (i < cnt) {
+        float re = 0.f, im = 0.f, re1 = 0.f, im1 = 0.f;                       // mode 0
+        dacc re0{0.f, 0.f}, im0{0.f, 0.f}, dre1{0.f, 0.f}, dim1{0.f, 0.f};    // mode 1
+        for (int sc = 0; sc < a.dot_sub; ++sc) {
+            const long n0 = ((long)blk * a.dot_sub + sc) * kDotNE;
+            const int len = (int)max(0L, min((long)kDotNE, a.n - n0));
+            const float4 *bv = a.Vb + (long)i * a.bs_i + (long)c * a.bs_c + n0;
+            const float4 *xv = a.W + (long)c * a.n + n0;
+            float4 v[kDotPL], x[kDotPL];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            re += __shfl_xor_sync(0xffffffffu, re, off);
-            im += __shfl_xor_sync(0xffffffffu, im, off);
-        }
-        if (lane == 0) part[(long)i * a.nblk_dot + blk] = make_float4(re, im, 0.f, 0.f);
-    } else if (i < cnt) {
-        const float4 *bv = a.Vb + (long)i * a.bs_i + (long)c * a.bs_c + n0;
-        const float4 *xv = a.W + (long)c * a.n + n0;
-        dacc re0{0.f, 0.f}, im0{0.f, 0.f}, re1{0.f, 0.f}, im1{0.f, 0.f};
-#pragma unroll 4
-        for (int e = lane; e < len; e += 64) {
-            const float4 v = bv[e], x = xv[e];
-            dacc_mac(re0, v.x, v.z, x.x, x.z);
-            dacc_mac(re0, v.y, v.w, x.y, x.w);
-            dacc_mac(im0, v.x, v.z, x.y, x.w);
-            dacc_mac(im0, -v.y, -v.w, x.x, x.z);
-            if (e + 32 < len) {
-                const float4 v2 = bv[e + 32], x2 = xv[e + 32];
-                dacc_mac(re1, v2.x, v2.z, x2.x, x2.z);
-                dacc_mac(re1, v2.y, v2.w, x2.y, x2.w);
-                dacc_mac(im1, v2.x, v2.z, x2.y, x2.w);
-                dacc_mac(im1, -v2.y, -v2.w, x2.x, x2.z);
+            for (int q = 0; q < kDotPL; ++q) {
+                const int e = lane + 32 * q;
+                v[q] = e < len ? bv[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                x[q] = e < len ? xv[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (mode == 0) {
+#pragma unroll
+                for (int q = 0; q < kDotPL; q += 2) {
+                    re = fmaf(v[q].x, x[q].x, fmaf(v[q].y, x[q].y, re));
+                    im = fmaf(v[q].x, x[q].y, fmaf(-v[q].y, x[q].x, im));
+                    re1 = fmaf(v[q + 1].x, x[q + 1].x, fmaf(v[q + 1].y, x[q + 1].y, re1));
+                    im1 = fmaf(v[q + 1].x, x[q + 1].y, fmaf(-v[q + 1].y, x[q + 1].x, im1));
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kDotPL; q += 2) {
+                    dacc_mac(re0, v[q].x, v[q].z, x[q].x, x[q].z);
+                    dacc_mac(re0, v[q].y, v[q].w, x[q].y, x[q].w);
+                    dacc_mac(im0, v[q].x, v[q].z, x[q].y, x[q].w);
+                    dacc_mac(im0, -v[q].y, -v[q].w, x[q].x, x[q].z);
+                    dacc_mac(dre1, v[q + 1].x, v[q + 1].z, x[q + 1].x, x[q + 1].z);
+                    dacc_mac(dre1, v[q + 1].y, v[q + 1].w, x[q + 1].y, x[q + 1].w);
+                    dacc_mac(dim1, v[q + 1].x, v[q + 1].z, x[q + 1].y, x[q + 1].w);
+                    dacc_mac(dim1, -v[q + 1].y, -v[q + 1].w, x[q + 1].x, x[q + 1].z);
+                }
             }
         }
-        dacc_add(re0, re1);
-        dacc_add(im0, im1);
-        warp_reduce_dacc(re0);
-        warp_reduce_dacc(im0);
-        if (lane == 0) {
-            const df r = dacc_result(re0), q = dacc_result(im0);
-            part[(long)i * a.nblk_dot + blk] = make_float4(r.hi, q.hi, r.lo, q.lo);
+        if (mode == 0) {
+            re += re1;
+            im += im1;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, off);
+                im += __shfl_xor_sync(0xffffffffu, im, off);
+            }
+            if (lane == 0) part[(long)i * a.nblk_dot + blk] = make_float4(re, im, 0.f, 0.f);
+        } else {
+            dacc_add(re0, dre1);
+            dacc_add(im0, dim1);
+            warp_reduce_dacc(re0);
+            warp_reduce_dacc(im0);
+            if (lane == 0) {
+                const df r = dacc_result(re0), q = dacc_result(im0);
+                part[(long)i * a.nblk_dot + blk] = make_float4(r.hi, q.hi, r.lo, q.lo);
+            }
         }
     }
     pdl_trigger();
-    if (!arrive_last(counter + c, a.nblk_dot * nich)) return;
+    if (!arrive_last(counter + c, (int)gridDim.x)) return;
     for (int ii = warp; ii < cnt; ii += kDotIW) {
         const float4 *pp = part + (long)ii * a.nblk_dot;
         dacc re{0.f, 0.f}, im{0.f, 0.f};
@@ -430,18 +481,29 @@ __global__ void __launch_bounds__(kDotIW * 32) step_dots_kernel(const StepArgs a
     }
 }
 
-// w -= sum_{i<cnt} B_i h_i for this thread's entry (compensated), returns the new value.
+// w -= sum_{i<cnt} B_i h_i for this thread's entry (compensated), returns the
+// new value.  The basis entries are loaded UB at a time, all loads of a batch
+// issued before its accumulations: a deep batch when few columns leave the GPU
+// short of warps, a shallow one (fewer registers, more warps) otherwise.
+template <int UB>
 __device__ __forceinline__ float4 cta_update_entry(const float4 *basis, long bs_i, long boff, const float4 *hs,
                                                    int cnt, float4 x) {
     dacc re{x.x, x.z}, im{x.y, x.w};
-#pragma unroll 8
-    for (int i = 0; i < cnt; ++i) {
-        const float4 v = basis[(long)i * bs_i + boff];
-        const float4 h = hs[i];                     // already negated
-        dacc_mac(re, v.x, v.z, h.x, h.z);
-        dacc_mac(re, -v.y, -v.w, h.y, h.w);
-        dacc_mac(im, v.x, v.z, h.y, h.w);
-        dacc_mac(im, v.y, v.w, h.x, h.z);
+    for (int i0 = 0; i0 < cnt; i0 += UB) {
+        float4 v[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u)
+            if (i0 + u < cnt) v[u] = basis[(long)(i0 + u) * bs_i + boff];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            if (i0 + u < cnt) {
+                const float4 h = hs[i0 + u];              // already negated
+                dacc_mac(re, v[u].x, v[u].z, h.x, h.z);
+                dacc_mac(re, -v[u].y, -v[u].w, h.y, h.w);
+                dacc_mac(im, v[u].x, v[u].z, h.y, h.w);
+                dacc_mac(im, v[u].y, v[u].w, h.x, h.z);
+            }
+        }
     }
     const df r = dacc_result(re), q = dacc_result(im);
     return make_float4(r.hi, q.hi, r.lo, q.lo);
@@ -449,8 +511,9 @@ __device__ __forceinline__ float4 cta_update_entry(const float4 *basis, long bs_
 
 // w -= V h (one entry per thread).  With `last` set (second pass) the kernel
 // also forms ||w||^2 and the last CTA of the column runs its Givens step.
+template <int UB>
 __global__ void __launch_bounds__(kStepNB) step_update_kernel(const StepArgs a, int last, int j) {
-    extern __shared__ __align__(16) float4 dyn[];          // hs: m+1, then Givens scratch 3m+2
+    extern __shared__ __align__(16) float4 dyn[];          // hs: m+1, then Givens scratch 4m+4
     __shared__ dacc red[kStepNB / 32];
     const int c = blockIdx.y, blk = blockIdx.x;
     pdl_wait();
@@ -466,7 +529,7 @@ __global__ void __launch_bounds__(kStepNB) step_update_kernel(const StepArgs a, 
     dacc nrm{0.f, 0.f};
     if (e < a.n) {
         float4 &wv = a.W[(long)c * a.n + e];
-        const float4 x = cta_update_entry(a.Vb, a.bs_i, (long)c * a.bs_c + e, hs, cnt, wv);
+        const float4 x = cta_update_entry<UB>(a.Vb, a.bs_i, (long)c * a.bs_c + e, hs, cnt, wv);
         wv = x;
         dacc_mac(nrm, x.x, x.z, x.x, x.z);
         dacc_mac(nrm, x.y, x.w, x.y, x.w);
@@ -703,8 +766,10 @@ static int arnoldi_step(Plan *p, GmresWork *g, int inner, int j) {
     a.bs_c = n;
     a.m = m;
     a.k = k;
-    a.nblk_dot = (int)((n + kDotNE - 1) / kDotNE);
-    a.ich = (m + 1 + kDotIW - 1) / kDotIW;
+    a.dot_sub = 1;
+    while ((n + (long)kDotNE * a.dot_sub - 1) / ((long)kDotNE * a.dot_sub) > 4096) a.dot_sub <<= 1;
+    a.nblk_dot = (int)((n + (long)kDotNE * a.dot_sub - 1) / ((long)kDotNE * a.dot_sub));
+    a.ich = (int)(((long)a.nblk_dot * (j + 1) + kDotIW - 1) / kDotIW);
     a.nblk_vec = g->nblk;
     a.part = g->part;
     a.pstride = std::max((long)(m + 1) * a.nblk_dot, (long)g->nblk);
@@ -726,16 +791,19 @@ static int arnoldi_step(Plan *p, GmresWork *g, int inner, int j) {
     a.mlimit = g->mlimit;
     a.target = g->target;
     a.err = p->d_err;
-    const dim3 dgrid(a.nblk_dot, a.ich, k), vgrid(a.nblk_vec, k);
+    const dim3 dgrid(a.ich, k), vgrid(a.nblk_vec, k);
     const size_t hs_bytes = (size_t)(m + 1) * sizeof(float4);
-    const size_t upd_smem = hs_bytes + (size_t)(3 * m + 2) * sizeof(float4);
+    const size_t upd_smem = hs_bytes + (size_t)(4 * m + 4) * sizeof(float4);
     int tok;
     for (int pass = 0; pass < 2; ++pass) {
         tok = prof_begin(p, 3);
         launch_pdl(step_dots_kernel, dgrid, dim3(kDotIW * 32), 0, st, a, pass, pass == 0 ? a.cnt_a : a.cnt_b, j);
         prof_end(p, tok, 0.0);
         tok = prof_begin(p, pass == 0 ? 4 : 5);
-        launch_pdl(step_update_kernel, vgrid, dim3(kStepNB), upd_smem, st, a, pass, j);
+        if ((long)a.nblk_vec * k < 4L * p->nsm)
+            launch_pdl(step_update_kernel<16>, vgrid, dim3(kStepNB), upd_smem, st, a, pass, j);
+        else
+            launch_pdl(step_update_kernel<4>, vgrid, dim3(kStepNB), upd_smem, st, a, pass, j);
         prof_end(p, tok, 0.0);
     }
     tok = prof_begin(p, 6);
@@ -902,7 +970,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
                     mlim[c] = std::min(m, max_iters - total[c]);
                     const double b0 = std::sqrt(b2[c]);
                     double t = 0.9 * o->tol * vnorm[c];
-                    if (inner == BTTB_MV_FP32) t = std::max(t, 1e-5 * b0);
+                    if (inner == BTTB_MV_FP32 || inner == BTTB_MV_TC_3XTF32) t = std::max(t, 1e-5 * b0);
                     tgt[c] = t;
                     cycles[c] += 1;
                 }
@@ -936,7 +1004,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
                 act[0] = 1;
                 mlim[0] = std::min(m, max_iters - total[0]);
                 double t = 0.9 * o->tol * (std::isfinite(vmin) ? vmin : 0.0);
-                if (inner == BTTB_MV_FP32) t = std::max(t, 1e-5 * std::sqrt(f2));
+                if (inner == BTTB_MV_FP32 || inner == BTTB_MV_TC_3XTF32) t = std::max(t, 1e-5 * std::sqrt(f2));
                 tgt[0] = t;
                 for (int c = 0; c < k; ++c) cycles[c] += 1;
                 e = cudaMemcpyAsync(g->beta2, &f2, sizeof(double), cudaMemcpyHostToDevice, st);

@@ -49,7 +49,12 @@ struct FftPass {
     int P, log2P;                 // inner chunk per CTA (power of two)
 };
 
-enum Prec { PREC_DF64 = BTTB_MV_FP64, PREC_F32 = BTTB_MV_FP32, PREC_F64N = BTTB_MV_FP64_NATIVE };
+enum Prec { PREC_DF64 = BTTB_MV_FP64, PREC_F32 = BTTB_MV_FP32, PREC_F64N = BTTB_MV_FP64_NATIVE,
+            PREC_TC = BTTB_MV_TC_3XTF32 };
+// Columns from which BTTB_MV_TC_3XTF32 runs the block product on the tensor cores.
+constexpr int kTcMinCols = 16;
+// FFT passes and vector format of a product precision (the tensor-core product is binary32 around the GEMM).
+inline int fft_prec_of(int prec) { return prec == PREC_TC ? PREC_F32 : prec; }
 
 struct GmresWork;
 struct Learned;
@@ -89,7 +94,7 @@ struct Plan {
 
     // Profiling (bttb_profile): event pairs around timed launches, launch count.
     struct ProfRec { int ev0, ev1, kid; double bytes; };
-    bool prof = false;
+    int prof = 0;                 // 0 off, 1 block product + FFT (outside graphs), 2 every timed kernel
     std::vector<cudaEvent_t> ev_pool;
     int ev_used = 0;
     std::vector<ProfRec> recs;

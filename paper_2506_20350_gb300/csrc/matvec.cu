@@ -23,12 +23,15 @@
 
 namespace bttb {
 
-static int native_of(int prec) { return prec == PREC_F64N ? FMT_C128 : (prec == PREC_F32 ? FMT_C64 : FMT_CDF); }
+static int native_of(int prec) {
+    return prec == PREC_F64N ? FMT_C128 : ((prec == PREC_F32 || prec == PREC_TC) ? FMT_C64 : FMT_CDF);
+}
 
 int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int nrhs, int prec,
                const int *in_sel, long in_sel_stride, const double *in_scale, const int *active) {
     const int nx = p->nx, ny = p->ny, b = p->b, mx = p->mx, my = p->my;
     const int NF = native_of(prec);
+    const int fprec = fft_prec_of(prec);
     const long plane = (long)ny * mx * b;
     int rc;
 
@@ -39,7 +42,7 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     a.in_sel = in_sel; a.in_sel_stride = in_sel_stride; a.in_scale = in_scale; a.active = active;
     a.O = ny; a.pdim = b; a.ncols = nrhs;
     a.nin = nx; a.nout = mx; a.M = mx;
-    if ((rc = fft_pass_launch(p, a, prec, xfmt, NF, false)) != BTTB_OK) return rc;
+    if ((rc = fft_pass_launch(p, a, fprec, xfmt, NF, false)) != BTTB_OK) return rc;
 
     FftPass c{};
     c.in = p->wsB; c.out = p->wsA;
@@ -47,7 +50,7 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     c.out_cs = b; c.out_os = p->ubs; c.out_ns = (long)mx * p->ubs;
     c.O = mx; c.pdim = b; c.ncols = nrhs; c.active = active;
     c.nin = ny; c.nout = my; c.M = my;
-    if ((rc = fft_pass_launch(p, c, prec, NF, NF, false)) != BTTB_OK) return rc;
+    if ((rc = fft_pass_launch(p, c, fprec, NF, NF, false)) != BTTB_OK) return rc;
 
     if ((rc = contract_launch(p, prec, p->wsA, p->wsB, nrhs, active)) != BTTB_OK) return rc;
 
@@ -57,7 +60,7 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     d.out_cs = plane; d.out_os = b; d.out_ns = (long)mx * b;
     d.O = mx; d.pdim = b; d.ncols = nrhs; d.active = active;
     d.nin = my; d.nout = ny; d.M = my;
-    if ((rc = fft_pass_launch(p, d, prec, NF, NF, true)) != BTTB_OK) return rc;
+    if ((rc = fft_pass_launch(p, d, fprec, NF, NF, true)) != BTTB_OK) return rc;
 
     FftPass e{};
     e.in = p->wsA; e.out = y;
@@ -65,7 +68,7 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     e.out_cs = ldy; e.out_os = (long)nx * b; e.out_ns = b;
     e.O = ny; e.pdim = b; e.ncols = nrhs; e.active = active;
     e.nin = mx; e.nout = nx; e.M = mx;
-    return fft_pass_launch(p, e, prec, NF, yfmt, true);
+    return fft_pass_launch(p, e, fprec, NF, yfmt, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -135,12 +138,18 @@ template <int INF, int OUTF>
 static int bj_launch(Plan *p, const void *x, long ldx, void *z, long ldz, int nrhs, const int *in_sel,
                      long in_sel_stride, const int *active) {
     const int b = p->b, ncells = p->nx * p->ny;
-    int cpb = (8 * 1024) / b;                                  // cells per CTA
+    // Cells per CTA: at most 8192/b, and few enough that the launch fills every SM
+    // twice over; CTAs with a handful of cells read R_0^{-1} through L1 instead of
+    // staging all b*b entries.
+    int cpb = (8 * 1024) / b;
+    const long want = 2L * p->nsm;
+    const long per = ((long)ncells * nrhs + want - 1) / want;
+    if (cpb > per) cpb = (int)per;
     if (cpb < 1) cpb = 1;
     if (cpb > ncells) cpb = ncells;
     const size_t xs_bytes = (size_t)cpb * (b + 1) * sizeof(float2);
     const size_t r_bytes = (size_t)b * b * sizeof(float2);
-    const int in_smem = (xs_bytes + r_bytes <= 160 * 1024) ? 1 : 0;
+    const int in_smem = (cpb >= 16 && xs_bytes + r_bytes <= 160 * 1024) ? 1 : 0;
     const size_t smem = xs_bytes + (in_smem ? r_bytes : 0);
     auto kern = bj_apply_kernel<INF, OUTF>;
     if (smem > 48 * 1024) {

@@ -67,7 +67,7 @@ def test_autotune_keeps_results(bt):
     vs = [torch.from_numpy(v).cuda() for _, v in probs]
     before, _, _ = batch.solve(vs, tol=1e-9, restart=20, inner=bt.BTTB_MV_FP32)
     widths = batch.autotune(reps=2)
-    assert len(widths) == len(SPECS) and all(w in (2, 4, 8, 16, 32) for w in widths)
+    assert len(widths) == len(SPECS) and all(w in (2, 4, 8, 16, 32, 64) for w in widths)
     after, rc, _ = batch.solve(vs, tol=1e-9, restart=20, inner=bt.BTTB_MV_FP32)
     assert rc == bt.BTTB_OK
     for a, c in zip(before, after):

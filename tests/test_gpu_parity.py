@@ -106,6 +106,33 @@ def test_multi_rhs_product_binary32(bt, nx, ny, b, k):
     _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64).cpu().numpy(), ref, FP64_TOL, "multi-RHS df64")
 
 
+@pytest.mark.parametrize("nx,ny,b,k", [(5, 4, 60, 16), (6, 5, 60, 70), (4, 3, 64, 130), (7, 6, 12, 65),
+                                        (3, 5, 1, 33), (4, 4, 37, 20), (5, 3, 96, 40), (4, 4, 60, 9)])
+def test_tensor_core_product(bt, nx, ny, b, k):
+    """BTTB_MV_TC_3XTF32: the per-bin GEMM on the tensor cores (3xTF32) for >= 16 columns and b <= 64,
+    binary32 elsewhere (b = 96, k = 9); binary32-level accuracy either way."""
+    gen = arrays.random_generator_blocks(nx, ny, b, seed=400 + b + k)
+    plan = bt.Plan(nx, ny, b, max_rhs=k, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_TC_3XTF32))
+    plan.set_generators(gen)
+    x = _rand(np.random.default_rng(8), k, plan.n)
+    ref = oracle.matvec(gen, x.T).T
+    y = plan.matvec(_dev(x.astype(np.complex64)), prec=bt.BTTB_MV_TC_3XTF32).cpu().numpy()
+    _check(y, ref, FP32_TOL, "tensor-core product")
+
+
+def test_tensor_core_ir_solve(bt):
+    """GMRES-IR with tensor-core inner products reaches the FP64-class residual on every column."""
+    nx, ny, b = 8, 6, 12
+    gen = arrays.generator_blocks(nx, ny, b, seed=32)
+    v = arrays.port_excitations(nx, ny, b).T.copy()          # 48 columns
+    plan = bt.Plan(nx, ny, b, max_rhs=v.shape[0], prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_TC_3XTF32))
+    plan.set_generators(gen)
+    sol, rc, res = plan.solve(_dev(v), tol=1e-8, restart=30, inner=bt.BTTB_MV_TC_3XTF32)
+    assert rc == bt.BTTB_OK, bt.bttb_last_error()
+    rr = oracle.relres(gen, v.T, sol.cpu().numpy().T)
+    assert np.all(rr <= 1e-8), rr.max()
+
+
 def test_multi_rhs_solve_all_ports(bt):
     """Every element's port excitation (the embedded-element-pattern workload), IR per column."""
     nx, ny, b = 8, 6, 12

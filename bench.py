@@ -159,8 +159,17 @@ def product_bytes(nx, ny, b, mx, my, prec):
 def traffic_from_profiles(kernel_key: str):
     """ncu DRAM bytes per launch recorded in profiles/, if the kernel source is unchanged."""
     src = os.path.join(ROOT, "paper_2506_20350_gb300", "csrc", "contract.cu")
-    # digest of the code lines only: comment edits keep the capture valid
-    code = [ln for ln in open(src).read().splitlines() if not ln.strip().startswith("//")]
+    # digest of the code lines (comments excluded) of the block-product kernel template and its
+    # launch configuration: other kernels of the file, and comment edits, keep the capture valid
+    text = open(src).read()
+    try:
+        a = text.index("// KC: right-hand sides per launch")
+        b = text.index("template <class A>\nconstexpr int prec_of()")
+        c = text.index("static int launch_contract_impl(")
+        d = text.index("\n}\n", c)
+    except ValueError:
+        return None
+    code = [ln for ln in (text[a:b] + "\n" + text[c:d]).splitlines() if not ln.strip().startswith("//")]
     digest = hashlib.sha1("\n".join(code).encode()).hexdigest()[:12]
     path = os.path.join(ROOT, "profiles", "contract_traffic.txt")
     if not os.path.exists(path):

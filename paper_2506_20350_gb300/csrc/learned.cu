@@ -35,7 +35,8 @@ struct Learned {
     long step = 0;
     float2 *ubuf = nullptr, *rh = nullptr, *zh = nullptr, *zs = nullptr, *dz = nullptr, *bjr = nullptr;
     float *hc = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dg = nullptr, *dx = nullptr, *dh = nullptr;
-    float *wt = nullptr, *wpart = nullptr, *colred = nullptr;
+    float *wpart = nullptr, *colred = nullptr;
+    __nv_bfloat16 *wtb = nullptr;      // one convolution's weights in the tensor-core layout
     long wpart_len = 0;
     size_t bytes = 0;
 };
@@ -126,47 +127,84 @@ __global__ void __launch_bounds__(256) lp_decode_kernel(const __nv_bfloat16 *Aw,
     }
 }
 
-// Wt[(ci*9 + tap)*Co + co] = W[co][ci][tap]            (forward layout)
-// Wt[(co*9 + tap)*Ci + ci] = W[co][ci][8 - tap]        (flip = 1: data-gradient layout)
-__global__ void lp_wt_kernel(const __nv_bfloat16 *W, float *Wt, int Co, int Ci, int flip) {
-    const int total = Co * Ci * 9;
+// Row stride (bfloat16 entries) of the tensor-core weight layout: >= 9*Ci and
+// = 8 (mod 64), i.e. 4 (mod 32) words, so that fragment loads are conflict-free.
+__host__ __device__ constexpr int conv_kst(int ci) { return ((9 * ci + 55) / 64) * 64 + 8; }
+
+// Wb[co][tap*Ci + ci] = W[co][ci][tap]                 (forward: W is [Co][Ci][9])
+// Wb[co][tap*Ci + ci] = W[ci][co][8 - tap]             (flip = 1, data gradient: W is [Ci][Co][9])
+// for the convolution with Ci inputs and Co outputs; padding entries are zero.
+__global__ void lp_wtb_kernel(const __nv_bfloat16 *W, __nv_bfloat16 *Wb, int Co, int Ci, int flip) {
+    const int kst = conv_kst(Ci);
+    const int total = Co * kst;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int co = i / (Ci * 9), ci = (i / 9) % Ci, tap = i % 9;
-        const float v = bf(W, i);
-        if (!flip) Wt[((long)ci * 9 + tap) * Co + co] = v;
-        else Wt[((long)co * 9 + (8 - tap)) * Ci + ci] = v;
+        const int co = i / kst, k = i - co * kst;
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (k < 9 * Ci) {
+            const int tap = k / Ci, ci = k - tap * Ci;
+            v = flip ? W[((long)ci * Co + co) * 9 + (8 - tap)] : W[((long)co * Ci + ci) * 9 + tap];
+        }
+        Wb[i] = v;
     }
 }
 
-// Circular 3x3 convolution over the (ky, kx) grid of every column:
-//   out[n][co] = bias[co] + sum_{tap, ci} Wt[(ci*9 + tap)*CO + co] * in(nb(n, tap))[ci],
-// nb(n, tap) the neighbour (y + tap/3 - 1, x + tap%3 - 1) mod (my, mx) of position n
-// in its column, in = relu(X) when relu_in; the result is zeroed where
-// mask[n][co] <= 0 when a mask is given (the ReLU derivative of the backward pass).
-// Persistent CTAs of 256 threads hold the CI*9*CO weights in shared memory and
-// walk tiles of TP = 4096/CO positions.  For each tile a table of the 9 x TP
-// neighbour rows is built once (double-buffered: the next tile's table is
-// built while the current one is used); per tap the TP neighbour rows (CI
-// floats each) are copied in with 16-byte cp.async, double-buffered across
-// taps.  A thread owns 4 positions (strided by TP/4) x 4 output channels.
+// Circular 3x3 convolution over the (ky, kx) grid of every column, on the
+// tensor cores:
+//   out[n][co] = bias[co] + sum_{tap, ci} W(co, ci, tap) * in(nb(n, tap))[ci],
+// nb(n, tap) the neighbour (y + tap/3 - 1, x + tap%3 - 1) mod (my, mx) of
+// position n in its column, in = relu(X) when relu_in; the result is zeroed
+// where mask[n][co] <= 0 when a mask is given (the ReLU derivative of the
+// backward pass).  An implicit GEMM: M = positions (tiles of kConvTP), N = CO,
+// K = 9 taps x Ci.  The bfloat16 weights (the B operand, exact) stay in shared
+// memory; per tap the kConvTP neighbour rows (Ci binary32 values each) are
+// copied in with 16-byte cp.async, double-buffered across taps, through a
+// per-tile table of neighbour rows.  Each binary32 activation enters the
+// mma.sync m16n8k16 (bf16 inputs, binary32 accumulation) as three bfloat16
+// terms, x = hi + mid + lo, and the weights are bfloat16 already, so the
+// products carry binary32 accuracy (split-BF16x3).  Warp w owns 16 positions x
+// all CO channels.
+constexpr int kConvTP = 128;
+
+// x = hi + mid + lo with three bfloat16 terms (24 significant bits: the
+// binary32 value up to its last bit or so), for a pair of activations.
+__device__ __forceinline__ void split3_bf16x2(float a, float b, uint32_t &hi, uint32_t &mid, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const float ra = a - hf.x, rb = b - hf.y;
+    const __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+    const float2 mf = __bfloat1622float2(m);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(ra - mf.x, rb - mf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    mid = *reinterpret_cast<const uint32_t *>(&m);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 template <int CO>
-__global__ void __launch_bounds__(256) lp_conv_kernel(const float *X, int Ci, int relu_in, const float *Wt,
-                                                      const float *bias, float *out, long npos, int my, int mx,
-                                                      long bins, const float *mask) {
-    constexpr int TP = 4096 / CO;
-    constexpr int CG = CO / 4;
-    constexpr int PS = TP / 4;                 // position stride of a thread's 4 positions
-    extern __shared__ __align__(16) float lsm[];
-    float *ws = lsm;                           // Ci*9*CO
-    const int xstride = Ci + 4;                // floats per staged row (keeps 16-byte alignment)
-    float *xs0 = ws + (long)Ci * 9 * CO;       // 2 buffers of TP*xstride
-    int *nbr0 = reinterpret_cast<int *>(xs0 + 2 * TP * xstride);   // 2 tables of 9*TP rows
+__global__ void __launch_bounds__(256, 1) lp_conv_kernel(const float *X, int Ci, int relu_in,
+                                                         const __nv_bfloat16 *Wb, const float *bias, float *out,
+                                                         long npos, int my, int mx, long bins, const float *mask) {
+    constexpr int TP = kConvTP;
+    constexpr int NT = CO / 8;
+    extern __shared__ __align__(16) unsigned char lsm_raw[];
+    const int kst = conv_kst(Ci);
+    const int xstride = Ci + 4;                                      // floats per staged row
+    __nv_bfloat16 *ws = reinterpret_cast<__nv_bfloat16 *>(lsm_raw); // CO * kst
+    float *xs0 = reinterpret_cast<float *>(lsm_raw + (((size_t)CO * kst * 2 + 15) & ~(size_t)15));
+    int *nbr0 = reinterpret_cast<int *>(xs0 + 2 * TP * xstride);    // 2 tables of 9*TP rows
     const long ntiles = (npos + TP - 1) / TP;
     if ((long)blockIdx.x >= ntiles) return;
     {
-        const float4 *src = reinterpret_cast<const float4 *>(Wt);
-        float4 *dst = reinterpret_cast<float4 *>(ws);
-        for (int i = threadIdx.x; i < Ci * 9 * CO / 4; i += blockDim.x) dst[i] = src[i];
+        const uint4 *src = reinterpret_cast<const uint4 *>(Wb);
+        uint4 *dst = reinterpret_cast<uint4 *>(ws);
+        for (int i = threadIdx.x; i < CO * kst / 8; i += blockDim.x) dst[i] = src[i];
     }
     // neighbour rows of tile t (row = c*bins + yy*mx + xx, -1 past the end)
     auto build_table = [&](long t, int *tab) {
@@ -200,9 +238,8 @@ __global__ void __launch_bounds__(256) lp_conv_kernel(const float *X, int Ci, in
         }
         cp_async_commit();
     };
-    const int cg = threadIdx.x % CG, pg = threadIdx.x / CG;
-    float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (bias) bv = *reinterpret_cast<const float4 *>(bias + cg * 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gid = lane >> 2, tig = lane & 3;
     int buf = 0, tb = 0;
     build_table(blockIdx.x, nbr0);
     __syncthreads();
@@ -211,11 +248,11 @@ __global__ void __launch_bounds__(256) lp_conv_kernel(const float *X, int Ci, in
         const long tn = t + gridDim.x;
         int *tab = nbr0 + tb * 9 * TP, *tabn = nbr0 + (tb ^ 1) * 9 * TP;
         if (tn < ntiles) build_table(tn, tabn);       // read first at tap 8, after two barriers
-        float acc[4][4];
+        float acc[NT][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[j][k] = 0.f;
+            for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
 #pragma unroll 1
         for (int tap = 0; tap < 9; ++tap) {
             if (tap < 8) stage(tab, tap + 1, xs0 + (buf ^ 1) * TP * xstride);
@@ -223,32 +260,34 @@ __global__ void __launch_bounds__(256) lp_conv_kernel(const float *X, int Ci, in
             else cp_async_commit();
             cp_async_wait<1>();
             __syncthreads();
-            const float *xr = xs0 + buf * TP * xstride + pg * xstride;
-            const float *wr = ws + tap * CO + cg * 4;
-#pragma unroll 2
-            for (int ci = 0; ci < Ci; ci += 4) {
-                float4 xv[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    xv[j] = *reinterpret_cast<const float4 *>(xr + j * PS * xstride + ci);
-                    if (relu_in) {
-                        xv[j].x = fmaxf(xv[j].x, 0.f);
-                        xv[j].y = fmaxf(xv[j].y, 0.f);
-                        xv[j].z = fmaxf(xv[j].z, 0.f);
-                        xv[j].w = fmaxf(xv[j].w, 0.f);
-                    }
+            const float *xr0 = xs0 + buf * TP * xstride + (warp * 16 + gid) * xstride + 2 * tig;
+            const float *xr1 = xr0 + 8 * xstride;
+            const __nv_bfloat16 *wr = ws + gid * kst + tap * Ci + 2 * tig;
+#pragma unroll 1
+            for (int kc = 0; kc < Ci; kc += 16) {
+                float2 v00 = *reinterpret_cast<const float2 *>(xr0 + kc);
+                float2 v10 = *reinterpret_cast<const float2 *>(xr1 + kc);
+                float2 v01 = *reinterpret_cast<const float2 *>(xr0 + kc + 8);
+                float2 v11 = *reinterpret_cast<const float2 *>(xr1 + kc + 8);
+                if (relu_in) {
+                    v00 = make_float2(fmaxf(v00.x, 0.f), fmaxf(v00.y, 0.f));
+                    v10 = make_float2(fmaxf(v10.x, 0.f), fmaxf(v10.y, 0.f));
+                    v01 = make_float2(fmaxf(v01.x, 0.f), fmaxf(v01.y, 0.f));
+                    v11 = make_float2(fmaxf(v11.x, 0.f), fmaxf(v11.y, 0.f));
                 }
+                uint32_t ah[4], am[4], al[4];
+                split3_bf16x2(v00.x, v00.y, ah[0], am[0], al[0]);
+                split3_bf16x2(v10.x, v10.y, ah[1], am[1], al[1]);
+                split3_bf16x2(v01.x, v01.y, ah[2], am[2], al[2]);
+                split3_bf16x2(v11.x, v11.y, ah[3], am[3], al[3]);
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    const float4 w = *reinterpret_cast<const float4 *>(wr + (long)(ci + cc) * 9 * CO);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float v = cc == 0 ? xv[j].x : cc == 1 ? xv[j].y : cc == 2 ? xv[j].z : xv[j].w;
-                        acc[j][0] = fmaf(v, w.x, acc[j][0]);
-                        acc[j][1] = fmaf(v, w.y, acc[j][1]);
-                        acc[j][2] = fmaf(v, w.z, acc[j][2]);
-                        acc[j][3] = fmaf(v, w.w, acc[j][3]);
-                    }
+                for (int nt = 0; nt < NT; ++nt) {
+                    const __nv_bfloat16 *wn = wr + nt * 8 * kst + kc;
+                    const uint32_t b0 = *reinterpret_cast<const uint32_t *>(wn);
+                    const uint32_t b1 = *reinterpret_cast<const uint32_t *>(wn + 8);
+                    mma_bf16(acc[nt], al, b0, b1);              // smallest terms first
+                    mma_bf16(acc[nt], am, b0, b1);
+                    mma_bf16(acc[nt], ah, b0, b1);
                 }
             }
             __syncthreads();
@@ -256,18 +295,24 @@ __global__ void __launch_bounds__(256) lp_conv_kernel(const float *X, int Ci, in
         }
         tb ^= 1;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const long n = t * TP + pg + j * PS;
+        for (int half = 0; half < 2; ++half) {
+            const long n = t * TP + warp * 16 + gid + half * 8;
             if (n >= npos) continue;
-            float4 o = make_float4(acc[j][0] + bv.x, acc[j][1] + bv.y, acc[j][2] + bv.z, acc[j][3] + bv.w);
-            if (mask) {
-                const float4 mv = *reinterpret_cast<const float4 *>(mask + n * CO + cg * 4);
-                if (!(mv.x > 0.f)) o.x = 0.f;
-                if (!(mv.y > 0.f)) o.y = 0.f;
-                if (!(mv.z > 0.f)) o.z = 0.f;
-                if (!(mv.w > 0.f)) o.w = 0.f;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int co = nt * 8 + 2 * tig;
+                float2 o = make_float2(acc[nt][2 * half], acc[nt][2 * half + 1]);
+                if (bias) {
+                    o.x += bias[co];
+                    o.y += bias[co + 1];
+                }
+                if (mask) {
+                    const float2 mv = *reinterpret_cast<const float2 *>(mask + n * CO + co);
+                    if (!(mv.x > 0.f)) o.x = 0.f;
+                    if (!(mv.y > 0.f)) o.y = 0.f;
+                }
+                *reinterpret_cast<float2 *>(out + n * CO + co) = o;
             }
-            *reinterpret_cast<float4 *>(out + n * CO + cg * 4) = o;
         }
     }
     cp_async_wait<0>();
@@ -591,24 +636,28 @@ static int fft_inv(Plan *p, Learned *L, const float2 *in, int nc, void *out, int
 }
 
 template <int CO>
+static size_t conv_smem(int Ci) {
+    return (((size_t)CO * conv_kst(Ci) * 2 + 15) & ~(size_t)15) +
+           (2 * (size_t)kConvTP * (Ci + 4) + 2 * 9 * (size_t)kConvTP) * sizeof(float);
+}
+
+template <int CO>
 static int conv_launch_co(Plan *p, Learned *L, const float *X, int Ci, int relu_in, const float *bias, float *out,
                           int nc, const float *mask) {
-    constexpr int TP = 4096 / CO;
-    const size_t smem = ((size_t)Ci * 9 * CO + 2 * (size_t)TP * (Ci + 4) + 2 * 9 * (size_t)TP) * sizeof(float);
+    const size_t smem = conv_smem<CO>(Ci);
     cudaFuncSetAttribute(lp_conv_kernel<CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
     const long npos = (long)nc * L->bins;
-    const long ntiles = (npos + TP - 1) / TP;
+    const long ntiles = (npos + kConvTP - 1) / kConvTP;
     const long blocks = std::min<long>(ntiles, p->nsm);
-    lp_conv_kernel<CO><<<(unsigned)blocks, 256, smem, p->stream>>>(X, Ci, relu_in, L->wt, bias, out, npos, L->my,
+    lp_conv_kernel<CO><<<(unsigned)blocks, 256, smem, p->stream>>>(X, Ci, relu_in, L->wtb, bias, out, npos, L->my,
                                                                    L->mx, L->bins, mask);
     return BTTB_OK;
 }
 
 static int conv_launch(Plan *p, Learned *L, const float *X, int Ci, int relu_in, const __nv_bfloat16 *W,
                        const float *bias, float *out, int Co, int nc, int flip, const float *mask) {
-    // flip = 1: data gradient (input channels Co of W, output channels Ci of W)
-    const int wCo = flip ? Ci : Co, wCi = flip ? Co : Ci;
-    lp_wt_kernel<<<64, 256, 0, p->stream>>>(W, L->wt, wCo, wCi, flip);
+    // flip = 1: data gradient (W is [Ci][Co][9], the forward convolution from Co to Ci channels)
+    lp_wtb_kernel<<<64, 256, 0, p->stream>>>(W, L->wtb, Co, Ci, flip);
     if (Co == 64) conv_launch_co<64>(p, L, X, Ci, relu_in, bias, out, nc, mask);
     else if (Co == 32) conv_launch_co<32>(p, L, X, Ci, relu_in, bias, out, nc, mask);
     else conv_launch_co<16>(p, L, X, Ci, relu_in, bias, out, nc, mask);
@@ -724,7 +773,7 @@ void learned_free(Learned *L) {
     cudaFree(L->master); cudaFree(L->grad); cudaFree(L->m1); cudaFree(L->m2); cudaFree(L->wbf);
     cudaFree(L->ubuf); cudaFree(L->rh); cudaFree(L->zh); cudaFree(L->zs); cudaFree(L->dz); cudaFree(L->bjr);
     cudaFree(L->hc); cudaFree(L->a1); cudaFree(L->a2); cudaFree(L->a3); cudaFree(L->dg); cudaFree(L->dx);
-    cudaFree(L->dh); cudaFree(L->wt); cudaFree(L->wpart); cudaFree(L->colred);
+    cudaFree(L->dh); cudaFree(L->wtb); cudaFree(L->wpart); cudaFree(L->colred);
     delete L;
 }
 
@@ -799,7 +848,7 @@ int bttb_learned_create(bttb_learned *out, bttb_plan plan, int rank, int channel
     alloc(&L->dg, sizeof(float) * pos * 2 * R);
     alloc(&L->dx, sizeof(float) * pos * std::max(C, 2 * R));
     alloc(&L->dh, sizeof(float) * pos * C);
-    alloc(&L->wt, sizeof(float) * (size_t)std::max(C, 2 * R) * 9 * C);
+    alloc(&L->wtb, sizeof(__nv_bfloat16) * (size_t)std::max(C, 2 * R) * conv_kst(std::max(C, 2 * R)));
     const long mc = std::max(C, 2 * R);
     L->wpart_len = (long)kWgChunks * mc * (mc * 9 + 1);
     alloc(&L->wpart, sizeof(float) * L->wpart_len);

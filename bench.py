@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned-probe", action="store_true",
+                    help="profiling target: three applications of the learned correction to 16 columns and two "
+                         "training steps on 64 columns (40x40, b=96), then exit; prints no bench line")
     return ap.parse_args()
 
 
@@ -628,8 +631,36 @@ def run_ours(args):
     plan.close()
 
 
+def learned_probe():
+    """A short, fixed launch sequence of the learned correction for kernel profilers."""
+    import torch
+
+    import paper_2506_20350_gb300 as bt
+    from workloads import arrays
+
+    if not torch.cuda.is_available():
+        raise SystemExit("the learned probe needs a CUDA GPU")
+    c = arrays.CONFIGS["learned"]
+    nx, ny, b = c["nx"], c["ny"], c["b"]
+    plan = bt.Plan(nx, ny, b, max_rhs=64)
+    plan.set_generators(arrays.generator_blocks_torch(nx, ny, b, c["seed"]))
+    lrn = bt.Learned(plan, rank=16, channels=64, max_cols=64, seed=c["seed"])
+    r = torch.from_numpy(arrays.random_vectors(plan.n, 64, seed=0).T.astype(np.complex64)).cuda().contiguous()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        lrn.apply(r[:16].contiguous())
+    for _ in range(2):
+        lrn.train_step(r, r, lr=1e-4, want_loss=False)
+    torch.cuda.synchronize()
+    lrn.close()
+    plan.close()
+
+
 def main():
     args = parse_args()
+    if args.learned_probe:
+        learned_probe()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

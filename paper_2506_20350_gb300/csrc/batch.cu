@@ -60,6 +60,7 @@ int bttb_batch_create(bttb_batch *out, int count, const int *nx, const int *ny, 
             batch_release(h);
             return rc;
         }
+        h->plans[i]->p.in_batch = true;
     }
     *out = h;
     return BTTB_OK;

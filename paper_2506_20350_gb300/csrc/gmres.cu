@@ -800,7 +800,7 @@ static int arnoldi_step(Plan *p, GmresWork *g, int inner, int j) {
         launch_pdl(step_dots_kernel, dgrid, dim3(kDotIW * 32), 0, st, a, pass, pass == 0 ? a.cnt_a : a.cnt_b, j);
         prof_end(p, tok, 0.0);
         tok = prof_begin(p, pass == 0 ? 4 : 5);
-        if ((long)a.nblk_vec * k < 4L * p->nsm)
+        if (!p->in_batch && (long)a.nblk_vec * k < 4L * p->nsm)
             launch_pdl(step_update_kernel<16>, vgrid, dim3(kStepNB), upd_smem, st, a, pass, j);
         else
             launch_pdl(step_update_kernel<4>, vgrid, dim3(kStepNB), upd_smem, st, a, pass, j);

@@ -69,6 +69,7 @@ struct Plan {
     size_t smem_optin = 0;
     FftPlan fx, fy;
     int fft_pmax = 16;            // widest batch chunk of an FFT pass (power of two; autotuned in batches)
+    bool in_batch = false;        // runs beside other plans' kernels (bttb_batch): prefer occupancy
 
     // Spectrum copies, scaled by 1/(mx*my).  Bin k holds its b x b block
     // column-major (entry (p, q) at q*b + p) at offset k*gbs elements.

@@ -17,6 +17,9 @@
 //  - the spectrum is stored column-major per bin, so a lane reads R
 //    consecutive rows of one column (a 16-byte vector for R = 2) and the
 //    vector entry is a broadcast;
+//  - the spectrum does not depend on the preceding kernel, so each warp starts
+//    streaming its first chunk before the programmatic-dependent-launch wait;
+//    only the transformed vectors wait for the preceding FFT pass;
 //  - double-float accumulation is compensated (Dot2); every mbarrier wait is
 //    bounded by the global timer and reports a timeout instead of hanging.
 // A second kernel (contract_multi_kernel, below) covers many right-hand sides.
@@ -124,12 +127,6 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
     constexpr int NPL = GElem<A>::planes;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    pdl_wait();
-    if (a.active) {                                        // skip a group of finished columns (uniform)
-        bool any = false;
-        for (int c = 0; c < a.kc; ++c) any |= a.active[c] != 0;
-        if (!any) return;
-    }
     uint64_t *full = reinterpret_cast<uint64_t *>(smem) + warp * kWarpStages;
     unsigned char *stages = smem + 256 + (size_t)warp * kWarpStages * a.st_bytes;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8 * kConsumerWarps * kWarpStages);
@@ -149,23 +146,50 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
     const uint64_t pol_stream = l2_policy_evict_first();
     const uint64_t pol_keep = l2_policy_evict_last();
 
-    auto issue = [&](int it) {
+    // An item's stage fills in two parts: the spectrum chunk (expect_tx, no arrival) and the bin's
+    // transformed vectors (arrive.expect_tx); the phase completes when both have landed.
+    auto issue_g = [&](int it) {
         const int s = it % kWarpStages;
         const int bin = first + step * (it / a.nchunks), ch = it % a.nchunks;
         const int q0 = ch * a.Qc;
         const int qn = min(a.Qc, b - q0);
         const uint32_t gbytes = round_up16((uint32_t)(qn * b) * (uint32_t)sizeof(GT));
-        const uint32_t ubytes = round_up16((uint32_t)(a.kc * b) * (uint32_t)sizeof(C));
         unsigned char *st = stages + (size_t)s * a.st_bytes;
-        mbar_arrive_expect_tx(&full[s], gbytes * NPL + ubytes);
+        mbar_expect_tx(&full[s], gbytes * NPL);
         const long goff = (long)bin * a.gbs + (long)q0 * b;
         bulk_g2s(st, reinterpret_cast<const GT *>(a.g0) + goff, gbytes, &full[s], pol_stream);
         if (NPL == 2)
             bulk_g2s(st + a.off_g1, reinterpret_cast<const GT *>(a.g1) + goff, gbytes, &full[s], pol_stream);
+    };
+    auto issue_u = [&](int it) {
+        const int s = it % kWarpStages;
+        const int bin = first + step * (it / a.nchunks);
+        const uint32_t ubytes = round_up16((uint32_t)(a.kc * b) * (uint32_t)sizeof(C));
+        unsigned char *st = stages + (size_t)s * a.st_bytes;
+        mbar_arrive_expect_tx(&full[s], ubytes);
         bulk_g2s(st + a.off_u, reinterpret_cast<const C *>(a.u) + (long)bin * a.ubs, ubytes, &full[s], pol_keep);
     };
+    // The spectrum does not depend on the preceding kernel: start streaming it before the
+    // dependency wait, so that its first DRAM round trip overlaps that kernel's tail.
+    const int npre = min(kWarpStages - 1, nitems);
     if (lane == 0)
-        for (int it = 0; it < kWarpStages - 1 && it < nitems; ++it) issue(it);
+        for (int it = 0; it < npre; ++it) issue_g(it);
+    pdl_wait();
+    if (a.active) {                                        // skip a group of finished columns (uniform)
+        bool any = false;
+        for (int c = 0; c < a.kc; ++c) any |= a.active[c] != 0;
+        if (!any) {
+            // let the prefetched copies land before the CTA's shared memory goes away
+            if (lane == 0)
+                for (int it = 0; it < npre; ++it) {
+                    mbar_arrive(&full[it % kWarpStages]);
+                    mbar_wait_drain(&full[it % kWarpStages], 0u);
+                }
+            return;
+        }
+    }
+    if (lane == 0)
+        for (int it = 0; it < npre; ++it) issue_u(it);
 
     Acc<A> acc[KC][R];
     const int p0 = lane * R;
@@ -174,7 +198,10 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
         const int s = it % kWarpStages;
         const uint32_t ph = (uint32_t)(it / kWarpStages) & 1u;
         // keep kWarpStages-1 items in flight: the stage refilled now was released last iteration
-        if (lane == 0 && it + kWarpStages - 1 < nitems) issue(it + kWarpStages - 1);
+        if (lane == 0 && it + kWarpStages - 1 < nitems) {
+            issue_g(it + kWarpStages - 1);
+            issue_u(it + kWarpStages - 1);
+        }
         const int bin = first + step * (it / a.nchunks), ch = it % a.nchunks;
         if (!failed && !mbar_wait_bounded(&full[s], ph, abort_flag)) {
             failed = true;

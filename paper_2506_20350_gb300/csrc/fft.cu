@@ -162,7 +162,6 @@ __device__ __forceinline__ float2 scale_by<F32>(float2 v, double s) {
 }
 
 constexpr int kFftThreads = 256;
-constexpr int kLdBatch = 8;          // loads in flight per thread while staging a pass
 
 template <class A, int INF, int OUTF, bool INV>
 __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) {
@@ -186,22 +185,14 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
     long ibase = (long)c * a.in_cs + (long)o * a.in_os;
     if (a.in_sel) ibase += (long)(*a.in_sel) * a.in_sel_stride;
     const double scl = a.in_scale ? a.in_scale[c] : 1.0;
-    // Loads are issued kLdBatch at a time into registers, so that each thread
-    // keeps several requests in flight before it writes shared memory.
-    for (int base = tid; base < M * P; base += nt * kLdBatch) {
-        C v[kLdBatch];
-#pragma unroll
-        for (int u = 0; u < kLdBatch; ++u) {
-            const int idx = base + u * nt;
-            const int n = idx >> lP, pi = p0 + (idx & (P - 1));
-            v[u] = A::zero();
-            if (idx < M * P && n < a.nin && pi < a.pdim) v[u] = load_vec<A, INF>(a.in, ibase + (long)n * a.in_ns + pi);
+    for (int idx = tid; idx < M * P; idx += nt) {
+        const int n = idx >> lP, pp = idx & (P - 1), pi = p0 + pp;
+        C v = A::zero();
+        if (n < a.nin && pi < a.pdim) {
+            v = load_vec<A, INF>(a.in, ibase + (long)n * a.in_ns + pi);
+            if (a.in_scale) v = scale_by<A>(v, scl);
         }
-#pragma unroll
-        for (int u = 0; u < kLdBatch; ++u) {
-            const int idx = base + u * nt;
-            if (idx < M * P) buf0[idx] = a.in_scale ? scale_by<A>(v[u], scl) : v[u];
-        }
+        buf0[idx] = v;
     }
     __syncthreads();
 

@@ -79,7 +79,7 @@ struct Plan {
     long gbs = 0;
     bool have_gen = false;
 
-    // Block-Jacobi: R_0^{-1} (column-major b x b, binary32) for P_K of Sec. III-B.
+    // Block-Jacobi: R_0^{-1} (column-major, rows padded to a multiple of 4, binary32) for P_K of Sec. III-B.
     float2 *bj_inv = nullptr;
     bool bj_ready = false;
 

@@ -80,26 +80,35 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
 // ---------------------------------------------------------------------------
 constexpr int kBjThreads = 256;
 
-// R_0^{-1} is stored column-major (entry (p, q) at q*b + p), so the threads of a
-// warp, which own consecutive output rows p, read consecutive words.  A thread
-// computes two outputs at a time (rows of two cells) for independent FMA chains.
-template <int INF, int OUTF>
+// R_0^{-1} is stored column-major with the rows padded to bq = 4*ceil(b/4)
+// (entry (p, q) at q*bq + p, zero rows beyond b), so the four rows a thread
+// owns are one 32-byte load.  Thread (row group rg, cell group cg) computes
+// rows 4rg .. 4rg+3 of CC consecutive cells: per basis q it loads four entries
+// of R_0^{-1} and CC entries of x for 4*CC complex multiply-adds.  With CC = 4
+// the CTA stages R_0^{-1} in shared memory; with CC = 1 (few cells: small CTAs
+// that fill every SM) it reads R_0^{-1} through L1.
+template <int INF, int OUTF, int CC>
 __global__ void __launch_bounds__(kBjThreads) bj_apply_kernel(const float2 *rinv, const void *x, long ldx, void *z,
-                                                               long ldz, int b, int ncells, int cpb,
+                                                               long ldz, int b, int ncells, int ncg,
                                                                const int *in_sel, long in_sel_stride,
                                                                int rinv_in_smem, const int *active) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int bq = (b + 3) & ~3;
     const int xst = b + 1;                                    // padded row stride of the staged cells
-    float2 *xs = reinterpret_cast<float2 *>(smem_raw);       // cpb*xst
-    float2 *rsm = xs + (long)cpb * xst;                       // b*b, column-major (when it fits)
+    const int cpb = ncg * CC;
+    float2 *rsm = reinterpret_cast<float2 *>(smem_raw);      // b*bq (when staged)
+    float2 *xs = rsm + (rinv_in_smem ? (long)b * bq : 0);    // cpb*xst
     const float2 *rs = rinv_in_smem ? rsm : rinv;
     const int c = blockIdx.y;
     pdl_wait();
     if (active && !active[c]) return;
     const int cell0 = blockIdx.x * cpb;
     const int nc = min(cpb, ncells - cell0);
-    if (rinv_in_smem)
-        for (int i = threadIdx.x; i < b * b; i += blockDim.x) rsm[i] = rinv[i];
+    if (rinv_in_smem) {
+        const float4 *src = reinterpret_cast<const float4 *>(rinv);
+        float4 *dst = reinterpret_cast<float4 *>(rsm);
+        for (int i = threadIdx.x; i < b * bq / 2; i += blockDim.x) dst[i] = src[i];
+    }
     long xoff = (long)c * ldx + (long)cell0 * b;
     if (in_sel) xoff += (long)(*in_sel) * in_sel_stride;
     for (int i = threadIdx.x; i < nc * b; i += blockDim.x) {
@@ -107,30 +116,42 @@ __global__ void __launch_bounds__(kBjThreads) bj_apply_kernel(const float2 *rinv
         xs[cl * xst + (i - cl * b)] = load_vec<F32, INF>(x, xoff + i);
     }
     __syncthreads();
+    const int nrg = bq / 4;
+    const int rg = threadIdx.x % nrg, cg = threadIdx.x / nrg;
+    if (cg >= ncg) return;
+    const int r0 = rg * 4;
+    float2 acc[CC][4];
+#pragma unroll
+    for (int u = 0; u < CC; ++u)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[u][r] = make_float2(0.f, 0.f);
+    const float2 *xv = xs + (long)cg * CC * xst;
+    for (int q = 0; q < b; ++q) {
+        const float4 g01 = *reinterpret_cast<const float4 *>(rs + (long)q * bq + r0);
+        const float4 g23 = *reinterpret_cast<const float4 *>(rs + (long)q * bq + r0 + 2);
+        const float2 g[4] = {make_float2(g01.x, g01.y), make_float2(g01.z, g01.w), make_float2(g23.x, g23.y),
+                             make_float2(g23.z, g23.w)};
+#pragma unroll
+        for (int u = 0; u < CC; ++u) {
+            const float2 v = xv[u * xst + q];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                acc[u][r].x = fmaf(g[r].x, v.x, acc[u][r].x);
+                acc[u][r].x = fmaf(-g[r].y, v.y, acc[u][r].x);
+                acc[u][r].y = fmaf(g[r].x, v.y, acc[u][r].y);
+                acc[u][r].y = fmaf(g[r].y, v.x, acc[u][r].y);
+            }
+        }
+    }
     long zoff = (long)c * ldz + (long)cell0 * b;
     if (in_sel) zoff += (long)(*in_sel) * in_sel_stride;       // same selected column slot on output
-    const int total = nc * b;
-    for (int o = threadIdx.x; o < total; o += 2 * blockDim.x) {
-        const int o2 = o + blockDim.x;
-        const bool two = o2 < total;
-        const int cl = o / b, pr = o - cl * b;
-        const int cl2 = two ? o2 / b : cl, pr2 = two ? o2 - cl2 * b : pr;
-        const float2 *xv = xs + (long)cl * xst, *xv2 = xs + (long)cl2 * xst;
-        float2 a = make_float2(0.f, 0.f), a2 = make_float2(0.f, 0.f);
-        for (int q = 0; q < b; ++q) {
-            const float2 g = rs[(long)q * b + pr], g2 = rs[(long)q * b + pr2];
-            const float2 u = xv[q], u2 = xv2[q];
-            a.x = fmaf(g.x, u.x, a.x);
-            a.x = fmaf(-g.y, u.y, a.x);
-            a.y = fmaf(g.x, u.y, a.y);
-            a.y = fmaf(g.y, u.x, a.y);
-            a2.x = fmaf(g2.x, u2.x, a2.x);
-            a2.x = fmaf(-g2.y, u2.y, a2.x);
-            a2.y = fmaf(g2.x, u2.y, a2.y);
-            a2.y = fmaf(g2.y, u2.x, a2.y);
-        }
-        store_vec<F32, OUTF>(z, zoff + o, a);
-        if (two) store_vec<F32, OUTF>(z, zoff + o2, a2);
+#pragma unroll
+    for (int u = 0; u < CC; ++u) {
+        const int cl = cg * CC + u;
+        if (cl >= nc) continue;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (r0 + r < b) store_vec<F32, OUTF>(z, zoff + (long)cl * b + r0 + r, acc[u][r]);
     }
 }
 
@@ -138,27 +159,28 @@ template <int INF, int OUTF>
 static int bj_launch(Plan *p, const void *x, long ldx, void *z, long ldz, int nrhs, const int *in_sel,
                      long in_sel_stride, const int *active) {
     const int b = p->b, ncells = p->nx * p->ny;
-    // Cells per CTA: at most 8192/b, and few enough that the launch fills every SM
-    // twice over; CTAs with a handful of cells read R_0^{-1} through L1 instead of
-    // staging all b*b entries.
-    int cpb = (8 * 1024) / b;
-    const long want = 2L * p->nsm;
-    const long per = ((long)ncells * nrhs + want - 1) / want;
-    if (cpb > per) cpb = (int)per;
-    if (cpb < 1) cpb = 1;
-    if (cpb > ncells) cpb = ncells;
-    const size_t xs_bytes = (size_t)cpb * (b + 1) * sizeof(float2);
-    const size_t r_bytes = (size_t)b * b * sizeof(float2);
-    const int in_smem = (cpb >= 16 && xs_bytes + r_bytes <= 160 * 1024) ? 1 : 0;
-    const size_t smem = xs_bytes + (in_smem ? r_bytes : 0);
-    auto kern = bj_apply_kernel<INF, OUTF>;
+    const int bq = (b + 3) & ~3, nrg = bq / 4;
+    const int gmax = kBjThreads / nrg;                          // cell groups per CTA at most (b <= 256: >= 4)
+    const long want = 2L * p->nsm;                              // CTAs that fill every SM twice over
+    const long total = (long)ncells * nrhs;
+    const size_t r_bytes = (size_t)b * bq * sizeof(float2);
+    // Four cells per thread when there are cells enough for full CTAs everywhere and R_0^{-1} fits on chip.
+    const bool wide = total >= 4L * want * gmax && r_bytes + (size_t)4 * gmax * (b + 1) * sizeof(float2) <= 160 * 1024;
+    const int CC = wide ? 4 : 1;
+    long ncg = (total + want * CC - 1) / (want * CC);
+    if (ncg > gmax) ncg = gmax;
+    if (ncg < 1) ncg = 1;
+    const int cpb = (int)ncg * CC;
+    const int in_smem = wide ? 1 : 0;
+    const size_t smem = (in_smem ? r_bytes : 0) + (size_t)cpb * (b + 1) * sizeof(float2);
+    auto kern = wide ? bj_apply_kernel<INF, OUTF, 4> : bj_apply_kernel<INF, OUTF, 1>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
         if (e != cudaSuccess) return check_cuda(p, e, "block-Jacobi smem attribute");
     }
     dim3 grid((ncells + cpb - 1) / cpb, nrhs);
-    cudaError_t le = launch_pdl(kern, grid, dim3(kBjThreads), smem, p->stream, (const float2 *)p->bj_inv, x, ldx, z,
-                                ldz, b, ncells, cpb, in_sel, in_sel_stride, in_smem, active);
+    cudaError_t le = launch_pdl(kern, grid, dim3(nrg * (int)ncg), smem, p->stream, (const float2 *)p->bj_inv, x, ldx,
+                                z, ldz, b, ncells, (int)ncg, in_sel, in_sel_stride, in_smem, active);
     count_launch(p);
     if (le != cudaSuccess) return check_cuda(p, le, "block-Jacobi launch");
     return check_cuda(p, cudaGetLastError(), "block-Jacobi launch");
@@ -217,7 +239,8 @@ int block_jacobi_setup(Plan *p, const double2 *t00) {
             }
         }
     }
-    std::vector<float2> inv((long)b * b);
+    const int bq = (b + 3) & ~3;                                // rows padded to a multiple of 4
+    std::vector<float2> inv((long)b * bq, make_float2(0.f, 0.f));
     std::vector<double> col(2 * b);
     for (int e = 0; e < b; ++e) {
         // solve R_0 x = e_e: permute, forward with unit L, back with U
@@ -242,14 +265,14 @@ int block_jacobi_setup(Plan *p, const double2 *t00) {
             col[2 * i] = (sr * dr + si * di) / dd;
             col[2 * i + 1] = (si * dr - sr * di) / dd;
         }
-        for (int i = 0; i < b; ++i) inv[(long)e * b + i] = make_float2((float)col[2 * i], (float)col[2 * i + 1]);
+        for (int i = 0; i < b; ++i) inv[(long)e * bq + i] = make_float2((float)col[2 * i], (float)col[2 * i + 1]);
     }
     if (!p->bj_inv) {
-        cudaError_t e = cudaMalloc(&p->bj_inv, (size_t)b * b * sizeof(float2));
+        cudaError_t e = cudaMalloc(&p->bj_inv, (size_t)b * bq * sizeof(float2));
         if (e != cudaSuccess) return check_cuda(p, e, "block-Jacobi buffer");
-        p->bytes_held += (size_t)b * b * sizeof(float2);
+        p->bytes_held += (size_t)b * bq * sizeof(float2);
     }
-    cudaError_t e = cudaMemcpy(p->bj_inv, inv.data(), (size_t)b * b * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(p->bj_inv, inv.data(), (size_t)b * bq * sizeof(float2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return check_cuda(p, e, "block-Jacobi upload");
     p->bj_ready = true;
     return BTTB_OK;

@@ -155,8 +155,14 @@ typedef struct {
  * column stays in the space until all columns meet tol (each cycle targets a
  * Frobenius residual of tol * min_c ||V_c||); every column reports the same
  * iteration count and its own true residual.  Default: one space per column,
- * converged columns masked. */
-enum { BTTB_GMRES_NO_GRAPH = 1, BTTB_GMRES_GLOBAL = 2 };
+ * converged columns masked.
+ *
+ * Orthogonalisation is classical Gram-Schmidt applied twice (CGS2).  Without a
+ * preconditioner the default is its delayed form (the reorthogonalisation of
+ * v_j is merged into step j+1's reduction: one reduction and one update over
+ * the basis per step, and the residual estimate one step behind);
+ * BTTB_GMRES_CGS2 selects the two-pass form. */
+enum { BTTB_GMRES_NO_GRAPH = 1, BTTB_GMRES_GLOBAL = 2, BTTB_GMRES_CGS2 = 4 };
 
 typedef struct {
     int status;          /* BTTB_OK, BTTB_NOT_CONVERGED or BTTB_BREAKDOWN          */

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libbttb.so")
 BTTB_C64, BTTB_C128 = 0, 1
 BTTB_MV_FP64, BTTB_MV_FP32, BTTB_MV_FP64_NATIVE, BTTB_MV_TC_3XTF32 = 0, 1, 2, 3
 BTTB_PC_NONE, BTTB_PC_BLOCK_JACOBI, BTTB_PC_LEARNED = 0, 1, 2
-BTTB_GMRES_NO_GRAPH, BTTB_GMRES_GLOBAL = 1, 2
+BTTB_GMRES_NO_GRAPH, BTTB_GMRES_GLOBAL, BTTB_GMRES_CGS2 = 1, 2, 4
 BTTB_OK, BTTB_NOT_CONVERGED, BTTB_BREAKDOWN = 0, 1, 2
 BTTB_ERR_INVALID_ARG, BTTB_ERR_CUDA, BTTB_ERR_OOM = -1, -2, -3
 BTTB_ERR_NO_GENERATORS, BTTB_ERR_TIMEOUT, BTTB_ERR_NONFINITE, BTTB_ERR_SINGULAR = -4, -5, -6, -7

@@ -30,6 +30,10 @@ struct GmresWork {
     long np = 0;                  // product vector length (N)
     bool glob = false;            // global GMRES: one Krylov column over all kp user columns
     int *act_prod = nullptr;      // per product column copy of the global column's active flag
+    bool dcgs = false;            // delayed CGS2 (unpreconditioned cycles) instead of CGS2
+    float4 *U = nullptr;          // delayed CGS2: the not yet reorthogonalised vector u_j [k][n]
+    float4 *cco = nullptr, *hpre = nullptr;   // [k][m+1]: update coefficients, preliminary column
+    float4 *Horig = nullptr;      // [k][(m+1)*m] Hessenberg columns before the rotations
     bool flex = false;            // Zb allocated
     int pc = BTTB_PC_NONE;        // preconditioner of the current solve
     int NB = 0, nblk = 0;
@@ -53,6 +57,7 @@ struct GmresWork {
     cudaGraphExec_t cycle_exec = nullptr;
     int graph_inner = -1;
     int graph_pc = -1;
+    int graph_dcgs = -1;
     int graph_prof = 0;
     long launches_per_cycle = 0;
     std::vector<Plan::GraphRec> grecs;
@@ -579,6 +584,278 @@ __global__ void __launch_bounds__(kStepNB) step_scale_kernel(const StepArgs a, i
     pdl_trigger();
 }
 
+
+// ---------------------------------------------------------------------------
+// Delayed CGS2 for unpreconditioned cycles: one reduction and one update per
+// step instead of two of each.  The step applies the operator to u_j, the
+// previous step's vector after one Gram-Schmidt pass (not yet reorthogonalised
+// or normalised), x = A u_j, and in one reduction forms
+//   s = Q_{j-1}^H u_j,  t = Q_{j-1}^H x,  alpha = u_j^H u_j,  tau = u_j^H x.
+// The reorthogonalised q_j = (u_j - Q s)/nu, nu^2 = alpha - |s|^2, closes
+// Hessenberg column j-1 (its entries gain s, its subdiagonal is nu), and since
+// A Q_{j-1} = Q_j H, A q_j = (x - Q_j H s)/nu: the coefficients of A q_j on Q_j
+// are c = [t; (tau - s^H t)/nu], the preliminary column j is (c - H s)/nu, and
+//   u_{j+1} = (x - Q_{j-1} t - q_j c_j)/nu.
+// The update writes q_j and u_{j+1} in one pass over the basis.  A closing
+// reduction without x finalises the last column of the cycle.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        v = df_add(v, df{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)});
+    return v;
+}
+__device__ __forceinline__ dfc warp_sum_dfc(dfc v) { return dfc{warp_sum_df(v.re), warp_sum_df(v.im)}; }
+
+struct DcgsArgs {
+    const float4 *Vb;     // basis q_0 .. q_{j-1}, [i][c][n]
+    float4 *U;            // u_j on entry to the update, u_{j+1} on exit, [c][n]
+    const float4 *X;      // x = A u_j, [c][n]
+    long n, bs_i, bs_c;
+    int m, k;
+    int dot_sub, nblk_dot, ich, nblk_vec;
+    float4 *part;
+    long pstride;
+    float4 *sco, *cco, *hpre, *Horig, *hcol;   // [c][m+1] x 4, Horig [c][(m+1)*m]
+    unsigned *cnt;
+    int *active, *d_any_step;
+    float4 *H, *gv, *sn;
+    float2 *cs;
+    double *inv_beta;
+    int *steps, *bdown;
+    const int *mlimit;
+    const double *target;
+    int *err;
+};
+
+__global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a, int j, int has_x) {
+    extern __shared__ __align__(16) float4 dsm[];      // s, t: 2(m+1); Givens scratch 4m+4; Hs: m+1; partials
+    const int c = blockIdx.y;
+    pdl_wait();
+    if (!a.active[c]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long t = (long)blockIdx.x * kDotIW + warp;
+    const int i = (int)(t / a.nblk_dot), blk = (int)(t - (long)i * a.nblk_dot);
+    float4 *part = a.part + (long)c * a.pstride;
+    if (i <= j) {
+        // i < j: (q_i, u) and (q_i, x); i == j: (u, u) and (u, x)
+        const float4 *uv = a.U + (long)c * a.n;
+        const float4 *xv = a.X + (long)c * a.n;
+        const float4 *qv = i < j ? a.Vb + (long)i * a.bs_i + (long)c * a.bs_c : uv;
+        dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
+        for (int sc = 0; sc < a.dot_sub; ++sc) {
+            const long n0 = ((long)blk * a.dot_sub + sc) * kDotNE;
+            const int len = (int)max(0L, min((long)kDotNE, a.n - n0));
+            float4 q[kDotPL], u[kDotPL], x[kDotPL];
+#pragma unroll
+            for (int r = 0; r < kDotPL; ++r) {
+                const int e = lane + 32 * r;
+                const bool in = e < len;
+                q[r] = in ? qv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                u[r] = in ? uv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                x[r] = in && has_x ? xv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int r = 0; r < kDotPL; ++r) {
+                // conj(q) u and conj(q) x, compensated
+                dacc_mac(sr, q[r].x, q[r].z, u[r].x, u[r].z);
+                dacc_mac(sr, q[r].y, q[r].w, u[r].y, u[r].w);
+                dacc_mac(si, q[r].x, q[r].z, u[r].y, u[r].w);
+                dacc_mac(si, -q[r].y, -q[r].w, u[r].x, u[r].z);
+                dacc_mac(tr, q[r].x, q[r].z, x[r].x, x[r].z);
+                dacc_mac(tr, q[r].y, q[r].w, x[r].y, x[r].w);
+                dacc_mac(ti, q[r].x, q[r].z, x[r].y, x[r].w);
+                dacc_mac(ti, -q[r].y, -q[r].w, x[r].x, x[r].z);
+            }
+        }
+        warp_reduce_dacc(sr);
+        warp_reduce_dacc(si);
+        warp_reduce_dacc(tr);
+        warp_reduce_dacc(ti);
+        if (lane == 0) {
+            const df a0 = dacc_result(sr), a1 = dacc_result(si), b0 = dacc_result(tr), b1 = dacc_result(ti);
+            part[(long)i * a.nblk_dot + blk] = make_float4(a0.hi, a1.hi, a0.lo, a1.lo);
+            part[(long)(a.m + 1 + i) * a.nblk_dot + blk] = make_float4(b0.hi, b1.hi, b0.lo, b1.lo);
+        }
+    }
+    pdl_trigger();
+    if (!arrive_last(a.cnt + c, (int)gridDim.x)) return;
+    // ---- last CTA of the column: sums in chunk order
+    const int m = a.m;
+    float4 *ssm = dsm, *tsm = dsm + (m + 1);
+    float4 *gscr = dsm + 2 * (m + 1);
+    float4 *hs = gscr + (4 * m + 4);
+    for (int q = warp; q < 2 * (j + 1); q += kDotIW) {
+        const int slot = q <= j ? q : (m + 1) + (q - j - 1);
+        const float4 *pp = part + (long)slot * a.nblk_dot;
+        dacc re{0.f, 0.f}, im{0.f, 0.f};
+        for (int e = lane; e < a.nblk_dot; e += 32) {
+            const float4 v = __ldcg(pp + e);
+            dacc_add(re, dacc{v.x, v.z});
+            dacc_add(im, dacc{v.y, v.w});
+        }
+        warp_reduce_dacc(re);
+        warp_reduce_dacc(im);
+        if (lane == 0) {
+            const df r = dacc_result(re), z = dacc_result(im);
+            (q <= j ? ssm[q] : tsm[q - j - 1]) = make_float4(r.hi, z.hi, r.lo, z.lo);
+        }
+    }
+    __syncthreads();
+    // nu^2 = alpha - |s|^2 (alpha = u^H u is the real part of slot j) by warp 0, and
+    // s^H t for c_j by warp 1, each a strided sum and a fixed-order warp reduction
+    __shared__ float4 s_nu;                               // {nu.hi, 1/nu.hi, nu.lo, 1/nu.lo}
+    __shared__ float4 s_sht;                              // s^H t
+    __shared__ int s_cont;
+    if (warp == 0) {
+        df acc{0.f, 0.f};
+        for (int q = lane; q < j; q += 32) acc = df_add(acc, dfc_abs2(dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
+        acc = warp_sum_df(acc);
+        if (lane == 0) {
+            df nu2 = df_sub(df{ssm[j].x, ssm[j].z}, acc);
+            if (!(nu2.hi > 0.f)) nu2 = df{0.f, 0.f};
+            const df nu = df_sqrt(nu2);
+            const df inu = nu.hi > 0.f ? df_recip(nu) : df{0.f, 0.f};
+            s_nu = make_float4(nu.hi, inu.hi, nu.lo, inu.lo);
+        }
+    } else if (warp == 1 && has_x) {
+        dfc acc{df{0.f, 0.f}, df{0.f, 0.f}};
+        for (int q = lane; q < j; q += 32)
+            acc = dfc_add(acc, dfc_mul(dfc_conj(dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))),
+                                       dfc_load(*reinterpret_cast<const cdf *>(&tsm[q]))));
+        acc = warp_sum_dfc(acc);
+        if (lane == 0) {
+            const cdf st = dfc_store(acc);
+            s_sht = make_float4(st.rh, st.ih, st.rl, st.il);
+        }
+    }
+    __syncthreads();
+    const df nu{s_nu.x, s_nu.z}, inu{s_nu.y, s_nu.w};
+    float4 *Hoc = a.Horig + (long)c * (m + 1) * m;
+    if (j >= 1) {
+        // close column j-1: entries hpre + s (rows 0..j-1), subdiagonal nu
+        float4 *fc = a.hcol + (long)c * (m + 1);
+        const float4 *hp = a.hpre + (long)c * (m + 1);
+        for (int q = threadIdx.x; q < j; q += blockDim.x) {
+            const dfc v = dfc_add(dfc_load(*reinterpret_cast<const cdf *>(&hp[q])),
+                                  dfc_load(*reinterpret_cast<const cdf *>(&ssm[q])));
+            const cdf st = dfc_store(v);
+            fc[q] = make_float4(st.rh, st.ih, st.rl, st.il);
+            Hoc[(long)(j - 1) * (m + 1) + q] = fc[q];
+        }
+        if (threadIdx.x == 0) Hoc[(long)(j - 1) * (m + 1) + j] = make_float4(nu.hi, 0.f, nu.lo, 0.f);
+        __threadfence_block();
+        __syncthreads();
+        if (warp == 0) {
+            const double nu2d = df_to_double(df_mul(nu, nu));
+            const int cont = givens_column(c, j - 1, m, gscr, a.H, a.hcol, nu2d, a.cs, a.sn, a.gv, a.active,
+                                           a.steps, a.bdown, a.mlimit, a.target, a.inv_beta, a.err);
+            if (lane == 0) s_cont = cont;
+        }
+        __syncthreads();
+        if (!s_cont || !has_x) return;
+    } else {
+        if (threadIdx.x == 0) a.inv_beta[c] = df_to_double(inu);
+    }
+    if (!has_x) return;
+    if (threadIdx.x == 0) atomicMax(a.d_any_step, j + 1);
+    // H s (rows 0..j) from the unrotated columns 0..j-1 (column q has rows 0..q+1): thread (row r,
+    // group g) sums the columns q = g, g+G, ... of row r; the G partial sums of a row are then added
+    // in group order.  Meanwhile thread 0 forms c_j = (tau - s^H t)/nu.
+    const int R = j + 1, G = max(1, (int)blockDim.x / R);
+    float4 *hpart = hs + (m + 1);                         // R*G partial sums
+    if ((int)threadIdx.x < R * G) {
+        const int r = threadIdx.x % R, gq = threadIdx.x / R;
+        dfc acc{df{0.f, 0.f}, df{0.f, 0.f}};
+        for (int q = max(r - 1, 0) + ((gq - max(r - 1, 0) % G) % G + G) % G; q < j; q += G)
+            acc = dfc_add(acc, dfc_mul(dfc_load(*reinterpret_cast<const cdf *>(&Hoc[(long)q * (m + 1) + r])),
+                                       dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
+        const cdf st = dfc_store(acc);
+        hpart[gq * R + r] = make_float4(st.rh, st.ih, st.rl, st.il);
+    }
+    if (threadIdx.x == 0) {
+        const dfc cj = dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&tsm[j])),
+                               dfc_load(*reinterpret_cast<const cdf *>(&s_sht)));
+        const cdf st = dfc_store(dfc_scale(cj, inu));
+        tsm[j] = make_float4(st.rh, st.ih, st.rl, st.il);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        dfc acc = dfc_load(*reinterpret_cast<const cdf *>(&hpart[r]));
+        for (int gq = 1; gq < G; ++gq) acc = dfc_add(acc, dfc_load(*reinterpret_cast<const cdf *>(&hpart[gq * R + r])));
+        const cdf st = dfc_store(acc);
+        hs[r] = make_float4(st.rh, st.ih, st.rl, st.il);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r <= j; r += blockDim.x) {
+        const long o = (long)c * (m + 1) + r;
+        if (r < j) a.sco[o] = ssm[r];
+        a.cco[o] = tsm[r];
+        const dfc hp = dfc_scale(dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&tsm[r])),
+                                         dfc_load(*reinterpret_cast<const cdf *>(&hs[r]))), inu);
+        const cdf st = dfc_store(hp);
+        a.hpre[o] = make_float4(st.rh, st.ih, st.rl, st.il);
+    }
+}
+
+// q_j = (u_j - Q s)/nu and u_{j+1} = (x - Q t - q_j c_j)/nu, one entry per thread, the basis
+// entries loaded UB at a time and shared by both sums.
+template <int UB>
+__global__ void __launch_bounds__(kStepNB) dcgs_update_kernel(const DcgsArgs a, int j) {
+    extern __shared__ __align__(16) float4 csm[];        // -s: j entries, -c: j+1 entries
+    const int c = blockIdx.y, blk = blockIdx.x;
+    pdl_wait();
+    if (!a.active[c]) return;
+    float4 *sn_ = csm, *cn_ = csm + (a.m + 1);
+    for (int q = threadIdx.x; q <= j; q += blockDim.x) {
+        const long o = (long)c * (a.m + 1) + q;
+        if (q < j) {
+            const float4 v = a.sco[o];
+            sn_[q] = make_float4(-v.x, -v.y, -v.z, -v.w);
+        }
+        const float4 w = a.cco[o];
+        cn_[q] = make_float4(-w.x, -w.y, -w.z, -w.w);
+    }
+    __syncthreads();
+    const long e = (long)blk * kStepNB + threadIdx.x;
+    if (e < a.n) {
+        const float4 u = a.U[(long)c * a.n + e], x = a.X[(long)c * a.n + e];
+        dacc qr{u.x, u.z}, qi{u.y, u.w}, xr{x.x, x.z}, xi{x.y, x.w};
+        const float4 *basis = a.Vb + (long)c * a.bs_c + e;
+        for (int i0 = 0; i0 < j; i0 += UB) {
+            float4 v[UB];
+#pragma unroll
+            for (int r = 0; r < UB; ++r)
+                if (i0 + r < j) v[r] = basis[(long)(i0 + r) * a.bs_i];
+#pragma unroll
+            for (int r = 0; r < UB; ++r) {
+                if (i0 + r < j) {
+                    const float4 h = sn_[i0 + r], g = cn_[i0 + r];
+                    dacc_mac(qr, v[r].x, v[r].z, h.x, h.z);
+                    dacc_mac(qr, -v[r].y, -v[r].w, h.y, h.w);
+                    dacc_mac(qi, v[r].x, v[r].z, h.y, h.w);
+                    dacc_mac(qi, v[r].y, v[r].w, h.x, h.z);
+                    dacc_mac(xr, v[r].x, v[r].z, g.x, g.z);
+                    dacc_mac(xr, -v[r].y, -v[r].w, g.y, g.w);
+                    dacc_mac(xi, v[r].x, v[r].z, g.y, g.w);
+                    dacc_mac(xi, v[r].y, v[r].w, g.x, g.z);
+                }
+            }
+        }
+        const df inu = df_from_double(a.inv_beta[c]);
+        const df q0 = df_mul(dacc_result(qr), inu), q1 = df_mul(dacc_result(qi), inu);
+        const float4 g = cn_[j];
+        dacc_mac(xr, q0.hi, q0.lo, g.x, g.z);
+        dacc_mac(xr, -q1.hi, -q1.lo, g.y, g.w);
+        dacc_mac(xi, q0.hi, q0.lo, g.y, g.w);
+        dacc_mac(xi, q1.hi, q1.lo, g.x, g.z);
+        const df x0 = df_mul(dacc_result(xr), inu), x1 = df_mul(dacc_result(xi), inu);
+        const_cast<float4 *>(a.Vb)[(long)j * a.bs_i + (long)c * a.bs_c + e] = make_float4(q0.hi, q1.hi, q0.lo, q1.lo);
+        a.U[(long)c * a.n + e] = make_float4(x0.hi, x1.hi, x0.lo, x1.lo);
+    }
+    pdl_trigger();
+}
+
 // y = H^{-1} g (upper triangular, steps[c] x steps[c]) for column c = blockIdx.x,
 // in double-float.  Column-oriented back substitution: one diagonal division
 // per step, the remaining right-hand side updated in parallel.
@@ -640,6 +917,7 @@ static void free_work(GmresWork *g) {
     cudaFree(g->target); cudaFree(g->active); cudaFree(g->steps); cudaFree(g->bdown); cudaFree(g->mlimit);
     cudaFree(g->d_j); cudaFree(g->d_any); cudaFree(g->io); cudaFree(g->act_cycle);
     cudaFree(g->counters); cudaFree(g->d_any_step); cudaFree(g->act_prod);
+    cudaFree(g->U); cudaFree(g->cco); cudaFree(g->hpre); cudaFree(g->Horig);
     cudaFreeHost(g->h_any);
     delete g;
 }
@@ -651,7 +929,8 @@ void gmres_free(Plan *p) {
 }
 
 static long norm_pstride(int m, long len) {
-    return std::max((long)(m + 1) * ((len + kDotNE - 1) / kDotNE), (len + kStepNB - 1) / kStepNB);
+    // dots: two slots (s and t of delayed CGS2) per basis vector and chunk; norms: one per block
+    return std::max(2L * (m + 1) * ((len + kDotNE - 1) / kDotNE), (len + kStepNB - 1) / kStepNB);
 }
 
 // Workspace for k Krylov columns of length n; the product sees kp columns of
@@ -692,6 +971,10 @@ static int ensure_work(Plan *p, int m, int k, long nv, int kp, bool flex, bool h
     alloc(&g->gv, sizeof(float4) * (size_t)k * (m + 1));
     alloc(&g->sn, sizeof(float4) * (size_t)k * m);
     alloc(&g->hco, sizeof(float4) * (size_t)k * (m + 1));
+    alloc(&g->cco, sizeof(float4) * (size_t)k * (m + 1));
+    alloc(&g->hpre, sizeof(float4) * (size_t)k * (m + 1));
+    alloc(&g->Horig, sizeof(float4) * (size_t)k * (m + 1) * m);
+    alloc(&g->U, sizeof(float4) * k * n);
     alloc(&g->ycoef, sizeof(float4) * (size_t)k * (m + 1));
     alloc(&g->part, sizeof(float4) * (size_t)pstride);
     alloc(&g->cs, sizeof(float2) * (size_t)k * m);
@@ -772,7 +1055,7 @@ static int arnoldi_step(Plan *p, GmresWork *g, int inner, int j) {
     a.ich = (int)(((long)a.nblk_dot * (j + 1) + kDotIW - 1) / kDotIW);
     a.nblk_vec = g->nblk;
     a.part = g->part;
-    a.pstride = std::max((long)(m + 1) * a.nblk_dot, (long)g->nblk);
+    a.pstride = norm_pstride(m, n);
     a.hco = g->hco;
     a.hacc = g->hacc;
     a.cnt_a = g->counters;
@@ -813,10 +1096,96 @@ static int arnoldi_step(Plan *p, GmresWork *g, int inner, int j) {
     return check_cuda(p, cudaGetLastError(), "Arnoldi step launch");
 }
 
+
+static DcgsArgs dcgs_args(Plan *p, GmresWork *g, int j) {
+    DcgsArgs a{};
+    const long n = g->n;
+    a.Vb = g->Vb;
+    a.U = g->U;
+    a.X = g->W;
+    a.n = n;
+    a.bs_i = (long)g->k * n;
+    a.bs_c = n;
+    a.m = g->m;
+    a.k = g->k;
+    a.dot_sub = 1;
+    while ((n + (long)kDotNE * a.dot_sub - 1) / ((long)kDotNE * a.dot_sub) > 4096) a.dot_sub <<= 1;
+    a.nblk_dot = (int)((n + (long)kDotNE * a.dot_sub - 1) / ((long)kDotNE * a.dot_sub));
+    a.ich = (int)(((long)a.nblk_dot * (j + 1) + kDotIW - 1) / kDotIW);
+    a.nblk_vec = g->nblk;
+    a.part = g->part;
+    a.pstride = norm_pstride(g->m, n);
+    a.sco = g->hco;
+    a.cco = g->cco;
+    a.hpre = g->hpre;
+    a.Horig = g->Horig;
+    a.hcol = g->hacc;
+    a.cnt = g->counters;
+    a.active = g->active;
+    a.d_any_step = g->d_any_step;
+    a.H = g->H;
+    a.gv = g->gv;
+    a.sn = g->sn;
+    a.cs = g->cs;
+    a.inv_beta = g->inv_beta;
+    a.steps = g->steps;
+    a.bdown = g->bdown;
+    a.mlimit = g->mlimit;
+    a.target = g->target;
+    a.err = p->d_err;
+    return a;
+}
+
+static int dcgs_dots_launch(Plan *p, GmresWork *g, int j, int has_x) {
+    const DcgsArgs a = dcgs_args(p, g, j);
+    const size_t smem = (size_t)(7 * g->m + 7 + kDotIW * 32 + g->m + 1) * sizeof(float4);
+    const int tok = prof_begin(p, 3);
+    cudaError_t e = launch_pdl(dcgs_dots_kernel, dim3(a.ich, g->k), dim3(kDotIW * 32), smem, p->stream, a, j, has_x);
+    prof_end(p, tok, 0.0);
+    count_launch(p);
+    if (e != cudaSuccess) return check_cuda(p, e, "delayed CGS2 reduction launch");
+    return BTTB_OK;
+}
+
+// One Arnoldi step with delayed CGS2 (unpreconditioned): x = A u_j, the reduction
+// (which closes column j-1 and runs its Givens step), then the update.
+static int arnoldi_step_dcgs(Plan *p, GmresWork *g, int inner, int j) {
+    const int kp = g->kp;
+    const long np = g->np;
+    cudaStream_t st = p->stream;
+    const int *pact = g->active;
+    if (g->glob) {
+        bcast_active_kernel<<<(kp + 255) / 256, 256, 0, st>>>(g->active, g->act_prod, kp);
+        count_launch(p);
+        pact = g->act_prod;
+    }
+    int rc = matvec_run(p, g->U, FMT_CDF, np, g->W, FMT_CDF, np, kp, inner, nullptr, 0, nullptr, pact);
+    if (rc != BTTB_OK) return rc;
+    if ((rc = dcgs_dots_launch(p, g, j, 1)) != BTTB_OK) return rc;
+    const DcgsArgs a = dcgs_args(p, g, j);
+    const size_t smem = (size_t)(2 * g->m + 2) * sizeof(float4);
+    const dim3 vgrid(a.nblk_vec, g->k);
+    const int tok = prof_begin(p, 4);
+    cudaError_t e;
+    if (!p->in_batch && (long)a.nblk_vec * g->k < 4L * p->nsm)
+        e = launch_pdl(dcgs_update_kernel<16>, vgrid, dim3(kStepNB), smem, st, a, j);
+    else
+        e = launch_pdl(dcgs_update_kernel<4>, vgrid, dim3(kStepNB), smem, st, a, j);
+    prof_end(p, tok, 0.0);
+    count_launch(p);
+    if (e != cudaSuccess) return check_cuda(p, e, "delayed CGS2 update launch");
+    return check_cuda(p, cudaGetLastError(), "Arnoldi step launch");
+}
+
 // Back substitution and x += (preconditioned) basis * y for the columns of this cycle.
 static int cycle_finish(Plan *p, GmresWork *g) {
     const int m = g->m, k = g->k;
     const long n = g->n, bs_i = (long)k * n, bs_c = n;
+    if (g->dcgs) {
+        // close the cycle's last column (a reduction without x)
+        const int rc = dcgs_dots_launch(p, g, m, 0);
+        if (rc != BTTB_OK) return rc;
+    }
     const int vgrid = (int)std::min<long>((n + kVecThreads - 1) / kVecThreads, 1024);
     finish_kernel<<<k, kFinishThreads, (m + 1) * sizeof(double2), p->stream>>>(g->H, g->gv, g->steps, g->ycoef, m,
                                                                                g->act_cycle);
@@ -845,7 +1214,7 @@ static int build_cycle_graph(Plan *p, GmresWork *g, int inner) {
     int rc = BTTB_OK;
     for (int step = 0; step < g->m && rc == BTTB_OK; ++step) {
         p->sink_step = step;
-        rc = arnoldi_step(p, g, inner, step);
+        rc = g->dcgs ? arnoldi_step_dcgs(p, g, inner, step) : arnoldi_step(p, g, inner, step);
     }
     p->sink_step = g->m;
     if (rc == BTTB_OK) rc = cycle_finish(p, g);
@@ -865,6 +1234,7 @@ static int build_cycle_graph(Plan *p, GmresWork *g, int inner) {
     if (e != cudaSuccess) return check_cuda(p, e, "graph instantiate");
     g->graph_inner = inner;
     g->graph_pc = g->pc;
+    g->graph_dcgs = g->dcgs;
     g->graph_prof = p->prof;
     return BTTB_OK;
 }
@@ -884,6 +1254,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
     if (rc != BTTB_OK) return rc;
     GmresWork *g = p->gw;
     g->pc = o->pc;
+    g->dcgs = o->pc == BTTB_PC_NONE && !(o->flags & BTTB_GMRES_CGS2);
     const long bs_i = (long)kg * nv, bs_c = nv;  // basis layout [i][c][nv]
     cudaStream_t st = p->stream;
     cudaError_t e;
@@ -1023,17 +1394,20 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
         cudaMemsetAsync(g->d_any_step, 0, sizeof(int), st);
         cycle_start_kernel<<<1, 256, 0, st>>>(g->beta2, g->gv, g->inv_beta, m, kg, g->active);
         count_launch(p);
-        scale_kernel<<<dim3(kgrid, kg), kVecThreads, 0, st>>>(g->R, g->Vb, bs_i, bs_c, 0, g->inv_beta, nv,
-                                                              g->active);
+        // the first basis vector r/beta: into the basis (CGS2) or as u_0 (delayed CGS2)
+        scale_kernel<<<dim3(kgrid, kg), kVecThreads, 0, st>>>(g->R, g->dcgs ? g->U : g->Vb, g->dcgs ? bs_c : bs_i,
+                                                              bs_c, 0, g->inv_beta, nv, g->active);
         count_launch(p);
         if (use_graph) {
-            if (!g->cycle_exec || g->graph_inner != inner || g->graph_pc != g->pc || g->graph_prof != p->prof)
+            if (!g->cycle_exec || g->graph_inner != inner || g->graph_pc != g->pc || g->graph_prof != p->prof ||
+                g->graph_dcgs != (int)g->dcgs)
                 if ((rc = build_cycle_graph(p, g, inner)) != BTTB_OK) return rc;
             if ((e = cudaGraphLaunch(g->cycle_exec, st)) != cudaSuccess) return check_cuda(p, e, "graph launch");
             p->launches += g->launches_per_cycle;
         } else {
             for (int step = 0; step < m; ++step) {
-                if ((rc = arnoldi_step(p, g, inner, step)) != BTTB_OK) return rc;
+                rc = g->dcgs ? arnoldi_step_dcgs(p, g, inner, step) : arnoldi_step(p, g, inner, step);
+                if (rc != BTTB_OK) return rc;
                 e = cudaMemcpyAsync(g->h_any, g->d_any_step, sizeof(int), cudaMemcpyDeviceToHost, st);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(st);
                 if (e != cudaSuccess) return check_cuda(p, e, "Arnoldi step");

@@ -94,6 +94,29 @@ __device__ __forceinline__ void warp_reduce_dacc(dacc &a) {
     }
 }
 
+// Sum of n partials {re.hi, im.hi, re.lo, im.lo} by one warp: each lane issues its loads eight at
+// a time before adding them (in the same per-lane order as a plain loop), then the warp reduces.
+__device__ __forceinline__ void warp_sum_partials(const float4 *pp, int n, dacc &re, dacc &im) {
+    const int lane = threadIdx.x & 31;
+    re = dacc{0.f, 0.f};
+    im = dacc{0.f, 0.f};
+    for (int e0 = lane; e0 < n; e0 += 32 * 8) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + 32 * u;
+            v[u] = e < n ? __ldcg(pp + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            dacc_add(re, dacc{v[u].x, v[u].z});
+            dacc_add(im, dacc{v[u].y, v[u].w});
+        }
+    }
+    warp_reduce_dacc(re);
+    warp_reduce_dacc(im);
+}
+
 // ||x_c||^2 partials: part[c*pstride + blk] over the block's chunk of NB entries.
 __global__ void __launch_bounds__(kVecThreads) norm_partial_kernel(const float4 *x, long n, int NB, int nblk,
                                                                    long pstride, float4 *part) {
@@ -121,12 +144,8 @@ __global__ void __launch_bounds__(kVecThreads) norm_partial_kernel(const float4 
 // beta2[c] = sum of the column's partials (one warp per column).
 __global__ void norm_final_kernel(const float4 *part, int nblk, long pstride, double *beta2) {
     const int c = blockIdx.x, lane = threadIdx.x;
-    dacc acc{0.f, 0.f};
-    for (int e = lane; e < nblk; e += 32) {
-        const float4 v = part[(long)c * pstride + e];
-        dacc_add(acc, dacc{v.x, v.z});
-    }
-    warp_reduce_dacc(acc);
+    dacc acc, unused;
+    warp_sum_partials(part + (long)c * pstride, nblk, acc, unused);
     if (lane == 0) beta2[c] = df_to_double(dacc_result(acc));
 }
 
@@ -462,15 +481,8 @@ __global__ void __launch_bounds__(kDotIW * 32) step_dots_kernel(const StepArgs a
     pdl_trigger();
     if (!arrive_last(counter + c, (int)gridDim.x)) return;
     for (int ii = warp; ii < cnt; ii += kDotIW) {
-        const float4 *pp = part + (long)ii * a.nblk_dot;
-        dacc re{0.f, 0.f}, im{0.f, 0.f};
-        for (int e = lane; e < a.nblk_dot; e += 32) {
-            const float4 v = __ldcg(pp + e);
-            dacc_add(re, dacc{v.x, v.z});
-            dacc_add(im, dacc{v.y, v.w});
-        }
-        warp_reduce_dacc(re);
-        warp_reduce_dacc(im);
+        dacc re, im;
+        warp_sum_partials(part + (long)ii * a.nblk_dot, a.nblk_dot, re, im);
         if (lane == 0) {
             const df r = dacc_result(re), q = dacc_result(im);
             const long hidx = (long)c * (a.m + 1) + ii;
@@ -554,12 +566,8 @@ __global__ void __launch_bounds__(kStepNB) step_update_kernel(const StepArgs a, 
     }
     if (!arrive_last(a.cnt_c + c, a.nblk_vec)) return;
     if (warp == 0) {
-        dacc t{0.f, 0.f};
-        for (int b2 = lane; b2 < a.nblk_vec; b2 += 32) {
-            const float4 v = __ldcg(part + b2);
-            dacc_add(t, dacc{v.x, v.z});
-        }
-        warp_reduce_dacc(t);
+        dacc t, unused;
+        warp_sum_partials(part, a.nblk_vec, t, unused);
         const double beta2 = df_to_double(dacc_result(t));
         const int cont = givens_column(c, j, a.m, dyn + (a.m + 1), a.H, a.hacc, beta2, a.cs, a.sn, a.gv, a.active,
                                        a.steps, a.bdown, a.mlimit, a.target, a.inv_beta, a.err);
@@ -687,15 +695,8 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
     float4 *hs = gscr + (4 * m + 4);
     for (int q = warp; q < 2 * (j + 1); q += kDotIW) {
         const int slot = q <= j ? q : (m + 1) + (q - j - 1);
-        const float4 *pp = part + (long)slot * a.nblk_dot;
-        dacc re{0.f, 0.f}, im{0.f, 0.f};
-        for (int e = lane; e < a.nblk_dot; e += 32) {
-            const float4 v = __ldcg(pp + e);
-            dacc_add(re, dacc{v.x, v.z});
-            dacc_add(im, dacc{v.y, v.w});
-        }
-        warp_reduce_dacc(re);
-        warp_reduce_dacc(im);
+        dacc re, im;
+        warp_sum_partials(part + (long)slot * a.nblk_dot, a.nblk_dot, re, im);
         if (lane == 0) {
             const df r = dacc_result(re), z = dacc_result(im);
             (q <= j ? ssm[q] : tsm[q - j - 1]) = make_float4(r.hi, z.hi, r.lo, z.lo);

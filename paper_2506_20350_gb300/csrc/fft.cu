@@ -174,13 +174,13 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int o = blockIdx.x, c = blockIdx.z;
-    pdl_wait();
-    if (a.active && !a.active[c]) return;                  // finished column (uniform per CTA)
     const int p0 = blockIdx.y * a.P;
     const int P = a.P, lP = a.log2P, M = a.M;
-
+    // the twiddles are constant: stage them before waiting for the preceding kernel
     const C *twg = reinterpret_cast<const C *>(a.tw);
     for (int i = tid; i < M + 5; i += nt) tw[i] = twg[i];
+    pdl_wait();
+    if (a.active && !a.active[c]) return;                  // finished column (uniform per CTA)
 
     long ibase = (long)c * a.in_cs + (long)o * a.in_os;
     if (a.in_sel) ibase += (long)(*a.in_sel) * a.in_sel_stride;

@@ -239,7 +239,7 @@ __device__ __forceinline__ dfc shfl_dfc(dfc v, int src) {
 // run of consecutive rotations) instead of applying them one after another.
 // Lane 0 then forms the new rotation.  Returns (on every lane) whether the
 // column continues.  Scratch `wsm`: 4m+4 float4.
-__device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const float4 *hacc, double beta2,
+__device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const float4 *ha, double beta2,
                              float2 *cs, float4 *sn, float4 *gv, int *active, int *steps, int *bdown,
                              const int *mlimit, const double *target, double *inv_beta, int *err) {
     const int lane = threadIdx.x & 31;
@@ -248,7 +248,6 @@ __device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const 
     float2 *csw = reinterpret_cast<float2 *>(snw + m);          // m entries (m float4 reserved)
     float4 *hout = snw + 2 * m;                                 // m+1 entries
     float4 *Hc = H + (long)c * (m + 1) * m;
-    const float4 *ha = hacc + (long)c * (m + 1);
     float zn2 = 0.f;
     for (int i = lane; i <= j; i += 32) {
         const float4 h = ha[i];
@@ -569,7 +568,8 @@ __global__ void __launch_bounds__(kStepNB) step_update_kernel(const StepArgs a, 
         dacc t, unused;
         warp_sum_partials(part, a.nblk_vec, t, unused);
         const double beta2 = df_to_double(dacc_result(t));
-        const int cont = givens_column(c, j, a.m, dyn + (a.m + 1), a.H, a.hacc, beta2, a.cs, a.sn, a.gv, a.active,
+        const int cont = givens_column(c, j, a.m, dyn + (a.m + 1), a.H, a.hacc + (long)c * (a.m + 1), beta2, a.cs,
+                                       a.sn, a.gv, a.active,
                                        a.steps, a.bdown, a.mlimit, a.target, a.inv_beta, a.err);
         if (lane == 0 && cont) atomicMax(a.d_any_step, j + 1);
     }
@@ -642,15 +642,18 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
     pdl_wait();
     if (!a.active[c]) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long t = (long)blockIdx.x * kDotIW + warp;
-    const int i = (int)(t / a.nblk_dot), blk = (int)(t - (long)i * a.nblk_dot);
+    // CTA (vector i, group cb of kDotIW chunks); warp w takes chunk cb*kDotIW + w
+    const int cpv = (a.nblk_dot + kDotIW - 1) / kDotIW;
+    const int i = blockIdx.x / cpv, cb = blockIdx.x - i * cpv;
+    const int blk = cb * kDotIW + warp;
     float4 *part = a.part + (long)c * a.pstride;
-    if (i <= j) {
+    __shared__ dacc cred[kDotIW][4];
+    dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
+    if (i <= j && blk < a.nblk_dot) {
         // i < j: (q_i, u) and (q_i, x); i == j: (u, u) and (u, x)
         const float4 *uv = a.U + (long)c * a.n;
         const float4 *xv = a.X + (long)c * a.n;
         const float4 *qv = i < j ? a.Vb + (long)i * a.bs_i + (long)c * a.bs_c : uv;
-        dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
         for (int sc = 0; sc < a.dot_sub; ++sc) {
             const long n0 = ((long)blk * a.dot_sub + sc) * kDotNE;
             const int len = (int)max(0L, min((long)kDotNE, a.n - n0));
@@ -680,11 +683,25 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
         warp_reduce_dacc(si);
         warp_reduce_dacc(tr);
         warp_reduce_dacc(ti);
-        if (lane == 0) {
-            const df a0 = dacc_result(sr), a1 = dacc_result(si), b0 = dacc_result(tr), b1 = dacc_result(ti);
-            part[(long)i * a.nblk_dot + blk] = make_float4(a0.hi, a1.hi, a0.lo, a1.lo);
-            part[(long)(a.m + 1 + i) * a.nblk_dot + blk] = make_float4(b0.hi, b1.hi, b0.lo, b1.lo);
-        }
+    }
+    // the CTA's warps are summed in warp order into one partial per quantity
+    if (lane == 0) {
+        cred[warp][0] = sr;
+        cred[warp][1] = si;
+        cred[warp][2] = tr;
+        cred[warp][3] = ti;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && i <= j) {
+        dacc acc = cred[0][threadIdx.x];
+        for (int w = 1; w < kDotIW; ++w) dacc_add(acc, cred[w][threadIdx.x]);
+        const df r = dacc_result(acc);
+        cred[0][threadIdx.x] = dacc{r.hi, r.lo};
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && i <= j) {
+        part[(long)i * cpv + cb] = make_float4(cred[0][0].S, cred[0][1].S, cred[0][0].s, cred[0][1].s);
+        part[(long)(a.m + 1 + i) * cpv + cb] = make_float4(cred[0][2].S, cred[0][3].S, cred[0][2].s, cred[0][3].s);
     }
     pdl_trigger();
     if (!arrive_last(a.cnt + c, (int)gridDim.x)) return;
@@ -693,13 +710,39 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
     float4 *ssm = dsm, *tsm = dsm + (m + 1);
     float4 *gscr = dsm + 2 * (m + 1);
     float4 *hs = gscr + (4 * m + 4);
-    for (int q = warp; q < 2 * (j + 1); q += kDotIW) {
-        const int slot = q <= j ? q : (m + 1) + (q - j - 1);
-        dacc re, im;
-        warp_sum_partials(part + (long)slot * a.nblk_dot, a.nblk_dot, re, im);
-        if (lane == 0) {
-            const df r = dacc_result(re), z = dacc_result(im);
-            (q <= j ? ssm[q] : tsm[q - j - 1]) = make_float4(r.hi, z.hi, r.lo, z.lo);
+    // sums q < 2(j+1) (s_q for q <= j, then t): warp w takes q = w, w+8, ...; for up to kSumB of its sums
+    // at a time a lane loads its partials of all of them before adding (same per-sum order as one at a time)
+    {
+        constexpr int kSumB = 4;
+        const int nsum = 2 * (j + 1);
+        for (int q0 = warp; q0 < nsum; q0 += kDotIW * kSumB) {
+            dacc re[kSumB], im[kSumB];
+#pragma unroll
+            for (int u = 0; u < kSumB; ++u) re[u] = im[u] = dacc{0.f, 0.f};
+            for (int e0 = lane; e0 < cpv; e0 += 32) {
+                float4 v[kSumB];
+#pragma unroll
+                for (int u = 0; u < kSumB; ++u) {
+                    const int q = q0 + u * kDotIW;
+                    const int slot = q <= j ? q : (m + 1) + (q - j - 1);
+                    v[u] = q < nsum ? __ldcg(part + (long)slot * cpv + e0) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < kSumB; ++u) {
+                    dacc_add(re[u], dacc{v[u].x, v[u].z});
+                    dacc_add(im[u], dacc{v[u].y, v[u].w});
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSumB; ++u) {
+                warp_reduce_dacc(re[u]);
+                warp_reduce_dacc(im[u]);
+                const int q = q0 + u * kDotIW;
+                if (lane == 0 && q < nsum) {
+                    const df r = dacc_result(re[u]), z = dacc_result(im[u]);
+                    (q <= j ? ssm[q] : tsm[q - j - 1]) = make_float4(r.hi, z.hi, r.lo, z.lo);
+                }
+            }
         }
     }
     __syncthreads();
@@ -733,9 +776,35 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
     __syncthreads();
     const df nu{s_nu.x, s_nu.z}, inu{s_nu.y, s_nu.w};
     float4 *Hoc = a.Horig + (long)c * (m + 1) * m;
+    // H s (rows 0..j) from the unrotated columns 0..j-1 (column q has rows 0..q+1) and c_j = (tau - s^H t)/nu
+    // do not depend on the Givens step of column j-1: warps 1.. compute them while warp 0 runs it (all
+    // warps when j = 0).  Thread (row r, group g) sums the columns q = g, g+G, ... of row r; the G partial
+    // sums of a row are added in group order afterwards.
+    const int R = j + 1;
+    const int hs_t0 = j >= 1 ? 32 : 0;
+    const int G = max(1, min(j, ((int)blockDim.x - hs_t0) / R));   // no more groups than columns
+    float4 *hpart = hs + (m + 1);                         // R*G partial sums (hs itself holds column j-1 first)
+    auto hs_partials = [&]() {
+        const int tt = (int)threadIdx.x - hs_t0;
+        if (has_x && tt >= 0 && tt < R * G) {
+            const int r = tt % R, gq = tt / R;
+            dfc acc{df{0.f, 0.f}, df{0.f, 0.f}};
+            for (int q = max(r - 1, 0) + ((gq - max(r - 1, 0) % G) % G + G) % G; q < j; q += G)
+                acc = dfc_add(acc, dfc_mul(dfc_load(*reinterpret_cast<const cdf *>(&Hoc[(long)q * (m + 1) + r])),
+                                           dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
+            const cdf st = dfc_store(acc);
+            hpart[gq * R + r] = make_float4(st.rh, st.ih, st.rl, st.il);
+        }
+        if (has_x && (int)threadIdx.x == hs_t0) {
+            const dfc cj = dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&tsm[j])),
+                                   dfc_load(*reinterpret_cast<const cdf *>(&s_sht)));
+            const cdf st = dfc_store(dfc_scale(cj, inu));
+            tsm[j] = make_float4(st.rh, st.ih, st.rl, st.il);
+        }
+    };
     if (j >= 1) {
         // close column j-1: entries hpre + s (rows 0..j-1), subdiagonal nu
-        float4 *fc = a.hcol + (long)c * (m + 1);
+        float4 *fc = hs;                                  // the closed column, rows 0..j-1
         const float4 *hp = a.hpre + (long)c * (m + 1);
         for (int q = threadIdx.x; q < j; q += blockDim.x) {
             const dfc v = dfc_add(dfc_load(*reinterpret_cast<const cdf *>(&hp[q])),
@@ -745,42 +814,24 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
             Hoc[(long)(j - 1) * (m + 1) + q] = fc[q];
         }
         if (threadIdx.x == 0) Hoc[(long)(j - 1) * (m + 1) + j] = make_float4(nu.hi, 0.f, nu.lo, 0.f);
-        __threadfence_block();
         __syncthreads();
         if (warp == 0) {
             const double nu2d = df_to_double(df_mul(nu, nu));
-            const int cont = givens_column(c, j - 1, m, gscr, a.H, a.hcol, nu2d, a.cs, a.sn, a.gv, a.active,
+            const int cont = givens_column(c, j - 1, m, gscr, a.H, fc, nu2d, a.cs, a.sn, a.gv, a.active,
                                            a.steps, a.bdown, a.mlimit, a.target, a.inv_beta, a.err);
             if (lane == 0) s_cont = cont;
+        } else {
+            hs_partials();
         }
         __syncthreads();
         if (!s_cont || !has_x) return;
     } else {
         if (threadIdx.x == 0) a.inv_beta[c] = df_to_double(inu);
+        hs_partials();
+        __syncthreads();
     }
     if (!has_x) return;
     if (threadIdx.x == 0) atomicMax(a.d_any_step, j + 1);
-    // H s (rows 0..j) from the unrotated columns 0..j-1 (column q has rows 0..q+1): thread (row r,
-    // group g) sums the columns q = g, g+G, ... of row r; the G partial sums of a row are then added
-    // in group order.  Meanwhile thread 0 forms c_j = (tau - s^H t)/nu.
-    const int R = j + 1, G = max(1, (int)blockDim.x / R);
-    float4 *hpart = hs + (m + 1);                         // R*G partial sums
-    if ((int)threadIdx.x < R * G) {
-        const int r = threadIdx.x % R, gq = threadIdx.x / R;
-        dfc acc{df{0.f, 0.f}, df{0.f, 0.f}};
-        for (int q = max(r - 1, 0) + ((gq - max(r - 1, 0) % G) % G + G) % G; q < j; q += G)
-            acc = dfc_add(acc, dfc_mul(dfc_load(*reinterpret_cast<const cdf *>(&Hoc[(long)q * (m + 1) + r])),
-                                       dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
-        const cdf st = dfc_store(acc);
-        hpart[gq * R + r] = make_float4(st.rh, st.ih, st.rl, st.il);
-    }
-    if (threadIdx.x == 0) {
-        const dfc cj = dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&tsm[j])),
-                               dfc_load(*reinterpret_cast<const cdf *>(&s_sht)));
-        const cdf st = dfc_store(dfc_scale(cj, inu));
-        tsm[j] = make_float4(st.rh, st.ih, st.rl, st.il);
-    }
-    __syncthreads();
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
         dfc acc = dfc_load(*reinterpret_cast<const cdf *>(&hpart[r]));
         for (int gq = 1; gq < G; ++gq) acc = dfc_add(acc, dfc_load(*reinterpret_cast<const cdf *>(&hpart[gq * R + r])));
@@ -1112,7 +1163,7 @@ static DcgsArgs dcgs_args(Plan *p, GmresWork *g, int j) {
     a.dot_sub = 1;
     while ((n + (long)kDotNE * a.dot_sub - 1) / ((long)kDotNE * a.dot_sub) > 4096) a.dot_sub <<= 1;
     a.nblk_dot = (int)((n + (long)kDotNE * a.dot_sub - 1) / ((long)kDotNE * a.dot_sub));
-    a.ich = (int)(((long)a.nblk_dot * (j + 1) + kDotIW - 1) / kDotIW);
+    a.ich = (int)((long)((a.nblk_dot + kDotIW - 1) / kDotIW) * (j + 1));   // CTAs: chunk groups x vectors
     a.nblk_vec = g->nblk;
     a.part = g->part;
     a.pstride = norm_pstride(g->m, n);

@@ -120,6 +120,24 @@ def test_tensor_core_product(bt, nx, ny, b, k):
     _check(y, ref, FP32_TOL, "tensor-core product")
 
 
+@pytest.mark.parametrize("nx", list(range(1, 41)))
+def test_product_every_fft_length(bt, nx):
+    """nx = 1..40 makes the plan pick every padded length smallest_5smooth(2 nx - 1) up to 80 (1, 3, 5, 8,
+    9, 12, 15, 18, 20, 24, 25, 27, 30, 32, 36, 40, 45, 48, 50, 54, 60, 64, 72, 75, 80): every radix-2/3/4/5
+    stage combination of the FFT passes, forward and inverse, checked through the product."""
+    ny, b = 2, 3
+    gen = arrays.random_generator_blocks(nx, ny, b, seed=500 + nx)
+    plan = bt.Plan(nx, ny, b, max_rhs=2, prec_mask=ALL_PRECS)
+    plan.set_generators(gen)
+    x = _rand(np.random.default_rng(nx), 2, plan.n)
+    ref = oracle.matvec(gen, x.T).T
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64).cpu().numpy(), ref, FP64_TOL, f"df64 mx={plan.mx}")
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64_NATIVE).cpu().numpy(), ref, FP64_TOL, f"binary64 mx={plan.mx}")
+    _check(plan.matvec(_dev(x.astype(np.complex64)), prec=bt.BTTB_MV_FP32).cpu().numpy(), ref, FP32_TOL,
+           f"binary32 mx={plan.mx}")
+    plan.close()
+
+
 def test_tensor_core_ir_solve(bt):
     """GMRES-IR with tensor-core inner products reaches the FP64-class residual on every column."""
     nx, ny, b = 8, 6, 12

@@ -158,10 +158,12 @@ typedef struct {
  * converged columns masked.
  *
  * Orthogonalisation is classical Gram-Schmidt applied twice (CGS2).  Without a
- * preconditioner the default is its delayed form (the reorthogonalisation of
- * v_j is merged into step j+1's reduction: one reduction and one update over
- * the basis per step, and the residual estimate one step behind);
- * BTTB_GMRES_CGS2 selects the two-pass form. */
+ * preconditioner and with block-Jacobi (a fixed linear operator: plain right
+ * preconditioning, x += P_K^{-1} Q y at the end of each cycle) the default is
+ * its delayed form (the reorthogonalisation of v_j is merged into step j+1's
+ * reduction: one reduction and one update over the basis per step, and the
+ * residual estimate one step behind); the learned preconditioner runs flexible
+ * GMRES with the two-pass form, which BTTB_GMRES_CGS2 selects everywhere. */
 enum { BTTB_GMRES_NO_GRAPH = 1, BTTB_GMRES_GLOBAL = 2, BTTB_GMRES_CGS2 = 4 };
 
 typedef struct {

@@ -150,6 +150,17 @@ __global__ void norm_final_kernel(const float4 *part, int nblk, long pstride, do
 }
 
 // w[c][n] += sgn * sum_{i < cnt_col[c]} B_i[c][n] coef[c][i]
+// x += z (double-float) for the columns active in the cycle.
+__global__ void add_active_kernel(float4 *x, const float4 *z, long n, const int *active) {
+    const int c = blockIdx.y;
+    if (active && !active[c]) return;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const float4 a = x[(long)c * n + e], b = z[(long)c * n + e];
+        const df r = df_add(df{a.x, a.z}, df{b.x, b.z}), q = df_add(df{a.y, a.w}, df{b.y, b.w});
+        x[(long)c * n + e] = make_float4(r.hi, q.hi, r.lo, q.lo);
+    }
+}
+
 __global__ void __launch_bounds__(kVecThreads) update_kernel(const float4 *basis, long bs_i, long bs_c,
                                                              const int *cnt_col, const float4 *coef, int maxcnt,
                                                              float4 *w, long n, float sgn, const int *active) {
@@ -1211,7 +1222,15 @@ static int arnoldi_step_dcgs(Plan *p, GmresWork *g, int inner, int j) {
         count_launch(p);
         pact = g->act_prod;
     }
-    int rc = matvec_run(p, g->U, FMT_CDF, np, g->W, FMT_CDF, np, kp, inner, nullptr, 0, nullptr, pact);
+    // x = A u_j, or x = A P_K^{-1} u_j with block-Jacobi (fixed, linear: plain right preconditioning)
+    const float4 *src = g->U;
+    int rc;
+    if (g->pc == BTTB_PC_BLOCK_JACOBI) {
+        if ((rc = block_jacobi_run(p, g->U, FMT_CDF, np, g->Zb, FMT_CDF, np, kp, nullptr, 0, pact)) != BTTB_OK)
+            return rc;
+        src = g->Zb;
+    }
+    rc = matvec_run(p, src, FMT_CDF, np, g->W, FMT_CDF, np, kp, inner, nullptr, 0, nullptr, pact);
     if (rc != BTTB_OK) return rc;
     if ((rc = dcgs_dots_launch(p, g, j, 1)) != BTTB_OK) return rc;
     const DcgsArgs a = dcgs_args(p, g, j);
@@ -1242,9 +1261,23 @@ static int cycle_finish(Plan *p, GmresWork *g) {
     finish_kernel<<<k, kFinishThreads, (m + 1) * sizeof(double2), p->stream>>>(g->H, g->gv, g->steps, g->ycoef, m,
                                                                                g->act_cycle);
     count_launch(p);
-    update_kernel<<<dim3(vgrid, k), kVecThreads, (m + 1) * sizeof(float4), p->stream>>>(
-        g->pc != BTTB_PC_NONE ? g->Zb : g->Vb, bs_i, bs_c, g->steps, g->ycoef, m + 1, g->X, n, 1.f, g->act_cycle);
-    count_launch(p);
+    if (g->dcgs && g->pc == BTTB_PC_BLOCK_JACOBI) {
+        // x += P_K^{-1} (Q y): Q y into R (free until the next cycle's residual), then the preconditioner
+        fill_zero_kernel<<<1024, kVecThreads, 0, p->stream>>>(g->R, (long)k * n);
+        update_kernel<<<dim3(vgrid, k), kVecThreads, (m + 1) * sizeof(float4), p->stream>>>(
+            g->Vb, bs_i, bs_c, g->steps, g->ycoef, m + 1, g->R, n, 1.f, g->act_cycle);
+        count_launch(p, 2);
+        const int rc = block_jacobi_run(p, g->R, FMT_CDF, g->np, g->Zb, FMT_CDF, g->np, g->kp, nullptr, 0,
+                                        g->glob ? nullptr : g->act_cycle);
+        if (rc != BTTB_OK) return rc;
+        add_active_kernel<<<dim3(vgrid, k), kVecThreads, 0, p->stream>>>(g->X, g->Zb, n, g->act_cycle);
+        count_launch(p);
+    } else {
+        update_kernel<<<dim3(vgrid, k), kVecThreads, (m + 1) * sizeof(float4), p->stream>>>(
+            g->pc != BTTB_PC_NONE ? g->Zb : g->Vb, bs_i, bs_c, g->steps, g->ycoef, m + 1, g->X, n, 1.f,
+            g->act_cycle);
+        count_launch(p);
+    }
     return check_cuda(p, cudaGetLastError(), "cycle finish launch");
 }
 
@@ -1306,7 +1339,8 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
     if (rc != BTTB_OK) return rc;
     GmresWork *g = p->gw;
     g->pc = o->pc;
-    g->dcgs = o->pc == BTTB_PC_NONE && !(o->flags & BTTB_GMRES_CGS2);
+    // delayed CGS2 unless the preconditioner is the learned (nonlinear) one, which needs flexible GMRES
+    g->dcgs = (o->pc == BTTB_PC_NONE || o->pc == BTTB_PC_BLOCK_JACOBI) && !(o->flags & BTTB_GMRES_CGS2);
     const long bs_i = (long)kg * nv, bs_c = nv;  // basis layout [i][c][nv]
     cudaStream_t st = p->stream;
     cudaError_t e;

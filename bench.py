@@ -268,6 +268,7 @@ def learned_leg(dev, stream):
     pairs_s = time.perf_counter() - t0
     npairs = rtr.shape[0]
     lrn = bt.Learned(plan, rank=16, channels=64, max_cols=64, seed=c["seed"])
+    plan.autotune(c["ntest"], 3)              # FFT chunk width for the 50-column products and applications
     Vte = torch.from_numpy(arrays.random_port_excitations(nx, ny, b, c["ntest"], seed=c["test_seed"]).T.copy()).to(dev)
     steps, batch, lr = 1500, 64, 1e-3
     gen_t = torch.Generator().manual_seed(c["seed"])
@@ -353,6 +354,7 @@ def run_ours(args):
     all_prec = (1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_FP32) | (1 << bt.BTTB_MV_FP64_NATIVE)
     plan = bt.Plan(nx, ny, b, max_rhs=1, prec_mask=all_prec, stream=stream)
     plan.set_generators(gen)
+    fft_width = plan.autotune(1, 10)          # FFT batch-chunk width for one-column products
     n, mx, my = plan.n, plan.mx, plan.my
     v_host = arrays.centre_excitation(nx, ny, b)[None, :].copy()
     V = torch.from_numpy(v_host).to(dev)
@@ -607,6 +609,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32 products + df64 (double-float) residual/Arnoldi",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "b": b, "grid": [mx, my], "seed": c["seed"],
+                   "fft_chunk_width": fft_width,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: every product streams the 104-207 MB spectrum"},
         "roofline": roofline,

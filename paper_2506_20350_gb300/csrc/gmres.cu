@@ -352,7 +352,7 @@ __device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const 
             if (done) {
                 active[c] = 0;
             } else {
-                inv_beta[c] = 1.0 / df_to_double(beta);
+                if (inv_beta) inv_beta[c] = 1.0 / df_to_double(beta);
                 cont = 1;
             }
         }
@@ -636,6 +636,7 @@ struct DcgsArgs {
     float4 *part;
     long pstride;
     float4 *sco, *cco, *hpre, *Horig, *hcol;   // [c][m+1] x 4, Horig [c][(m+1)*m]
+    double *nu2;          // [c]: subdiagonal^2 of the column the update kernel's Givens CTA closes
     unsigned *cnt;
     int *active, *d_any_step;
     float4 *H, *gv, *sn;
@@ -825,24 +826,32 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
             Hoc[(long)(j - 1) * (m + 1) + q] = fc[q];
         }
         if (threadIdx.x == 0) Hoc[(long)(j - 1) * (m + 1) + j] = make_float4(nu.hi, 0.f, nu.lo, 0.f);
-        __syncthreads();
-        if (warp == 0) {
-            const double nu2d = df_to_double(df_mul(nu, nu));
-            const int cont = givens_column(c, j - 1, m, gscr, a.H, fc, nu2d, a.cs, a.sn, a.gv, a.active,
-                                           a.steps, a.bdown, a.mlimit, a.target, a.inv_beta, a.err);
-            if (lane == 0) s_cont = cont;
-        } else {
+        if (has_x) {
+            // the Givens step of column j-1 runs in an extra CTA of the update kernel, beside the update
+            float4 *hc = a.hcol + (long)c * (m + 1);
+            for (int q = threadIdx.x; q < j; q += blockDim.x) hc[q] = fc[q];
+            if (threadIdx.x == 0) {
+                a.nu2[c] = df_to_double(df_mul(nu, nu));
+                a.inv_beta[c] = df_to_double(inu);
+            }
+            __syncthreads();
             hs_partials();
+            __syncthreads();
+        } else {
+            __syncthreads();
+            if (warp == 0) {
+                const double nu2d = df_to_double(df_mul(nu, nu));
+                givens_column(c, j - 1, m, gscr, a.H, fc, nu2d, a.cs, a.sn, a.gv, a.active, a.steps, a.bdown,
+                              a.mlimit, a.target, a.inv_beta, a.err);
+            }
+            return;
         }
-        __syncthreads();
-        if (!s_cont || !has_x) return;
     } else {
         if (threadIdx.x == 0) a.inv_beta[c] = df_to_double(inu);
         hs_partials();
         __syncthreads();
     }
     if (!has_x) return;
-    if (threadIdx.x == 0) atomicMax(a.d_any_step, j + 1);
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
         dfc acc = dfc_load(*reinterpret_cast<const cdf *>(&hpart[r]));
         for (int gq = 1; gq < G; ++gq) acc = dfc_add(acc, dfc_load(*reinterpret_cast<const cdf *>(&hpart[gq * R + r])));
@@ -865,10 +874,22 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
 // entries loaded UB at a time and shared by both sums.
 template <int UB>
 __global__ void __launch_bounds__(kStepNB) dcgs_update_kernel(const DcgsArgs a, int j) {
-    extern __shared__ __align__(16) float4 csm[];        // -s: j entries, -c: j+1 entries
+    extern __shared__ __align__(16) float4 csm[];        // -s: j entries, -c: j+1 entries; Givens scratch
     const int c = blockIdx.y, blk = blockIdx.x;
     pdl_wait();
     if (!a.active[c]) return;
+    if (blk == a.nblk_vec) {
+        // the extra CTA: Givens step of column j-1 (closed by the reduction), off the update's path
+        if (j >= 1 && threadIdx.x < 32) {
+            const int cont = givens_column(c, j - 1, a.m, csm, a.H, a.hcol + (long)c * (a.m + 1), a.nu2[c], a.cs,
+                                           a.sn, a.gv, a.active, a.steps, a.bdown, a.mlimit, a.target, nullptr,
+                                           a.err);
+            if (threadIdx.x == 0 && cont) atomicMax(a.d_any_step, j + 1);
+        } else if (j == 0 && threadIdx.x == 0) {
+            atomicMax(a.d_any_step, 1);
+        }
+        return;
+    }
     float4 *sn_ = csm, *cn_ = csm + (a.m + 1);
     for (int q = threadIdx.x; q <= j; q += blockDim.x) {
         const long o = (long)c * (a.m + 1) + q;
@@ -1183,6 +1204,7 @@ static DcgsArgs dcgs_args(Plan *p, GmresWork *g, int j) {
     a.hpre = g->hpre;
     a.Horig = g->Horig;
     a.hcol = g->hacc;
+    a.nu2 = g->beta2;
     a.cnt = g->counters;
     a.active = g->active;
     a.d_any_step = g->d_any_step;
@@ -1234,8 +1256,8 @@ static int arnoldi_step_dcgs(Plan *p, GmresWork *g, int inner, int j) {
     if (rc != BTTB_OK) return rc;
     if ((rc = dcgs_dots_launch(p, g, j, 1)) != BTTB_OK) return rc;
     const DcgsArgs a = dcgs_args(p, g, j);
-    const size_t smem = (size_t)(2 * g->m + 2) * sizeof(float4);
-    const dim3 vgrid(a.nblk_vec, g->k);
+    const size_t smem = (size_t)std::max(2 * g->m + 2, 4 * g->m + 4) * sizeof(float4);   // coefficients / Givens
+    const dim3 vgrid(a.nblk_vec + 1, g->k);                                                // + the Givens CTA
     const int tok = prof_begin(p, 4);
     cudaError_t e;
     if (!p->in_batch && (long)a.nblk_vec * g->k < 4L * p->nsm)

@@ -505,7 +505,9 @@ def run_ours(args):
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             im.zero_()
+            torch.cuda.nvtx.range_push("multi_solve")
             _, rcm, resm = planm.solve(vm, im, tol=tol, restart=restart, inner=bt.BTTB_MV_FP32)
+            torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         mt = time.perf_counter() - t0
         its = [r.iters for r in resm]

@@ -633,6 +633,7 @@ struct DcgsArgs {
     long n, bs_i, bs_c;
     int m, k;
     int dot_sub, nblk_dot, ich, nblk_vec;
+    int cmajor;           // 1: a CTA covers its chunks for every vector (u, x read once; many columns)
     float4 *part;
     long pstride;
     float4 *sco, *cco, *hpre, *Horig, *hcol;   // [c][m+1] x 4, Horig [c][(m+1)*m]
@@ -654,66 +655,127 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
     pdl_wait();
     if (!a.active[c]) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // CTA (vector i, group cb of kDotIW chunks); warp w takes chunk cb*kDotIW + w
     const int cpv = (a.nblk_dot + kDotIW - 1) / kDotIW;
-    const int i = blockIdx.x / cpv, cb = blockIdx.x - i * cpv;
-    const int blk = cb * kDotIW + warp;
     float4 *part = a.part + (long)c * a.pstride;
-    __shared__ dacc cred[kDotIW][4];
-    dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
-    if (i <= j && blk < a.nblk_dot) {
-        // i < j: (q_i, u) and (q_i, x); i == j: (u, u) and (u, x)
-        const float4 *uv = a.U + (long)c * a.n;
-        const float4 *xv = a.X + (long)c * a.n;
-        const float4 *qv = i < j ? a.Vb + (long)i * a.bs_i + (long)c * a.bs_c : uv;
-        for (int sc = 0; sc < a.dot_sub; ++sc) {
-            const long n0 = ((long)blk * a.dot_sub + sc) * kDotNE;
-            const int len = (int)max(0L, min((long)kDotNE, a.n - n0));
-            float4 q[kDotPL], u[kDotPL], x[kDotPL];
+    const int npart = a.cmajor ? a.nblk_dot : cpv;         // partials per quantity for the last CTA
+    if (a.cmajor) {
+        // chunk-major: CTA = chunk group blockIdx.x, warp w takes chunk blockIdx.x*kDotIW + w for every
+        // vector i <= j, so the warp reads its entries of u and x once; one partial per warp and quantity
+        const int blk = blockIdx.x * kDotIW + warp;
+        if (blk < a.nblk_dot) {
+            const float4 *uv = a.U + (long)c * a.n;
+            const float4 *xv = a.X + (long)c * a.n;
+            float4 u[kDotPL], x[kDotPL];
+            auto load_ux = [&](long n0, int len) {
 #pragma unroll
-            for (int r = 0; r < kDotPL; ++r) {
-                const int e = lane + 32 * r;
-                const bool in = e < len;
-                q[r] = in ? qv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                u[r] = in ? uv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                x[r] = in && has_x ? xv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int r = 0; r < kDotPL; ++r) {
+                    const int e = lane + 32 * r;
+                    const bool in = e < len;
+                    u[r] = in ? uv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x[r] = in && has_x ? xv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            };
+            if (a.dot_sub == 1) {
+                const long n0 = (long)blk * kDotNE;
+                load_ux(n0, (int)max(0L, min((long)kDotNE, a.n - n0)));
             }
+            for (int i = 0; i <= j; ++i) {
+                const float4 *qv = i < j ? a.Vb + (long)i * a.bs_i + (long)c * a.bs_c : uv;
+                dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
+                for (int sc = 0; sc < a.dot_sub; ++sc) {
+                    const long n0 = ((long)blk * a.dot_sub + sc) * kDotNE;
+                    const int len = (int)max(0L, min((long)kDotNE, a.n - n0));
+                    if (a.dot_sub > 1) load_ux(n0, len);
+                    float4 q[kDotPL];
 #pragma unroll
-            for (int r = 0; r < kDotPL; ++r) {
-                // conj(q) u and conj(q) x, compensated
-                dacc_mac(sr, q[r].x, q[r].z, u[r].x, u[r].z);
-                dacc_mac(sr, q[r].y, q[r].w, u[r].y, u[r].w);
-                dacc_mac(si, q[r].x, q[r].z, u[r].y, u[r].w);
-                dacc_mac(si, -q[r].y, -q[r].w, u[r].x, u[r].z);
-                dacc_mac(tr, q[r].x, q[r].z, x[r].x, x[r].z);
-                dacc_mac(tr, q[r].y, q[r].w, x[r].y, x[r].w);
-                dacc_mac(ti, q[r].x, q[r].z, x[r].y, x[r].w);
-                dacc_mac(ti, -q[r].y, -q[r].w, x[r].x, x[r].z);
+                    for (int r = 0; r < kDotPL; ++r) {
+                        const int e = lane + 32 * r;
+                        q[r] = e < len ? qv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int r = 0; r < kDotPL; ++r) {
+                        dacc_mac(sr, q[r].x, q[r].z, u[r].x, u[r].z);
+                        dacc_mac(sr, q[r].y, q[r].w, u[r].y, u[r].w);
+                        dacc_mac(si, q[r].x, q[r].z, u[r].y, u[r].w);
+                        dacc_mac(si, -q[r].y, -q[r].w, u[r].x, u[r].z);
+                        dacc_mac(tr, q[r].x, q[r].z, x[r].x, x[r].z);
+                        dacc_mac(tr, q[r].y, q[r].w, x[r].y, x[r].w);
+                        dacc_mac(ti, q[r].x, q[r].z, x[r].y, x[r].w);
+                        dacc_mac(ti, -q[r].y, -q[r].w, x[r].x, x[r].z);
+                    }
+                }
+                warp_reduce_dacc(sr);
+                warp_reduce_dacc(si);
+                warp_reduce_dacc(tr);
+                warp_reduce_dacc(ti);
+                if (lane == 0) {
+                    const df a0 = dacc_result(sr), a1 = dacc_result(si), b0 = dacc_result(tr), b1 = dacc_result(ti);
+                    part[(long)i * npart + blk] = make_float4(a0.hi, a1.hi, a0.lo, a1.lo);
+                    part[(long)(a.m + 1 + i) * npart + blk] = make_float4(b0.hi, b1.hi, b0.lo, b1.lo);
+                }
             }
         }
-        warp_reduce_dacc(sr);
-        warp_reduce_dacc(si);
-        warp_reduce_dacc(tr);
-        warp_reduce_dacc(ti);
-    }
-    // the CTA's warps are summed in warp order into one partial per quantity
-    if (lane == 0) {
-        cred[warp][0] = sr;
-        cred[warp][1] = si;
-        cred[warp][2] = tr;
-        cred[warp][3] = ti;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4 && i <= j) {
-        dacc acc = cred[0][threadIdx.x];
-        for (int w = 1; w < kDotIW; ++w) dacc_add(acc, cred[w][threadIdx.x]);
-        const df r = dacc_result(acc);
-        cred[0][threadIdx.x] = dacc{r.hi, r.lo};
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && i <= j) {
-        part[(long)i * cpv + cb] = make_float4(cred[0][0].S, cred[0][1].S, cred[0][0].s, cred[0][1].s);
-        part[(long)(a.m + 1 + i) * cpv + cb] = make_float4(cred[0][2].S, cred[0][3].S, cred[0][2].s, cred[0][3].s);
+    } else {
+        // vector-major: CTA (vector i, group cb of kDotIW chunks); warp w takes chunk cb*kDotIW + w.  The CTAs
+        // of one chunk group are adjacent (i fastest), so they run together and share u and x through L2
+        const int cb = blockIdx.x / (j + 1), i = blockIdx.x - cb * (j + 1);
+        const int blk = cb * kDotIW + warp;
+        __shared__ dacc cred[kDotIW][4];
+        dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
+        if (i <= j && blk < a.nblk_dot) {
+            // i < j: (q_i, u) and (q_i, x); i == j: (u, u) and (u, x)
+            const float4 *uv = a.U + (long)c * a.n;
+            const float4 *xv = a.X + (long)c * a.n;
+            const float4 *qv = i < j ? a.Vb + (long)i * a.bs_i + (long)c * a.bs_c : uv;
+            for (int sc = 0; sc < a.dot_sub; ++sc) {
+                const long n0 = ((long)blk * a.dot_sub + sc) * kDotNE;
+                const int len = (int)max(0L, min((long)kDotNE, a.n - n0));
+                float4 q[kDotPL], u[kDotPL], x[kDotPL];
+    #pragma unroll
+                for (int r = 0; r < kDotPL; ++r) {
+                    const int e = lane + 32 * r;
+                    const bool in = e < len;
+                    q[r] = in ? qv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    u[r] = in ? uv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x[r] = in && has_x ? xv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+    #pragma unroll
+                for (int r = 0; r < kDotPL; ++r) {
+                    // conj(q) u and conj(q) x, compensated
+                    dacc_mac(sr, q[r].x, q[r].z, u[r].x, u[r].z);
+                    dacc_mac(sr, q[r].y, q[r].w, u[r].y, u[r].w);
+                    dacc_mac(si, q[r].x, q[r].z, u[r].y, u[r].w);
+                    dacc_mac(si, -q[r].y, -q[r].w, u[r].x, u[r].z);
+                    dacc_mac(tr, q[r].x, q[r].z, x[r].x, x[r].z);
+                    dacc_mac(tr, q[r].y, q[r].w, x[r].y, x[r].w);
+                    dacc_mac(ti, q[r].x, q[r].z, x[r].y, x[r].w);
+                    dacc_mac(ti, -q[r].y, -q[r].w, x[r].x, x[r].z);
+                }
+            }
+            warp_reduce_dacc(sr);
+            warp_reduce_dacc(si);
+            warp_reduce_dacc(tr);
+            warp_reduce_dacc(ti);
+        }
+        // the CTA's warps are summed in warp order into one partial per quantity
+        if (lane == 0) {
+            cred[warp][0] = sr;
+            cred[warp][1] = si;
+            cred[warp][2] = tr;
+            cred[warp][3] = ti;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4 && i <= j) {
+            dacc acc = cred[0][threadIdx.x];
+            for (int w = 1; w < kDotIW; ++w) dacc_add(acc, cred[w][threadIdx.x]);
+            const df r = dacc_result(acc);
+            cred[0][threadIdx.x] = dacc{r.hi, r.lo};
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && i <= j) {
+            part[(long)i * cpv + cb] = make_float4(cred[0][0].S, cred[0][1].S, cred[0][0].s, cred[0][1].s);
+            part[(long)(a.m + 1 + i) * cpv + cb] = make_float4(cred[0][2].S, cred[0][3].S, cred[0][2].s, cred[0][3].s);
+        }
     }
     pdl_trigger();
     if (!arrive_last(a.cnt + c, (int)gridDim.x)) return;
@@ -731,13 +793,13 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
             dacc re[kSumB], im[kSumB];
 #pragma unroll
             for (int u = 0; u < kSumB; ++u) re[u] = im[u] = dacc{0.f, 0.f};
-            for (int e0 = lane; e0 < cpv; e0 += 32) {
+            for (int e0 = lane; e0 < npart; e0 += 32) {
                 float4 v[kSumB];
 #pragma unroll
                 for (int u = 0; u < kSumB; ++u) {
                     const int q = q0 + u * kDotIW;
                     const int slot = q <= j ? q : (m + 1) + (q - j - 1);
-                    v[u] = q < nsum ? __ldcg(part + (long)slot * cpv + e0) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[u] = q < nsum ? __ldcg(part + (long)slot * npart + e0) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
                 for (int u = 0; u < kSumB; ++u) {
@@ -1195,7 +1257,13 @@ static DcgsArgs dcgs_args(Plan *p, GmresWork *g, int j) {
     a.dot_sub = 1;
     while ((n + (long)kDotNE * a.dot_sub - 1) / ((long)kDotNE * a.dot_sub) > 4096) a.dot_sub <<= 1;
     a.nblk_dot = (int)((n + (long)kDotNE * a.dot_sub - 1) / ((long)kDotNE * a.dot_sub));
-    a.ich = (int)((long)((a.nblk_dot + kDotIW - 1) / kDotIW) * (j + 1));   // CTAs: chunk groups x vectors
+    {
+        const long cpv = (a.nblk_dot + kDotIW - 1) / kDotIW;
+        // many columns of one-piece chunks: each CTA covers all vectors of its chunk group and keeps u and x
+        // in registers; otherwise a CTA per (vector, chunk group) for parallelism
+        a.cmajor = a.dot_sub == 1 && cpv * g->k >= 2L * p->nsm;
+        a.ich = (int)(a.cmajor ? cpv : cpv * (j + 1));
+    }
     a.nblk_vec = g->nblk;
     a.part = g->part;
     a.pstride = norm_pstride(g->m, n);

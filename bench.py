@@ -516,6 +516,26 @@ def run_ours(args):
                  "iters_mean": float(np.mean(its)), "relres_true_max": max(r.relres_true for r in resm),
                  "speedup_vs_fp64_column_by_column": fp64_ms * kall / (mt * 1e3),
                  "workspace_gb": planm.workspace_bytes() / 1e9, "fft_chunk_width": width}
+        # per-kernel breakdown of the first cycle (restart steps), event nodes around every kernel
+        bt.bttb_profile(planm.handle, 2)
+        with torch.cuda.stream(stream):
+            im.zero_()
+            planm.solve(vm, im, tol=tol, restart=restart, inner=bt.BTTB_MV_FP32, max_iters=restart)
+        torch.cuda.synchronize()
+        vec_bytes = nx * ny * b * 16 * kall                  # one double-float Krylov vector of every column
+        # algorithmic traffic of one cycle: the reduction of step j reads q_0..q_{j-1}, u and x (plus the
+        # closing reduction: the basis and u); the update reads q_0..q_{j-1}, u, x and writes q_j, u_{j+1}
+        cyc_bytes = {3: vec_bytes * (sum(j + 2 for j in range(restart)) + restart + 1),
+                     4: vec_bytes * sum(j + 4 for j in range(restart))}
+        cyc = {}
+        for name, kid in {"fft_passes": bt.BTTB_K_FFT, "gs_dots": 3, "gs_update": 4,
+                          "block_product_fp32": bt.BTTB_K_BLOCK_PRODUCT_PREC + bt.BTTB_MV_FP32}.items():
+            st = bt.bttb_profile_read(planm.handle, kid)
+            cyc[name] = {"launches": st.launches, "total_ms": st.ms}
+            if kid in cyc_bytes and st.ms > 0:
+                cyc[name]["achieved_gbs"] = cyc_bytes[kid] / (st.ms / 1e3) / 1e9
+        bt.bttb_profile(planm.handle, 0)
+        multi["first_cycle_breakdown"] = cyc
         # the paper's global GMRES: one Krylov space over vec(I), Frobenius inner products
         with torch.cuda.stream(stream):
             planm.solve(vm, im, tol=tol, restart=restart, inner=bt.BTTB_MV_FP32, max_iters=2,

@@ -163,6 +163,38 @@ __device__ __forceinline__ float2 scale_by<F32>(float2 v, double s) {
 
 constexpr int kFftThreads = 256;
 
+// One Stockham stage of radix R over the P interleaved sequences: thread (pp, j0) takes the butterflies
+// j = j0, j0 + jstep, ... of batch index pp.  With Ns the product of the earlier radices, butterfly j reads
+// src[j + r m] (m = M/R), twiddles inputs r >= 1 by w^(r k tstep) (k = j mod Ns) and writes
+// dst[(j div Ns) Ns R + k + r Ns].  j div Ns is one high multiply by nsmagic = ceil(2^32 / Ns), exact for
+// j, Ns < 2^16.
+template <class A, int R, bool INV>
+__device__ __forceinline__ void fft_stage(const typename A::C *__restrict__ src, typename A::C *__restrict__ dst,
+                                          const typename A::C *tw, int m, int Ns, unsigned nsmagic, int tstep,
+                                          int lP, int pp, int j0, int jstep, typename A::K s3, typename A::K c1,
+                                          typename A::K c2, typename A::K s1, typename A::K s2) {
+    using C = typename A::C;
+    constexpr int sg = INV ? 1 : -1;
+    for (int j = j0; j < m; j += jstep) {
+        const int q = Ns == 1 ? j : (int)__umulhi((unsigned)j, nsmagic);
+        const int k = j - q * Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[((j + r * m) << lP) + pp];
+        if (k != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = A::cmul(v[r], tw[r * k * tstep], INV);
+        }
+        if constexpr (R == 2) Butterfly<A>::r2(v);
+        else if constexpr (R == 3) Butterfly<A>::r3(v, sg, s3);
+        else if constexpr (R == 4) Butterfly<A>::r4(v, sg);
+        else Butterfly<A>::r5(v, sg, c1, c2, s1, s2);
+        const int dbase = q * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[((dbase + r * Ns) << lP) + pp] = v[r];
+    }
+}
+
 template <class A, int INF, int OUTF, bool INV>
 __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) {
     using C = typename A::C;
@@ -170,7 +202,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *buf0 = tw + (a.M + 8);
-    C *buf1 = buf0 + (long)a.M * a.P;
+    C *buf1 = buf0 + a.M * a.P;
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int o = blockIdx.x, c = blockIdx.z;
@@ -199,7 +231,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
     const K s3 = real_const<A>(tw[M + 4]);
     const K c1 = real_const<A>(tw[M + 0]), c2 = real_const<A>(tw[M + 1]);
     const K s1 = real_const<A>(tw[M + 2]), s2 = real_const<A>(tw[M + 3]);
-    const int sg = INV ? 1 : -1;
+    const int pp = tid & (P - 1), j0 = tid >> lP, jstep = nt >> lP;
 
     C *src = buf0, *dst = buf1;
     int Ns = 1;
@@ -207,28 +239,12 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
         const int R = a.radix[s];
         const int m = M / R;
         const int tstep = M / (Ns * R);
-        for (int idx = tid; idx < m * P; idx += nt) {
-            const int j = idx >> lP, pp = idx & (P - 1);
-            const int k = j % Ns;
-            C v[5];
-#pragma unroll
-            for (int r = 0; r < 5; ++r)
-                if (r < R) v[r] = src[((long)(j + r * m) << lP) + pp];
-            if (k != 0) {
-#pragma unroll
-                for (int r = 1; r < 5; ++r)
-                    if (r < R) v[r] = A::cmul(v[r], tw[r * k * tstep], INV);
-            }
-            switch (R) {
-                case 2: Butterfly<A>::r2(v); break;
-                case 3: Butterfly<A>::r3(v, sg, s3); break;
-                case 4: Butterfly<A>::r4(v, sg); break;
-                default: Butterfly<A>::r5(v, sg, c1, c2, s1, s2); break;
-            }
-            const int dbase = (j / Ns) * Ns * R + k;
-#pragma unroll
-            for (int r = 0; r < 5; ++r)
-                if (r < R) dst[((long)(dbase + r * Ns) << lP) + pp] = v[r];
+        const unsigned mg = a.nsmagic[s];
+        switch (R) {
+            case 2: fft_stage<A, 2, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+            case 3: fft_stage<A, 3, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+            case 4: fft_stage<A, 4, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+            default: fft_stage<A, 5, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
         }
         __syncthreads();
         C *t = src;
@@ -240,7 +256,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
     pdl_trigger();                                         // the next pass may start launching
     const long obase = (long)c * a.out_cs + (long)o * a.out_os;
     for (int idx = tid; idx < a.nout * P; idx += nt) {
-        const int n = idx >> lP, pp = idx & (P - 1), pi = p0 + pp;
+        const int n = idx >> lP, pp2 = idx & (P - 1), pi = p0 + pp2;
         if (pi < a.pdim) store_vec<A, OUTF>(a.out, obase + (long)n * a.out_ns + pi, src[idx]);
     }
 }
@@ -295,7 +311,14 @@ int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool in
     const FftPlan &f = (a.M == p->fx.M) ? p->fx : p->fy;
     if (f.M != a.M) return set_error(p, BTTB_ERR_INVALID_ARG, "no FFT plan for this length");
     a.nst = f.nst;
-    for (int i = 0; i < f.nst; ++i) a.radix[i] = f.radix[i];
+    {
+        int ns = 1;
+        for (int i = 0; i < f.nst; ++i) {
+            a.radix[i] = f.radix[i];
+            a.nsmagic[i] = ns == 1 ? 0u : (unsigned)((0x100000000ull + ns - 1) / ns);   // ceil(2^32 / Ns)
+            ns *= f.radix[i];
+        }
+    }
     size_t elem = prec == PREC_F32 ? 8 : 16;
     a.P = choose_P(a.M, a.pdim, elem, p->fft_pmax);
     a.log2P = 0;

@@ -634,6 +634,7 @@ struct DcgsArgs {
     int m, k;
     int dot_sub, nblk_dot, ich, nblk_vec;
     int cmajor;           // 1: a CTA covers its chunks for every vector (u, x read once; many columns)
+    int dsm_last;         // float4 slots of dynamic shared memory used by the last CTA (stages follow)
     float4 *part;
     long pstride;
     float4 *sco, *cco, *hpre, *Horig, *hcol;   // [c][m+1] x 4, Horig [c][(m+1)*m]
@@ -660,50 +661,82 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
     const int npart = a.cmajor ? a.nblk_dot : cpv;         // partials per quantity for the last CTA
     if (a.cmajor) {
         // chunk-major: CTA = chunk group blockIdx.x, warp w takes chunk blockIdx.x*kDotIW + w for every
-        // vector i <= j, so the warp reads its entries of u and x once; one partial per warp and quantity
+        // vector i <= j.  The warp keeps its entries of u and x in registers and streams the basis chunks
+        // through two shared-memory stages (bulk copies on an mbarrier each): q_{i+1} lands while q_i is
+        // used.  One partial per warp and quantity.
+        float4 *stg = dsm + a.dsm_last + (long)warp * 2 * kDotNE;
+        uint64_t *bar = reinterpret_cast<uint64_t *>(dsm + a.dsm_last + kDotIW * 2 * kDotNE) + 2 * warp;
+        __shared__ int s_abort;
+        if (threadIdx.x == 0) s_abort = 0;
+        if (lane == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
         const int blk = blockIdx.x * kDotIW + warp;
         if (blk < a.nblk_dot) {
-            const float4 *uv = a.U + (long)c * a.n;
-            const float4 *xv = a.X + (long)c * a.n;
-            float4 u[kDotPL], x[kDotPL];
-            auto load_ux = [&](long n0, int len) {
-#pragma unroll
-                for (int r = 0; r < kDotPL; ++r) {
-                    const int e = lane + 32 * r;
-                    const bool in = e < len;
-                    u[r] = in ? uv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    x[r] = in && has_x ? xv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+            const long n0 = (long)blk * kDotNE;
+            const int len = (int)min((long)kDotNE, a.n - n0);
+            const float4 *uv = a.U + (long)c * a.n + n0;
+            const float4 *xv = a.X + (long)c * a.n + n0;
+            const float4 *qb = a.Vb + (long)c * a.bs_c + n0;
+            const uint64_t pol = l2_policy_evict_first();
+            auto issue = [&](int i) {
+                mbar_arrive_expect_tx(&bar[i & 1], (uint32_t)len * 16u);
+                bulk_g2s(stg + (i & 1) * kDotNE, qb + (long)i * a.bs_i, (uint32_t)len * 16u, &bar[i & 1], pol);
             };
-            if (a.dot_sub == 1) {
-                const long n0 = (long)blk * kDotNE;
-                load_ux(n0, (int)max(0L, min((long)kDotNE, a.n - n0)));
+            if (lane == 0 && j > 0) issue(0);
+            float4 u[kDotPL], x[kDotPL];
+#pragma unroll
+            for (int r = 0; r < kDotPL; ++r) {
+                const int e = lane + 32 * r;
+                const bool in = e < len;
+                u[r] = in ? uv[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                x[r] = in && has_x ? xv[e] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            bool failed = false;
+            int issued = j > 0 ? 0 : -1, waited = -1;     // lane 0's view of the copies
             for (int i = 0; i <= j; ++i) {
-                const float4 *qv = i < j ? a.Vb + (long)i * a.bs_i + (long)c * a.bs_c : uv;
-                dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
-                for (int sc = 0; sc < a.dot_sub; ++sc) {
-                    const long n0 = ((long)blk * a.dot_sub + sc) * kDotNE;
-                    const int len = (int)max(0L, min((long)kDotNE, a.n - n0));
-                    if (a.dot_sub > 1) load_ux(n0, len);
-                    float4 q[kDotPL];
+                float4 q[kDotPL];
+                if (i < j) {
+                    if (lane == 0 && !failed && i + 1 < j) {
+                        issue(i + 1);                     // its stage was released at the end of step i-1
+                        issued = i + 1;
+                    }
+                    if (!failed) {
+                        if (mbar_wait_bounded(&bar[i & 1], (uint32_t)(i >> 1) & 1u, &s_abort)) {
+                            waited = i;
+                        } else {
+                            failed = true;
+                            if (lane == 0) atomicOr(a.err, DEVERR_TIMEOUT);
+                        }
+                    }
+                    const float4 *sq = stg + (i & 1) * kDotNE;
 #pragma unroll
                     for (int r = 0; r < kDotPL; ++r) {
                         const int e = lane + 32 * r;
-                        q[r] = e < len ? qv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        q[r] = !failed && e < len ? sq[e] : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
+                } else {
 #pragma unroll
-                    for (int r = 0; r < kDotPL; ++r) {
-                        dacc_mac(sr, q[r].x, q[r].z, u[r].x, u[r].z);
-                        dacc_mac(sr, q[r].y, q[r].w, u[r].y, u[r].w);
-                        dacc_mac(si, q[r].x, q[r].z, u[r].y, u[r].w);
-                        dacc_mac(si, -q[r].y, -q[r].w, u[r].x, u[r].z);
-                        dacc_mac(tr, q[r].x, q[r].z, x[r].x, x[r].z);
-                        dacc_mac(tr, q[r].y, q[r].w, x[r].y, x[r].w);
-                        dacc_mac(ti, q[r].x, q[r].z, x[r].y, x[r].w);
-                        dacc_mac(ti, -q[r].y, -q[r].w, x[r].x, x[r].z);
-                    }
+                    for (int r = 0; r < kDotPL; ++r) q[r] = u[r];
                 }
+                dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
+#pragma unroll
+                for (int r = 0; r < kDotPL; ++r) {
+                    dacc_mac(sr, q[r].x, q[r].z, u[r].x, u[r].z);
+                    dacc_mac(sr, q[r].y, q[r].w, u[r].y, u[r].w);
+                    dacc_mac(si, q[r].x, q[r].z, u[r].y, u[r].w);
+                    dacc_mac(si, -q[r].y, -q[r].w, u[r].x, u[r].z);
+                    dacc_mac(tr, q[r].x, q[r].z, x[r].x, x[r].z);
+                    dacc_mac(tr, q[r].y, q[r].w, x[r].y, x[r].w);
+                    dacc_mac(ti, q[r].x, q[r].z, x[r].y, x[r].w);
+                    dacc_mac(ti, -q[r].y, -q[r].w, x[r].x, x[r].z);
+                }
+                // every lane has read stage i&1 before lane 0 refills it (next step)
+                __syncwarp();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 warp_reduce_dacc(sr);
                 warp_reduce_dacc(si);
                 warp_reduce_dacc(tr);
@@ -714,6 +747,8 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
                     part[(long)(a.m + 1 + i) * npart + blk] = make_float4(b0.hi, b1.hi, b0.lo, b1.lo);
                 }
             }
+            if (lane == 0)                                 // copies still in flight after a failed wait
+                for (int d = waited + 1; d <= issued; ++d) mbar_wait_drain(&bar[d & 1], (uint32_t)(d >> 1) & 1u);
         }
     } else {
         // vector-major: CTA (vector i, group cb of kDotIW chunks); warp w takes chunk cb*kDotIW + w.  The CTAs
@@ -1264,6 +1299,7 @@ static DcgsArgs dcgs_args(Plan *p, GmresWork *g, int j) {
         a.cmajor = a.dot_sub == 1 && cpv * g->k >= 2L * p->nsm;
         a.ich = (int)(a.cmajor ? cpv : cpv * (j + 1));
     }
+    a.dsm_last = 7 * g->m + 7 + kDotIW * 32 + g->m + 1;
     a.nblk_vec = g->nblk;
     a.part = g->part;
     a.pstride = norm_pstride(g->m, n);
@@ -1291,7 +1327,20 @@ static DcgsArgs dcgs_args(Plan *p, GmresWork *g, int j) {
 
 static int dcgs_dots_launch(Plan *p, GmresWork *g, int j, int has_x) {
     const DcgsArgs a = dcgs_args(p, g, j);
-    const size_t smem = (size_t)(7 * g->m + 7 + kDotIW * 32 + g->m + 1) * sizeof(float4);
+    // last-CTA scratch, then (chunk-major) two basis stages per warp and their mbarriers
+    const size_t smem = (size_t)a.dsm_last * sizeof(float4) +
+                        (a.cmajor ? (size_t)kDotIW * 2 * kDotNE * sizeof(float4) + kDotIW * 2 * sizeof(uint64_t) : 0);
+    if (smem > 48 * 1024) {
+        // the opt-in limit covers static and dynamic shared memory together
+        cudaFuncAttributes fa{};
+        cudaError_t ea = cudaFuncGetAttributes(&fa, dcgs_dots_kernel);
+        if (ea == cudaSuccess && smem + fa.sharedSizeBytes > p->smem_optin)
+            return set_error(p, BTTB_ERR_INVALID_ARG, "restart length too large for the reduction's shared memory");
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(dcgs_dots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(p->smem_optin - fa.sharedSizeBytes));
+        if (ea != cudaSuccess) return check_cuda(p, ea, "delayed CGS2 reduction shared memory");
+    }
     const int tok = prof_begin(p, 3);
     cudaError_t e = launch_pdl(dcgs_dots_kernel, dim3(a.ich, g->k), dim3(kDotIW * 32), smem, p->stream, a, j, has_x);
     prof_end(p, tok, 0.0);

@@ -45,6 +45,7 @@ struct FftPass {
     int nin, nout;                // nonzero input elements, kept output elements
     int M, nst;
     int radix[kMaxRadixStages];
+    unsigned nsmagic[kMaxRadixStages];   // ceil(2^32 / Ns) of each stage (Ns = product of the earlier radices)
     const void *tw;
     int P, log2P;                 // inner chunk per CTA (power of two)
 };

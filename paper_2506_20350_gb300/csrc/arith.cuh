@@ -1,6 +1,9 @@
 // Number systems the kernels are instantiated for.  Each provides the complex
 // operations a radix butterfly and a block product need, plus conversions from
-// and to the storage types a caller's vectors may have.
+// and to the storage types a caller's vectors may have.  Every rounding step is
+// an explicit intrinsic (no compiler contraction), so the same butterfly gives
+// the same bits in every kernel that runs it (the strided FFT passes and the
+// fused two-level FFT).
 //
 //   F64N : IEEE binary64 (double2), on the binary64 pipe
 //   DF64 : double-float complex (cdf = float4), on the binary32 pipes
@@ -21,16 +24,16 @@ struct F64N {
     using K = double;            // real constant
     static constexpr int kind = 2;
     __device__ static C zero() { return make_double2(0.0, 0.0); }
-    __device__ static C add(C a, C b) { return make_double2(a.x + b.x, a.y + b.y); }
-    __device__ static C sub(C a, C b) { return make_double2(a.x - b.x, a.y - b.y); }
+    __device__ static C add(C a, C b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+    __device__ static C sub(C a, C b) { return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)); }
     // a * (s i), s = +1 or -1
     __device__ static C mul_i(C a, int s) { return s > 0 ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x); }
-    __device__ static C mul_k(C a, K k) { return make_double2(a.x * k, a.y * k); }
-    __device__ static C half(C a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
+    __device__ static C mul_k(C a, K k) { return make_double2(__dmul_rn(a.x, k), __dmul_rn(a.y, k)); }
+    __device__ static C half(C a) { return make_double2(__dmul_rn(0.5, a.x), __dmul_rn(0.5, a.y)); }
     // a * w (conj(w) when cj)
     __device__ static C cmul(C a, C w, bool cj) {
         double wi = cj ? -w.y : w.y;
-        return make_double2(a.x * w.x - a.y * wi, a.x * wi + a.y * w.x);
+        return make_double2(__fma_rn(a.x, w.x, -__dmul_rn(a.y, wi)), __fma_rn(a.x, wi, __dmul_rn(a.y, w.x)));
     }
     __device__ static K kconst(double v) { return v; }
     __device__ static C from_c128(double2 v) { return v; }
@@ -81,14 +84,14 @@ struct F32 {
     using K = float;
     static constexpr int kind = 1;
     __device__ static C zero() { return make_float2(0.f, 0.f); }
-    __device__ static C add(C a, C b) { return make_float2(a.x + b.x, a.y + b.y); }
-    __device__ static C sub(C a, C b) { return make_float2(a.x - b.x, a.y - b.y); }
+    __device__ static C add(C a, C b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+    __device__ static C sub(C a, C b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
     __device__ static C mul_i(C a, int s) { return s > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
-    __device__ static C mul_k(C a, K k) { return make_float2(a.x * k, a.y * k); }
-    __device__ static C half(C a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
+    __device__ static C mul_k(C a, K k) { return make_float2(__fmul_rn(a.x, k), __fmul_rn(a.y, k)); }
+    __device__ static C half(C a) { return make_float2(__fmul_rn(0.5f, a.x), __fmul_rn(0.5f, a.y)); }
     __device__ static C cmul(C a, C w, bool cj) {
         float wi = cj ? -w.y : w.y;
-        return make_float2(a.x * w.x - a.y * wi, a.x * wi + a.y * w.x);
+        return make_float2(__fmaf_rn(a.x, w.x, -__fmul_rn(a.y, wi)), __fmaf_rn(a.x, wi, __fmul_rn(a.y, w.x)));
     }
     __device__ static K kconst(double v) { return (float)v; }
     __device__ static C from_c128(double2 v) { return make_float2((float)v.x, (float)v.y); }

@@ -9,9 +9,12 @@
 // and runs a Stockham autosort FFT with radix 2/3/4/5 butterflies; consecutive
 // threads work on consecutive batch indices, so every shared-memory access is
 // conflict-free and every global access is a coalesced run of P elements.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
+
+#include <cooperative_groups.h>
 
 #include "arith.cuh"
 #include "internal.h"
@@ -328,6 +331,302 @@ int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool in
         case PREC_F64N: a.tw = f.tw_f64; return dispatch_fmt<F64N>(p, a, infmt, outfmt, inverse);
         case PREC_F32: a.tw = f.tw_f32; return dispatch_fmt<F32>(p, a, infmt, outfmt, inverse);
         default: a.tw = f.tw_df; return dispatch_fmt<DF64>(p, a, infmt, outfmt, inverse);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Both levels of the forward (or inverse) 2-level FFT in one kernel, for
+// products of few vectors, where the two strided passes above are bound by
+// their launch and memory latency rather than by bandwidth.  A cluster of Q
+// CTAs takes one basis index p of one column.  For the forward transform CTA
+// r loads its share of the ny nonzero rows, transforms them along kx (the x
+// level, in shared memory [kx][row]), and sends every column kx to the CTA
+// that owns it in the cluster's distributed shared memory; after one cluster
+// barrier each CTA transforms its columns along iy (the y level, [kx][iy]
+// with the iy stride rounded up to odd: conflict-free) and writes its bins.
+// The inverse runs the same steps in reverse order.  The padding of Eq. (xc2)
+// is the zero fill of the unused slots; the crop of Sec. II-C keeps the first
+// nx, ny outputs.
+// ---------------------------------------------------------------------------
+struct Fft2Side {
+    int M, nst;
+    int radix[kMaxRadixStages];
+    unsigned nsmagic[kMaxRadixStages];
+};
+
+struct Fft2Args {
+    const void *in;
+    void *out;
+    long ld;                      // column stride of the cell-ordered vector (x for forward, y for inverse)
+    long ubs;                     // spectrum side: element (bin, c, p) at bin*ubs + c*b + p
+    const int *in_sel;            // forward only: input offset += (*in_sel) * in_sel_stride
+    long in_sel_stride;
+    const double *in_scale;       // forward only: per-column scale applied on load
+    const int *active;
+    int nx, ny, b, ms;            // ms: iy stride of a column share (my rounded up to odd)
+    int xs, ncmax;                // row stride of a row share (ceil(ny/Q) rounded up to odd); widest column share
+    Fft2Side sx, sy;
+    const void *twx, *twy;
+};
+
+// One Stockham stage of radix R over nb sequences of length m*R with element stride es: sequence t starts
+// at offset (t div g) * gs + (t mod g) (g = 1: t * gs).  The flat work index is split by multiply-high
+// divisions (exact below 2^16).
+template <class A, int R, bool INV>
+__device__ __forceinline__ void fft2_stage(const typename A::C *__restrict__ src, typename A::C *__restrict__ dst,
+                                           const typename A::C *tw, int m, int Ns, unsigned nsmagic, int tstep,
+                                           int es, int nb, unsigned nbmagic, int gs, typename A::K s3,
+                                           typename A::K c1, typename A::K c2, typename A::K s1, typename A::K s2) {
+    using C = typename A::C;
+    constexpr int sg = INV ? 1 : -1;
+    const int total = m * nb;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int j = nb == 1 ? idx : (int)__umulhi((unsigned)idx, nbmagic);
+        const int off = (idx - j * nb) * gs;
+        const int q = Ns == 1 ? j : (int)__umulhi((unsigned)j, nsmagic);
+        const int k = j - q * Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[(j + r * m) * es + off];
+        if (k != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = A::cmul(v[r], tw[r * k * tstep], INV);
+        }
+        if constexpr (R == 2) Butterfly<A>::r2(v);
+        else if constexpr (R == 3) Butterfly<A>::r3(v, sg, s3);
+        else if constexpr (R == 4) Butterfly<A>::r4(v, sg);
+        else Butterfly<A>::r5(v, sg, c1, c2, s1, s2);
+        const int dbase = q * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[(dbase + r * Ns) * es + off] = v[r];
+    }
+}
+
+// All stages of one level; returns the buffer that holds the result.
+template <class A, bool INV>
+__device__ typename A::C *fft2_level(typename A::C *src, typename A::C *dst, const typename A::C *tw,
+                                      const Fft2Side &sd, int es, int nb, int gs) {
+    using C = typename A::C;
+    using K = typename A::K;
+    const int M = sd.M;
+    const K s3 = real_const<A>(tw[M + 4]);
+    const K c1 = real_const<A>(tw[M + 0]), c2 = real_const<A>(tw[M + 1]);
+    const K s1 = real_const<A>(tw[M + 2]), s2 = real_const<A>(tw[M + 3]);
+    const unsigned nbm = nb > 1 ? (unsigned)((0x100000000ull + nb - 1) / nb) : 0u;
+    int Ns = 1;
+    for (int s = 0; s < sd.nst; ++s) {
+        const int R = sd.radix[s];
+        const int m = M / R, tstep = M / (Ns * R);
+        const unsigned mg = sd.nsmagic[s];
+        switch (R) {
+            case 2: fft2_stage<A, 2, INV>(src, dst, tw, m, Ns, mg, tstep, es, nb, nbm, gs, s3, c1, c2, s1, s2); break;
+            case 3: fft2_stage<A, 3, INV>(src, dst, tw, m, Ns, mg, tstep, es, nb, nbm, gs, s3, c1, c2, s1, s2); break;
+            case 4: fft2_stage<A, 4, INV>(src, dst, tw, m, Ns, mg, tstep, es, nb, nbm, gs, s3, c1, c2, s1, s2); break;
+            default: fft2_stage<A, 5, INV>(src, dst, tw, m, Ns, mg, tstep, es, nb, nbm, gs, s3, c1, c2, s1, s2); break;
+        }
+        __syncthreads();
+        C *t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
+constexpr int kFft2Threads = 128;
+
+// Forward: x (cell order, format INF) -> u^ (native).  Inverse: v^ (native) -> y (cell order, format OUTF).
+// Launched with clusters of Q CTAs along x: CTA (p*Q + r, c) is rank r of the cluster for basis p, column c.
+template <class A, int INF, int OUTF, bool INV>
+__global__ void __launch_bounds__(kFft2Threads) fft2_fused_kernel(const Fft2Args a) {
+    namespace cg = cooperative_groups;
+    using C = typename A::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int Q = (int)cl.num_blocks(), r = (int)cl.block_rank();
+    const int mx = a.sx.M, my = a.sy.M, ms = a.ms, xs = a.xs, nx = a.nx, ny = a.ny, b = a.b;
+    const int p = blockIdx.x / Q, c = blockIdx.y;
+    // row share [rlo, rhi) of the ny nonzero rows, column share [clo, chi) of the mx columns
+    const int rlo = r * ny / Q, nrow = (r + 1) * ny / Q - rlo;
+    const int clo = r * mx / Q, ncol = (r + 1) * mx / Q - clo;
+    C *twx = reinterpret_cast<C *>(smem_raw);
+    C *twy = twx + (mx + 8);
+    C *X0 = twy + (my + 8);                                // [kx][row of the share], stride xs
+    C *X1 = X0 + mx * xs;
+    C *Y0 = X1 + mx * xs;                                  // [column of the share][iy], stride ms
+    C *Y1 = Y0 + a.ncmax * ms;
+    for (int i = threadIdx.x; i < mx + 5; i += blockDim.x) twx[i] = reinterpret_cast<const C *>(a.twx)[i];
+    for (int i = threadIdx.x; i < my + 5; i += blockDim.x) twy[i] = reinterpret_cast<const C *>(a.twy)[i];
+    pdl_wait();
+    if (a.active && !a.active[c]) return;                  // uniform over the cluster (same column)
+    if (!INV) {
+        long ib = (long)c * a.ld + p;
+        if (a.in_sel) ib += (long)(*a.in_sel) * a.in_sel_stride;
+        const double scl = a.in_scale ? a.in_scale[c] : 1.0;
+        for (int idx = threadIdx.x; idx < mx * nrow; idx += blockDim.x) {
+            const int kx = idx / nrow, il = idx - kx * nrow;
+            C v = A::zero();
+            if (kx < nx) {
+                v = load_vec<A, INF>(a.in, ib + ((long)(rlo + il) * nx + kx) * b);
+                if (a.in_scale) v = scale_by<A>(v, scl);
+            }
+            X0[kx * xs + il] = v;
+        }
+        // the y level's padding rows of this CTA's columns (the exchange fills rows iy < ny)
+        for (int idx = threadIdx.x; idx < ncol * ms; idx += blockDim.x)
+            if (idx % ms >= ny) Y0[idx] = A::zero();
+        __syncthreads();
+        const C *R1 = fft2_level<A, false>(X0, X1, twx, a.sx, xs, nrow, 1);       // along kx, own rows
+        for (int idx = threadIdx.x; idx < mx * nrow; idx += blockDim.x) {
+            const int kx = idx / nrow, il = idx - kx * nrow;
+            const int q = ((kx + 1) * Q - 1) / mx;                                  // owner of column kx
+            C *dst = cl.map_shared_rank(Y0, q);
+            dst[(kx - q * mx / Q) * ms + rlo + il] = R1[kx * xs + il];
+        }
+        cl.sync();
+        const C *R2 = fft2_level<A, false>(Y0, Y1, twy, a.sy, 1, ncol, ms);       // along iy, own columns
+        pdl_trigger();
+        for (int idx = threadIdx.x; idx < ncol * ms; idx += blockDim.x) {
+            const int kl = idx / ms, ky = idx - kl * ms;
+            if (ky < my)
+                store_vec<A, native_fmt<A>>(a.out, ((long)ky * mx + clo + kl) * a.ubs + (long)c * b + p, R2[idx]);
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < ncol * ms; idx += blockDim.x) {
+            const int kl = idx / ms, ky = idx - kl * ms;
+            C v = A::zero();
+            if (ky < my) v = load_vec<A, native_fmt<A>>(a.in, ((long)ky * mx + clo + kl) * a.ubs + (long)c * b + p);
+            Y0[idx] = v;
+        }
+        __syncthreads();
+        const C *R1 = fft2_level<A, true>(Y0, Y1, twy, a.sy, 1, ncol, ms);        // along ky, own columns
+        for (int idx = threadIdx.x; idx < ncol * ny; idx += blockDim.x) {
+            const int kl = idx / ny, iy = idx - kl * ny;
+            const int q = ((iy + 1) * Q - 1) / ny;                                  // owner of row iy
+            C *dst = cl.map_shared_rank(X0, q);
+            dst[(clo + kl) * xs + iy - q * ny / Q] = R1[kl * ms + iy];
+        }
+        cl.sync();
+        const C *R2 = fft2_level<A, true>(X0, X1, twx, a.sx, xs, nrow, 1);        // along kx, own rows
+        pdl_trigger();
+        const long ob = (long)c * a.ld + p;
+        for (int idx = threadIdx.x; idx < nrow * nx; idx += blockDim.x) {
+            const int il = idx / nx, ix = idx - il * nx;
+            store_vec<A, OUTF>(a.out, ob + ((long)(rlo + il) * nx + ix) * b, R2[ix * xs + il]);
+        }
+    }
+}
+
+static void fft2_side(const FftPlan &f, Fft2Side &sd) {
+    sd.M = f.M;
+    sd.nst = f.nst;
+    int ns = 1;
+    for (int i = 0; i < f.nst; ++i) {
+        sd.radix[i] = f.radix[i];
+        sd.nsmagic[i] = ns == 1 ? 0u : (unsigned)((0x100000000ull + ns - 1) / ns);
+        ns *= f.radix[i];
+    }
+}
+
+// CTAs per cluster of the fused FFT: up to 8 (the portable cluster size), no more than the grid lengths.
+static int fft2_cluster(const Plan *p) { return std::max(1, std::min(8, std::min(p->mx, p->ny))); }
+
+static void fft2_shape(const Plan *p, int &Q, int &ms, int &xs, int &ncmax) {
+    Q = fft2_cluster(p);
+    ms = p->my | 1;
+    xs = ((p->ny + Q - 1) / Q) | 1;
+    ncmax = (p->mx + Q - 1) / Q;
+}
+
+size_t fft2_fused_smem(const Plan *p, int prec) {
+    const size_t elem = prec == PREC_F32 ? 8 : 16;
+    int Q, ms, xs, ncmax;
+    fft2_shape(p, Q, ms, xs, ncmax);
+    return ((size_t)p->mx + 8 + p->my + 8 + 2 * (size_t)p->mx * xs + 2 * (size_t)ncmax * ms) * elem;
+}
+
+template <class A, int INF, int OUTF, bool INV>
+static int launch_fused(Plan *p, const Fft2Args &a, int ncols, size_t smem) {
+    auto kern = fft2_fused_kernel<A, INF, OUTF, INV>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
+        if (e != cudaSuccess) return check_cuda(p, e, "fused fft smem attribute");
+    }
+    const int Q = fft2_cluster(p);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.b * Q, ncols);
+    cfg.blockDim = dim3(kFft2Threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = p->stream;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = Q;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    const int tok = prof_begin(p, BTTB_K_FFT);
+    cudaError_t le = cudaLaunchKernelEx(&cfg, kern, a);
+    count_launch(p);
+    if (le != cudaSuccess) return check_cuda(p, le, "fused fft launch");
+    const double esz_in = INF == FMT_C64 ? 8.0 : 16.0, esz_out = OUTF == FMT_C64 ? 8.0 : 16.0;
+    prof_end(p, tok, (double)ncols * a.b * ((double)a.nx * a.ny * esz_in + (double)a.sx.M * a.sy.M * esz_out));
+    return check_cuda(p, cudaGetLastError(), "fused fft launch");
+}
+
+template <class A>
+static int fused_dispatch(Plan *p, const Fft2Args &a, int ncols, int cellfmt, bool inv, size_t smem) {
+    constexpr int NF = native_fmt<A>;
+    if (!inv) {
+        switch (cellfmt) {
+            case FMT_C128: return launch_fused<A, FMT_C128, NF, false>(p, a, ncols, smem);
+            case FMT_C64: return launch_fused<A, FMT_C64, NF, false>(p, a, ncols, smem);
+            default: return launch_fused<A, FMT_CDF, NF, false>(p, a, ncols, smem);
+        }
+    }
+    switch (cellfmt) {
+        case FMT_C128: return launch_fused<A, NF, FMT_C128, true>(p, a, ncols, smem);
+        case FMT_C64: return launch_fused<A, NF, FMT_C64, true>(p, a, ncols, smem);
+        default: return launch_fused<A, NF, FMT_CDF, true>(p, a, ncols, smem);
+    }
+}
+
+int fft2_fused_launch(Plan *p, const void *in, void *out, long ld, int ncols, int prec, int cellfmt, bool inverse,
+                      const int *in_sel, long in_sel_stride, const double *in_scale, const int *active) {
+    Fft2Args a{};
+    a.in = in;
+    a.out = out;
+    a.ld = ld;
+    a.ubs = p->ubs;
+    a.in_sel = in_sel;
+    a.in_sel_stride = in_sel_stride;
+    a.in_scale = in_scale;
+    a.active = active;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.b = p->b;
+    int Q;
+    fft2_shape(p, Q, a.ms, a.xs, a.ncmax);
+    // with my == mx the plan keeps one set of tables (fx) and marks fy unused
+    const FftPlan &fx = p->fx, &fy = p->fy.M == p->my ? p->fy : p->fx;
+    if (fx.M != p->mx || fy.M != p->my)
+        return set_error(p, BTTB_ERR_INVALID_ARG, "no FFT plan for the grid lengths");
+    fft2_side(fx, a.sx);
+    fft2_side(fy, a.sy);
+    if (ncols <= 0) return BTTB_OK;
+    const size_t smem = fft2_fused_smem(p, prec);
+    switch (prec) {
+        case PREC_F64N: a.twx = fx.tw_f64; a.twy = fy.tw_f64; break;
+        case PREC_F32: a.twx = fx.tw_f32; a.twy = fy.tw_f32; break;
+        default: a.twx = fx.tw_df; a.twy = fy.tw_df; break;
+    }
+    if (!a.twx || !a.twy) return set_error(p, BTTB_ERR_INVALID_ARG, "FFT twiddle tables missing");
+    switch (prec) {
+        case PREC_F64N: return fused_dispatch<F64N>(p, a, ncols, cellfmt, inverse, smem);
+        case PREC_F32: return fused_dispatch<F32>(p, a, ncols, cellfmt, inverse, smem);
+        default: return fused_dispatch<DF64>(p, a, ncols, cellfmt, inverse, smem);
     }
 }
 

@@ -142,6 +142,13 @@ int check_cuda(Plan *p, cudaError_t e, const char *what);
 int fft_plan_init(Plan *p, FftPlan &f, int M);
 void fft_plan_free(FftPlan &f);
 int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool inverse);
+// Both FFT levels of a product in one kernel (few columns): forward cell-ordered x (cellfmt) -> u^, or
+// inverse v^ -> cell-ordered y (cellfmt); ld is the cell-ordered vector's column stride.
+int fft2_fused_launch(Plan *p, const void *in, void *out, long ld, int ncols, int prec, int cellfmt, bool inverse,
+                      const int *in_sel, long in_sel_stride, const double *in_scale, const int *active);
+size_t fft2_fused_smem(const Plan *p, int prec);
+// Products of at most this many columns run the fused FFT when its grid fits shared memory.
+constexpr int kFusedFftMaxCols = 4;
 int spectrum_compute(Plan *p, const void *gen, bttb_dtype dtype, int gen_is_host);
 int smallest_5smooth(int n);
 

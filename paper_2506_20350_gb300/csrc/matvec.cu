@@ -35,6 +35,19 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     const long plane = (long)ny * mx * b;
     int rc;
 
+    // few columns: both FFT levels in one kernel each way (no U / V round trip, two launches fewer).  Timed
+    // on GB300 it wins for the double-float and binary64 products and for plans that run beside other
+    // arrays' kernels in a batch; a lone binary32 product keeps the four passes, which overlap better with
+    // their neighbours under programmatic dependent launch.
+    if (nrhs <= kFusedFftMaxCols && (fprec != PREC_F32 || p->in_batch) &&
+        fft2_fused_smem(p, fprec) <= p->smem_optin / 2) {
+        if ((rc = fft2_fused_launch(p, x, p->wsA, ldx, nrhs, fprec, xfmt, false, in_sel, in_sel_stride, in_scale,
+                                    active)) != BTTB_OK)
+            return rc;
+        if ((rc = contract_launch(p, prec, p->wsA, p->wsB, nrhs, active)) != BTTB_OK) return rc;
+        return fft2_fused_launch(p, p->wsB, y, ldy, nrhs, fprec, yfmt, true, nullptr, 0, nullptr, active);
+    }
+
     FftPass a{};
     a.in = x; a.out = p->wsB;
     a.in_cs = ldx; a.in_os = (long)nx * b; a.in_ns = b;

@@ -120,6 +120,24 @@ def test_tensor_core_product(bt, nx, ny, b, k):
     _check(y, ref, FP32_TOL, "tensor-core product")
 
 
+@pytest.mark.parametrize("ny", [1, 2, 3, 5, 8, 13, 20, 31, 40])
+def test_product_fft_lengths_along_y(bt, ny):
+    """The y level of both FFT forms: a product of 2 columns (both levels fused in one kernel each way) and
+    of 6 columns (strided passes) on the same vectors, each against the oracle."""
+    nx, b = 7, 5
+    gen = arrays.random_generator_blocks(nx, ny, b, seed=600 + ny)
+    plan = bt.Plan(nx, ny, b, max_rhs=6, prec_mask=ALL_PRECS)
+    plan.set_generators(gen)
+    x = _rand(np.random.default_rng(ny), 6, plan.n)
+    ref = oracle.matvec(gen, x.T).T
+    for k in (2, 6):
+        for prec, tol in ((bt.BTTB_MV_FP64, FP64_TOL), (bt.BTTB_MV_FP64_NATIVE, FP64_TOL)):
+            _check(plan.matvec(_dev(x[:k]), prec=prec).cpu().numpy(), ref[:k], tol, f"prec {prec} k={k} my={plan.my}")
+        _check(plan.matvec(_dev(x[:k].astype(np.complex64)), prec=bt.BTTB_MV_FP32).cpu().numpy(), ref[:k], FP32_TOL,
+               f"binary32 k={k} my={plan.my}")
+    plan.close()
+
+
 @pytest.mark.parametrize("nx", list(range(1, 41)))
 def test_product_every_fft_length(bt, nx):
     """nx = 1..40 makes the plan pick every padded length smallest_5smooth(2 nx - 1) up to 80 (1, 3, 5, 8,

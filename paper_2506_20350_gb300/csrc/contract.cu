@@ -453,13 +453,100 @@ __global__ void __launch_bounds__(256) contract_multi_kernel(const float2 *g0, l
     pdl_trigger();
 }
 
+// Same product for b <= 64 with a 4 x 4 register tile: thread (row group rg, column group cg) of the 256
+// accumulates rows 2rg, 2rg+1, 32+2rg, 33+2rg of columns cg, cg+16, cg+32, cg+48 of the tile.  Per basis q it
+// loads its two row pairs of the spectrum block (16-byte loads, consecutive across the warp's lanes, when b
+// is even) and four vector entries (the two column groups of a warp are adjacent columns, on different
+// banks): 6 shared loads per 64 FMAs.
+__global__ void __launch_bounds__(256) contract_multi44_kernel(const float2 *g0, long gbs, const float2 *u,
+                                                                float2 *v, long ubs, int b, int k, int *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8);
+    float2 *gs = reinterpret_cast<float2 *>(smem + 128);
+    const uint32_t gbytes = round_up128((uint32_t)(b * b) * 8u);
+    float2 *us = reinterpret_cast<float2 *>(smem + 128 + gbytes);
+    const int bin = blockIdx.y, c0 = blockIdx.x * kMultiTile;
+    const int nc = min(kMultiTile, k - c0);
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t gb = round_up16((uint32_t)(b * b) * 8u);
+        const uint32_t ub = round_up16((uint32_t)(nc * b) * 8u);
+        mbar_arrive_expect_tx(bar, gb + ub);
+        bulk_g2s(gs, g0 + (long)bin * gbs, gb, bar, l2_policy_evict_last());
+        bulk_g2s(us, u + (long)bin * ubs + (long)c0 * b, ub, bar, l2_policy_evict_first());
+    }
+    const bool ok = mbar_wait_bounded(bar, 0, abort_flag);
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, DEVERR_TIMEOUT);
+            mbar_wait_drain(bar, 0);
+        }
+        return;
+    }
+    const int rg = threadIdx.x & 15, cg = threadIdx.x >> 4;
+    const int pa = 2 * rg, pb = 32 + 2 * rg;                  // the thread's row pairs
+    if (pa < b && cg < nc) {
+        int prow[4] = {pa, pa + 1, pb, pb + 1};
+        float2 acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[r][j] = make_float2(0.f, 0.f);
+        const bool even = b % 2 == 0, hasb = pb < b;
+        for (int q = 0; q < b; ++q) {
+            float2 g[4];
+            if (even) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(gs + q * b + pa);
+                const float4 a1 = hasb ? *reinterpret_cast<const float4 *>(gs + q * b + pb)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                g[0] = make_float2(a0.x, a0.y);
+                g[1] = make_float2(a0.z, a0.w);
+                g[2] = make_float2(a1.x, a1.y);
+                g[3] = make_float2(a1.z, a1.w);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) g[r] = prow[r] < b ? gs[q * b + prow[r]] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 x = us[(cg + 16 * j) * b + q];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    acc[r][j].x = fmaf(g[r].x, x.x, acc[r][j].x);
+                    acc[r][j].x = fmaf(-g[r].y, x.y, acc[r][j].x);
+                    acc[r][j].y = fmaf(g[r].x, x.y, acc[r][j].y);
+                    acc[r][j].y = fmaf(g[r].y, x.x, acc[r][j].y);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cc = cg + 16 * j;
+            if (cc < nc)
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (prow[r] < b) v[(long)bin * ubs + (long)(c0 + cc) * b + prow[r]] = acc[r][j];
+        }
+    }
+    pdl_trigger();
+}
+
 static int launch_contract_multi(Plan *p, const void *u, void *v, int k) {
     const int b = p->b;
     if (!p->ghat_hi) return set_error(p, BTTB_ERR_INVALID_ARG, "plan does not keep the binary32 spectrum");
     const int rw = (b + 31) / 32, cg = 8 / rw;     // b <= 128: rw in 1..4, cg in {8, 4, 2}
     const int cpg = kMultiTile / cg;                 // exactly covers the tile: 8, 16 or 32 columns
     const size_t smem = 128 + round_up128((uint32_t)(b * b) * 8u) + round_up128((uint32_t)(kMultiTile * b) * 8u);
-    auto kern = cpg == 8 ? contract_multi_kernel<8> : (cpg == 16 ? contract_multi_kernel<16> : contract_multi_kernel<32>);
+    auto kern = b <= 64 ? contract_multi44_kernel
+                        : (cpg == 8 ? contract_multi_kernel<8>
+                                    : (cpg == 16 ? contract_multi_kernel<16> : contract_multi_kernel<32>));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
     if (e != cudaSuccess) return check_cuda(p, e, "multi-RHS smem attribute");
     const dim3 grid((k + kMultiTile - 1) / kMultiTile, (unsigned)p->bins);

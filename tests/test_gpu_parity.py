@@ -93,6 +93,9 @@ def test_product_random_generators(bt, nx, ny, b, k):
     (4, 4, 12, 65),    # two tiles, the second with one column
     (3, 3, 33, 130),   # three row warps' layout (rw = 2), three tiles
     (3, 2, 96, 70),    # widest multi-RHS layout (rw = 3)
+    (5, 4, 60, 70),    # 4 x 4 register tiles (b <= 64), even b: 16-byte row-pair loads
+    (3, 3, 64, 129),   # largest b of the 4 x 4 tiles, a one-column third tile
+    (4, 3, 45, 17),    # odd b between 32 and 64: row-by-row loads, second row pairs partly valid
 ])
 def test_multi_rhs_product_binary32(bt, nx, ny, b, k):
     """k > 8 right-hand sides take the tiled per-bin GEMM (binary32)."""

@@ -198,82 +198,146 @@ __device__ __forceinline__ void fft_stage(const typename A::C *__restrict__ src,
     }
 }
 
+// Whether an input format is the number system's own element or its leading part, so that the load is a
+// plain copy (8 bytes for binary32, 16 for the others): then it can be an asynchronous copy.
+template <class A, int INF>
+constexpr bool async_copyable() {
+    return (A::kind == 1 && (INF == FMT_C64 || INF == FMT_CDF)) || (A::kind == 0 && INF == FMT_CDF) ||
+           (A::kind == 2 && INF == FMT_C128);
+}
+
 template <class A, int INF, int OUTF, bool INV>
 __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) {
     using C = typename A::C;
     using K = typename A::K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *buf0 = tw + (a.M + 8);
-    C *buf1 = buf0 + a.M * a.P;
+    C *const buf0 = tw + (a.M + 8);                        // buffers buf0 + k*M*P, k < 2 (3 with a.cpb > 1)
+    auto buf = [&](int k) { return buf0 + k * (a.M * a.P); };
 
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int o = blockIdx.x, c = blockIdx.z;
+    const int o = blockIdx.x;
     const int p0 = blockIdx.y * a.P;
     const int P = a.P, lP = a.log2P, M = a.M;
     // the twiddles are constant: stage them before waiting for the preceding kernel
     const C *twg = reinterpret_cast<const C *>(a.tw);
     for (int i = tid; i < M + 5; i += nt) tw[i] = twg[i];
     pdl_wait();
-    if (a.active && !a.active[c]) return;                  // finished column (uniform per CTA)
 
-    long ibase = (long)c * a.in_cs + (long)o * a.in_os;
-    if (a.in_sel) ibase += (long)(*a.in_sel) * a.in_sel_stride;
-    const double scl = a.in_scale ? a.in_scale[c] : 1.0;
-    for (int idx = tid; idx < M * P; idx += nt) {
-        const int n = idx >> lP, pp = idx & (P - 1), pi = p0 + pp;
-        C v = A::zero();
-        if (n < a.nin && pi < a.pdim) {
-            v = load_vec<A, INF>(a.in, ibase + (long)n * a.in_ns + pi);
-            if (a.in_scale) v = scale_by<A>(v, scl);
-        }
-        buf0[idx] = v;
-    }
-    __syncthreads();
-
-    const K s3 = real_const<A>(tw[M + 4]);
-    const K c1 = real_const<A>(tw[M + 0]), c2 = real_const<A>(tw[M + 1]);
-    const K s1 = real_const<A>(tw[M + 2]), s2 = real_const<A>(tw[M + 3]);
     const int pp = tid & (P - 1), j0 = tid >> lP, jstep = nt >> lP;
+    const long sel = a.in_sel ? (long)(*a.in_sel) * a.in_sel_stride : 0;
 
-    C *src = buf0, *dst = buf1;
-    int Ns = 1;
-    for (int s = 0; s < a.nst; ++s) {
-        const int R = a.radix[s];
-        const int m = M / R;
-        const int tstep = M / (Ns * R);
-        const unsigned mg = a.nsmagic[s];
-        switch (R) {
-            case 2: fft_stage<A, 2, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
-            case 3: fft_stage<A, 3, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
-            case 4: fft_stage<A, 4, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
-            default: fft_stage<A, 5, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+    // column c's M x P input: zero-padded beyond nin rows and pdim bases
+    auto load_direct = [&](int c, C *dst) {
+        const long ibase = (long)c * a.in_cs + (long)o * a.in_os + sel;
+        const double scl = a.in_scale ? a.in_scale[c] : 1.0;
+        for (int idx = tid; idx < M * P; idx += nt) {
+            const int n = idx >> lP, q = idx & (P - 1), pi = p0 + q;
+            C v = A::zero();
+            if (n < a.nin && pi < a.pdim) {
+                v = load_vec<A, INF>(a.in, ibase + (long)n * a.in_ns + pi);
+                if (a.in_scale) v = scale_by<A>(v, scl);
+            }
+            dst[idx] = v;
         }
-        __syncthreads();
-        C *t = src;
-        src = dst;
-        dst = t;
-        Ns *= R;
-    }
+    };
+    auto load_async = [&](int c, C *dst) {
+        if constexpr (async_copyable<A, INF>()) {
+            const long ibase = (long)c * a.in_cs + (long)o * a.in_os + sel;
+            for (int idx = tid; idx < M * P; idx += nt) {
+                const int n = idx >> lP, q = idx & (P - 1), pi = p0 + q;
+                if (n < a.nin && pi < a.pdim) {
+                    const long e = ibase + (long)n * a.in_ns + pi;
+                    if constexpr (sizeof(C) == 8) {
+                        // binary32: the element itself, or the leading (high) part of a double-float element
+                        const char *src = reinterpret_cast<const char *>(a.in) + e * (INF == FMT_CDF ? 16 : 8);
+                        cp_async8(dst + idx, src);
+                    } else {
+                        cp_async16(dst + idx, reinterpret_cast<const char *>(a.in) + e * 16);
+                    }
+                } else {
+                    dst[idx] = A::zero();
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    // (called after a barrier that follows the twiddle staging)
+    auto stages = [&](C *src, C *dst) -> C * {
+        const K s3 = real_const<A>(tw[M + 4]);
+        const K c1 = real_const<A>(tw[M + 0]), c2 = real_const<A>(tw[M + 1]);
+        const K s1 = real_const<A>(tw[M + 2]), s2 = real_const<A>(tw[M + 3]);
+        int Ns = 1;
+        for (int s = 0; s < a.nst; ++s) {
+            const int R = a.radix[s];
+            const int m = M / R;
+            const int tstep = M / (Ns * R);
+            const unsigned mg = a.nsmagic[s];
+            switch (R) {
+                case 2: fft_stage<A, 2, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+                case 3: fft_stage<A, 3, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+                case 4: fft_stage<A, 4, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+                default: fft_stage<A, 5, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+            }
+            __syncthreads();
+            C *t = src;
+            src = dst;
+            dst = t;
+            Ns *= R;
+        }
+        return src;
+    };
+    auto store = [&](int c, const C *res) {
+        const long obase = (long)c * a.out_cs + (long)o * a.out_os;
+        for (int idx = tid; idx < a.nout * P; idx += nt) {
+            const int n = idx >> lP, q = idx & (P - 1), pi = p0 + q;
+            if (pi < a.pdim) store_vec<A, OUTF>(a.out, obase + (long)n * a.out_ns + pi, res[idx]);
+        }
+    };
 
-    pdl_trigger();                                         // the next pass may start launching
-    const long obase = (long)c * a.out_cs + (long)o * a.out_os;
-    for (int idx = tid; idx < a.nout * P; idx += nt) {
-        const int n = idx >> lP, pp2 = idx & (P - 1), pi = p0 + pp2;
-        if (pi < a.pdim) store_vec<A, OUTF>(a.out, obase + (long)n * a.out_ns + pi, src[idx]);
+    const int cfirst = blockIdx.z * a.cpb, cend = min(cfirst + a.cpb, a.ncols);
+    if (a.cpb == 1 || !async_copyable<A, INF>() || a.in_scale) {
+        for (int c = cfirst; c < cend; ++c) {
+            if (a.active && !a.active[c]) continue;         // finished column (uniform per CTA)
+            load_direct(c, buf(0));
+            __syncthreads();
+            const C *res = stages(buf(0), buf(1));
+            if (c == cend - 1) pdl_trigger();               // the next pass may start launching
+            store(c, res);
+            __syncthreads();                                // the buffers are reused by the next column
+        }
+        if (cfirst >= cend) pdl_trigger();
+        return;
     }
+    // several columns: input of column c+1 streams into the third buffer while column c is transformed
+    int i = 0;                                              // column c: input buf(i), temporary buf(i+1)
+    load_async(cfirst, buf(0));
+    for (int c = cfirst; c < cend; ++c) {
+        cp_async_wait<0>();
+        __syncthreads();                                    // column c's input landed; column c-1 is stored
+        C *in = buf(i), *tmp = buf(i == 2 ? 0 : i + 1), *nxt = buf(i == 0 ? 2 : i - 1);
+        if (c + 1 < cend) load_async(c + 1, nxt);
+        if (!a.active || a.active[c]) {                     // finished column (uniform per CTA)
+            const C *res = stages(in, tmp);
+            if (c == cend - 1) pdl_trigger();
+            store(c, res);
+        }
+        i = i == 0 ? 2 : i - 1;
+    }
+    cp_async_wait<0>();
+    pdl_trigger();
 }
 
 template <class A, int INF, int OUTF, bool INV>
 static int launch_one(Plan *p, const FftPass &a) {
     using C = typename A::C;
-    size_t smem = ((size_t)a.M + 8 + 2 * (size_t)a.M * a.P) * sizeof(C);
+    size_t smem = ((size_t)a.M + 8 + (a.cpb > 1 ? 3 : 2) * (size_t)a.M * a.P) * sizeof(C);
     auto kern = fft_pass_kernel<A, INF, OUTF, INV>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
         if (e != cudaSuccess) return check_cuda(p, e, "fft smem attribute");
     }
-    dim3 grid(a.O, (a.pdim + a.P - 1) / a.P, a.ncols);
+    dim3 grid(a.O, (a.pdim + a.P - 1) / a.P, (a.ncols + a.cpb - 1) / a.cpb);
     const int tok = prof_begin(p, BTTB_K_FFT);
     cudaError_t le = launch_pdl(kern, grid, dim3(kFftThreads), smem, p->stream, a);
     count_launch(p);
@@ -303,12 +367,17 @@ static int dispatch_fmt(Plan *p, const FftPass &a, int infmt, int outfmt, bool i
     }
 }
 
-static int choose_P(int M, int pdim, size_t elem, int pmax) {
+static int choose_P(int M, int pdim, size_t elem, int pmax, int nbuf) {
     int P = 1;
     while (P < pmax && P < pdim) P <<= 1;
-    while (P > 1 && ((size_t)M + 8 + 2 * (size_t)M * P) * elem > 96 * 1024) P >>= 1;
+    while (P > 1 && ((size_t)M + 8 + nbuf * (size_t)M * P) * elem > 96 * 1024) P >>= 1;
     return P;
 }
+
+// Columns per CTA of a pass: one for few columns; with many, four, so that each CTA prefetches the next
+// column's input while it transforms one (the grid still fills every SM many times over).
+constexpr int kFftMultiCols = 4;
+constexpr int kFftMultiMinCols = 32;
 
 int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool inverse) {
     const FftPlan &f = (a.M == p->fx.M) ? p->fx : p->fy;
@@ -323,7 +392,8 @@ int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool in
         }
     }
     size_t elem = prec == PREC_F32 ? 8 : 16;
-    a.P = choose_P(a.M, a.pdim, elem, p->fft_pmax);
+    a.cpb = a.ncols >= kFftMultiMinCols ? kFftMultiCols : 1;
+    a.P = choose_P(a.M, a.pdim, elem, p->fft_pmax, a.cpb > 1 ? 3 : 2);
     a.log2P = 0;
     while ((1 << a.log2P) < a.P) ++a.log2P;
     if (a.O <= 0 || a.ncols <= 0 || a.pdim <= 0) return BTTB_OK;

@@ -48,6 +48,7 @@ struct FftPass {
     unsigned nsmagic[kMaxRadixStages];   // ceil(2^32 / Ns) of each stage (Ns = product of the earlier radices)
     const void *tw;
     int P, log2P;                 // inner chunk per CTA (power of two)
+    int cpb;                      // columns per CTA (> 1: the next column's input is prefetched while one runs)
 };
 
 enum Prec { PREC_DF64 = BTTB_MV_FP64, PREC_F32 = BTTB_MV_FP32, PREC_F64N = BTTB_MV_FP64_NATIVE,

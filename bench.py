@@ -61,6 +61,10 @@ def parse_args():
     ap.add_argument("--learned-probe", action="store_true",
                     help="profiling target: three applications of the learned correction to 16 columns and two "
                          "training steps on 64 columns (40x40, b=96), then exit; prints no bench line")
+    ap.add_argument("--multi-probe", action="store_true",
+                    help="profiling target: four GMRES(10)-IR steps on 64 port excitations of the 30x30, b=60 "
+                         "array (the many-column kernels at a workspace of about 1 GB), then exit; prints no "
+                         "bench line")
     return ap.parse_args()
 
 
@@ -681,10 +685,35 @@ def learned_probe():
     plan.close()
 
 
+def multi_probe():
+    """A short, fixed launch sequence of the many-column kernels for kernel profilers: 64 columns take the
+    per-bin GEMM, the chunk-major delayed-CGS2 reduction and the multi-column FFT passes."""
+    import torch
+
+    import paper_2506_20350_gb300 as bt
+    from workloads import arrays
+
+    if not torch.cuda.is_available():
+        raise SystemExit("the multi-column probe needs a CUDA GPU")
+    c = arrays.CONFIGS["precision"]
+    nx, ny, b = c["nx"], c["ny"], c["b"]
+    k = 64
+    plan = bt.Plan(nx, ny, b, max_rhs=k, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_FP32))
+    plan.set_generators(arrays.generator_blocks_torch(nx, ny, b, c["seed"]))
+    cells = [(i % nx, i // nx) for i in range(k)]
+    v = torch.from_numpy(arrays.port_excitations(nx, ny, b, cells).T.copy()).cuda()
+    plan.solve(v, tol=1e-8, restart=10, inner=bt.BTTB_MV_FP32, max_iters=4)
+    torch.cuda.synchronize()
+    plan.close()
+
+
 def main():
     args = parse_args()
     if args.learned_probe:
         learned_probe()
+        return
+    if args.multi_probe:
+        multi_probe()
         return
     if args.impl == "reference":
         run_reference(args)

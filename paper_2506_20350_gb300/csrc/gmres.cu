@@ -650,6 +650,25 @@ struct DcgsArgs {
     int *err;
 };
 
+// Sums four per-lane accumulators over the warp by a reduce-scatter butterfly: at offset 16 each half keeps
+// two of them, at offset 8 each quarter keeps one, offsets 4, 2, 1 finish it.  Lanes 0-7 return the sum of
+// a, 8-15 of b, 16-23 of c, 24-31 of d (12 shuffles of pairs and 6 merges instead of 40 and 20).
+__device__ __forceinline__ dacc warp_reduce_scatter4(dacc a, dacc b, dacc c, dacc d, int lane) {
+    const bool hi16 = lane & 16;
+    dacc k0 = hi16 ? c : a, k1 = hi16 ? d : b;
+    const dacc s0 = hi16 ? a : c, s1 = hi16 ? b : d;
+    dacc_add(k0, dacc{__shfl_xor_sync(0xffffffffu, s0.S, 16), __shfl_xor_sync(0xffffffffu, s0.s, 16)});
+    dacc_add(k1, dacc{__shfl_xor_sync(0xffffffffu, s1.S, 16), __shfl_xor_sync(0xffffffffu, s1.s, 16)});
+    const bool hi8 = lane & 8;
+    dacc k = hi8 ? k1 : k0;
+    const dacc sd = hi8 ? k0 : k1;
+    dacc_add(k, dacc{__shfl_xor_sync(0xffffffffu, sd.S, 8), __shfl_xor_sync(0xffffffffu, sd.s, 8)});
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1)
+        dacc_add(k, dacc{__shfl_xor_sync(0xffffffffu, k.S, off), __shfl_xor_sync(0xffffffffu, k.s, off)});
+    return k;
+}
+
 __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a, int j, int has_x) {
     extern __shared__ __align__(16) float4 dsm[];      // s, t: 2(m+1); Givens scratch 4m+4; Hs: m+1; partials
     const int c = blockIdx.y;
@@ -737,14 +756,12 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
                 // every lane has read stage i&1 before lane 0 refills it (next step)
                 __syncwarp();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                warp_reduce_dacc(sr);
-                warp_reduce_dacc(si);
-                warp_reduce_dacc(tr);
-                warp_reduce_dacc(ti);
-                if (lane == 0) {
-                    const df a0 = dacc_result(sr), a1 = dacc_result(si), b0 = dacc_result(tr), b1 = dacc_result(ti);
-                    part[(long)i * npart + blk] = make_float4(a0.hi, a1.hi, a0.lo, a1.lo);
-                    part[(long)(a.m + 1 + i) * npart + blk] = make_float4(b0.hi, b1.hi, b0.lo, b1.lo);
+                // reduce-scatter of the four sums: lanes 0-7 end with Re s, 8-15 Im s, 16-23 Re t, 24-31 Im t
+                const dacc tot = warp_reduce_scatter4(sr, si, tr, ti, lane);
+                const dacc oth{__shfl_down_sync(0xffffffffu, tot.S, 8), __shfl_down_sync(0xffffffffu, tot.s, 8)};
+                if ((lane & 15) == 0) {
+                    const df re = dacc_result(tot), im = dacc_result(oth);
+                    part[(long)(lane == 0 ? i : a.m + 1 + i) * npart + blk] = make_float4(re.hi, im.hi, re.lo, im.lo);
                 }
             }
             if (lane == 0)                                 // copies still in flight after a failed wait

@@ -669,7 +669,10 @@ __device__ __forceinline__ dacc warp_reduce_scatter4(dacc a, dacc b, dacc c, dac
     return k;
 }
 
-__global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a, int j, int has_x) {
+// CM: the chunk-major layout (a.cmajor), a separate instance so that the vector-major one keeps its
+// smaller register count (three CTAs per SM; the chunk-major one holds u and x in registers: two).
+template <bool CM>
+__global__ void __launch_bounds__(kDotIW * 32, CM ? 2 : 3) dcgs_dots_kernel(const DcgsArgs a, int j, int has_x) {
     extern __shared__ __align__(16) float4 dsm[];      // s, t: 2(m+1); Givens scratch 4m+4; Hs: m+1; partials
     const int c = blockIdx.y;
     pdl_wait();
@@ -677,8 +680,8 @@ __global__ void __launch_bounds__(kDotIW * 32) dcgs_dots_kernel(const DcgsArgs a
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cpv = (a.nblk_dot + kDotIW - 1) / kDotIW;
     float4 *part = a.part + (long)c * a.pstride;
-    const int npart = a.cmajor ? a.nblk_dot : cpv;         // partials per quantity for the last CTA
-    if (a.cmajor) {
+    const int npart = CM ? a.nblk_dot : cpv;               // partials per quantity for the last CTA
+    if constexpr (CM) {
         // chunk-major: CTA = chunk group blockIdx.x, warp w takes chunk blockIdx.x*kDotIW + w for every
         // vector i <= j.  The warp keeps its entries of u and x in registers and streams the basis chunks
         // through two shared-memory stages (bulk copies on an mbarrier each): q_{i+1} lands while q_i is
@@ -1350,16 +1353,19 @@ static int dcgs_dots_launch(Plan *p, GmresWork *g, int j, int has_x) {
     if (smem > 48 * 1024) {
         // the opt-in limit covers static and dynamic shared memory together
         cudaFuncAttributes fa{};
-        cudaError_t ea = cudaFuncGetAttributes(&fa, dcgs_dots_kernel);
+        auto kern = a.cmajor ? dcgs_dots_kernel<true> : dcgs_dots_kernel<false>;
+        cudaError_t ea = cudaFuncGetAttributes(&fa, kern);
         if (ea == cudaSuccess && smem + fa.sharedSizeBytes > p->smem_optin)
             return set_error(p, BTTB_ERR_INVALID_ARG, "restart length too large for the reduction's shared memory");
         if (ea == cudaSuccess)
-            ea = cudaFuncSetAttribute(dcgs_dots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(p->smem_optin - fa.sharedSizeBytes));
         if (ea != cudaSuccess) return check_cuda(p, ea, "delayed CGS2 reduction shared memory");
     }
     const int tok = prof_begin(p, 3);
-    cudaError_t e = launch_pdl(dcgs_dots_kernel, dim3(a.ich, g->k), dim3(kDotIW * 32), smem, p->stream, a, j, has_x);
+    cudaError_t e = a.cmajor
+        ? launch_pdl(dcgs_dots_kernel<true>, dim3(a.ich, g->k), dim3(kDotIW * 32), smem, p->stream, a, j, has_x)
+        : launch_pdl(dcgs_dots_kernel<false>, dim3(a.ich, g->k), dim3(kDotIW * 32), smem, p->stream, a, j, has_x);
     prof_end(p, tok, 0.0);
     count_launch(p);
     if (e != cudaSuccess) return check_cuda(p, e, "delayed CGS2 reduction launch");

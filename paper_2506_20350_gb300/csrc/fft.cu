@@ -529,6 +529,9 @@ __global__ void __launch_bounds__(kFft2Threads) fft2_fused_kernel(const Fft2Args
     for (int i = threadIdx.x; i < my + 5; i += blockDim.x) twy[i] = reinterpret_cast<const C *>(a.twy)[i];
     pdl_wait();
     if (a.active && !a.active[c]) return;                  // uniform over the cluster (same column)
+    // every CTA of the cluster must have started before another writes into its shared memory: arrive now,
+    // wait just before the exchange (long satisfied by then)
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
     if (!INV) {
         long ib = (long)c * a.ld + p;
         if (a.in_sel) ib += (long)(*a.in_sel) * a.in_sel_stride;
@@ -547,6 +550,7 @@ __global__ void __launch_bounds__(kFft2Threads) fft2_fused_kernel(const Fft2Args
             if (idx % ms >= ny) Y0[idx] = A::zero();
         __syncthreads();
         const C *R1 = fft2_level<A, false>(X0, X1, twx, a.sx, xs, nrow, 1);       // along kx, own rows
+        asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
         for (int idx = threadIdx.x; idx < mx * nrow; idx += blockDim.x) {
             const int kx = idx / nrow, il = idx - kx * nrow;
             const int q = ((kx + 1) * Q - 1) / mx;                                  // owner of column kx
@@ -570,6 +574,7 @@ __global__ void __launch_bounds__(kFft2Threads) fft2_fused_kernel(const Fft2Args
         }
         __syncthreads();
         const C *R1 = fft2_level<A, true>(Y0, Y1, twy, a.sy, 1, ncol, ms);        // along ky, own columns
+        asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
         for (int idx = threadIdx.x; idx < ncol * ny; idx += blockDim.x) {
             const int kl = idx / ny, iy = idx - kl * ny;
             const int q = ((iy + 1) * Q - 1) / ny;                                  // owner of row iy

@@ -465,10 +465,10 @@ def run_ours(args):
         return float(np.median(out))
 
     fp64_res = solve(inner=bt.BTTB_MV_FP64)
-    fp64_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP64), 3)
-    ir_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP32), 3)
+    fp64_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP64), 5)
+    ir_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP32), 5)
     bj_res = solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_BLOCK_JACOBI)
-    bj_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_BLOCK_JACOBI), 3)
+    bj_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_BLOCK_JACOBI), 5)
 
     x = torch.randn(1, n, dtype=torch.complex128, device=dev)
     y = torch.empty_like(x)

@@ -58,13 +58,6 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--learned-probe", action="store_true",
-                    help="profiling target: three applications of the learned correction to 16 columns and two "
-                         "training steps on 64 columns (40x40, b=96), then exit; prints no bench line")
-    ap.add_argument("--multi-probe", action="store_true",
-                    help="profiling target: four GMRES(10)-IR steps on 64 port excitations of the 30x30, b=60 "
-                         "array (the many-column kernels at a workspace of about 1 GB), then exit; prints no "
-                         "bench line")
     return ap.parse_args()
 
 
@@ -213,6 +206,83 @@ def cpu_oracle_product_time(gen, n, budget_s=12.0):
     return (time.perf_counter() - t0) / reps, reps
 
 
+class HostMlfft:
+    """The paper's multilevel-FFT product restated on the host cores (Sec. II-C, III-A, App. B), the second
+    CPU baseline: the spectrum of the wrapped first block column once (Eq. (circL2)), then per product the
+    zero padding of Eq. (xc2), the 2-level DFT (level 1 along the cells of a row, then level 2 along the
+    rows, App. B), the per-bin b x b block product of Eq. (multL), the inverse and the crop.  scipy.fft
+    with workers = the host's cores; numpy's batched matmul for the per-bin product; complex128."""
+
+    def __init__(self, gen, nx, ny, b, mx, my, workers):
+        import scipy.fft as sfft
+        self.fft, self.nx, self.ny, self.b, self.mx, self.my, self.w = sfft, nx, ny, b, mx, my, workers
+        c1 = np.zeros((my, mx, b, b), dtype=np.complex128)
+        for j in range(-(ny - 1), ny):
+            for i in range(-(nx - 1), nx):
+                c1[j % my, i % mx] = gen[j + ny - 1, i + nx - 1]
+        g = sfft.fft(c1, axis=1, workers=workers)
+        g = sfft.fft(g, axis=0, workers=workers) / (mx * my)
+        self.G = np.ascontiguousarray(g.reshape(my * mx, b, b))          # bin-major b x b blocks
+
+    def matvec(self, x):
+        """y = Z x for x of shape (N,) or (N, k)."""
+        nx, ny, b, mx, my, w = self.nx, self.ny, self.b, self.mx, self.my, self.w
+        k = 1 if x.ndim == 1 else x.shape[1]
+        u = np.zeros((my, mx, b, k), dtype=np.complex128)
+        u[:ny, :nx] = x.reshape(ny, nx, b, k)
+        u = self.fft.fft(u[:ny], n=mx, axis=1, workers=w)                 # level 1 on the ny nonzero rows
+        u = self.fft.fft(u, n=my, axis=0, workers=w)                      # level 2 (rows ny.. are zero)
+        v = np.matmul(self.G, u.reshape(my * mx, b, k)).reshape(my, mx, b, k)
+        v = self.fft.ifft(v, axis=0, workers=w)[:ny] * my
+        v = self.fft.ifft(v, axis=1, workers=w)[:, :nx] * mx
+        return v.reshape(-1) if x.ndim == 1 else v.reshape(-1, k)
+
+
+def host_mlfft_baseline(gen, nx, ny, b, mx, my, gmres_iters, cores, budget_s=10.0):
+    """Time the host MLFFT product on this workload (bounded sample) and a CPU GMRES(50) of the 4x4, b=12
+    array to 1e-10 with it; the 30x30 solve time is the per-product time times the products a solve needs."""
+    import oracle
+    from workloads import arrays
+    t0 = time.perf_counter()
+    hm = HostMlfft(gen, nx, ny, b, mx, my, cores)
+    setup_s = time.perf_counter() - t0
+    n = nx * ny * b
+    x = np.random.default_rng(0).standard_normal(n) + 1j * np.random.default_rng(1).standard_normal(n)
+    y = hm.matvec(x)
+    rows = np.random.default_rng(2).choice(n, size=8, replace=False)
+    ref = oracle.matvec_rows(gen, x, rows)
+    err = float(np.abs(y[rows] - ref).max() / np.abs(ref).max())
+    t0, reps = time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s or reps < 2:
+        hm.matvec(x)
+        reps += 1
+    per = (time.perf_counter() - t0) / reps
+    c = arrays.CONFIGS["tiny"]
+    gt = arrays.generator_blocks(c["nx"], c["ny"], c["b"], c["seed"])
+    ht = HostMlfft(gt, c["nx"], c["ny"], c["b"], 8, 8, cores)
+    vt = arrays.port_excitations(c["nx"], c["ny"], c["b"], [(1, 1)])[:, 0]
+    t0 = time.perf_counter()
+    xt, info = oracle.gmres(ht.matvec, vt, tol=c["tol"], restart=50, max_iters=5000)
+    tiny_s = time.perf_counter() - t0
+    tiny_rel = float(oracle.relres(gt, vt, xt)[0])
+    return {"kind": "paper_method_host", "cores": cores, "setup_s": setup_s, "product_ms": per * 1e3,
+            "product_gbs": product_bytes(nx, ny, b, mx, my, "fp64") / per / 1e9, "reps": reps,
+            "sampled_rows_rel_err_vs_oracle": err,
+            "solve_30x30_fp64_s_estimate": per * gmres_iters,
+            "solve_estimate_basis": f"{gmres_iters} products (the FP64 GMRES iterations and residuals on the GPU)",
+            "tiny_4x4_b12_gmres_s": tiny_s, "tiny_iters": int(info["iters"]), "tiny_relres_oracle": tiny_rel,
+            "sample": f"{reps} host MLFFT products of the 30x30 b=60 array (scipy.fft, workers={cores}, "
+                      "numpy batched matmul per bin)"}
+
+
+def oracle_relres_sampled(gen, V, I, cols):
+    """Relative residuals of the sampled columns, with the oracle's O(N^2) product (binary64)."""
+    import oracle
+    v = np.ascontiguousarray(V[:, cols])
+    i = np.ascontiguousarray(I[:, cols])
+    return [float(r) for r in oracle.relres(gen, v, i)]
+
+
 def run_reference(args):
     rank, world, _ = dist_setup(False)
     if rank != 0:
@@ -261,6 +331,7 @@ def learned_leg(dev, stream):
     plan = bt.Plan(nx, ny, b, max_rhs=64, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_FP32), stream=stream)
     g = arrays.generator_blocks_torch(nx, ny, b, c["seed"], device=dev)
     plan.set_generators(g)
+    gen_host = g.cpu().numpy()                # for the oracle's residual checks of sampled columns
     del g
     n = plan.n
     t0 = time.perf_counter()
@@ -326,13 +397,17 @@ def learned_leg(dev, stream):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            _, rc, rr = plan.solve(Vte, tol=tol, restart=50, max_iters=5000, pc=pc, inner=inner)
+            Isol, rc, rr = plan.solve(Vte, tol=tol, restart=50, max_iters=5000, pc=pc, inner=inner)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         its = [x.iters for x in rr]
         res[name] = {"solve_ms": dt * 1e3, "status_ok": sum(x.status == bt.BTTB_OK for x in rr),
                      "iters_mean": float(np.mean(its)), "iters_max": max(its),
                      "relres_true_max": max(x.relres_true for x in rr)}
+        if name in ("learned_ir", "block_jacobi_ir"):
+            samp = [0, c["ntest"] // 2, c["ntest"] - 1]
+            res[name]["oracle_relres_max_sampled"] = max(oracle_relres_sampled(
+                gen_host, Vte.cpu().numpy().T, Isol.cpu().numpy().T, samp))
     base = res["plain_fp64"]["solve_ms"]
     for v in res.values():
         v["speedup_vs_plain_fp64"] = base / v["solve_ms"]
@@ -466,7 +541,11 @@ def run_ours(args):
 
     fp64_res = solve(inner=bt.BTTB_MV_FP64)
     fp64_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP64), 5)
+    # GMRES whose products are IEEE binary64 (DFMA) end to end; Arnoldi, residuals and updates double-float
+    f64n_res = solve(inner=bt.BTTB_MV_FP64_NATIVE)
+    f64n_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP64_NATIVE), 5)
     ir_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP32), 5)
+    ir_oracle = oracle_relres_sampled(gen, v_host.T, I.cpu().numpy().T, [0])[0]     # I: the last IR solution
     bj_res = solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_BLOCK_JACOBI)
     bj_ms = timed(lambda: solve(inner=bt.BTTB_MV_FP32, pc=bt.BTTB_PC_BLOCK_JACOBI), 5)
 
@@ -528,7 +607,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         mt = time.perf_counter() - t0
         its = [r.iters for r in resm]
+        cols = [0, kall // 2, kall - 1]
+        vm_h, im_h = vm.cpu().numpy().T, im.cpu().numpy().T
+        multi_oracle = oracle_relres_sampled(gen, vm_h, im_h, cols)
         multi = {"columns": kall, "solve_ms": mt * 1e3, "ms_per_column": mt * 1e3 / kall,
+                 "oracle_relres_sampled": dict(zip(map(str, cols), multi_oracle)),
+                 "oracle_relres_max_sampled": max(multi_oracle),
                  "status_ok": sum(r.status == bt.BTTB_OK for r in resm), "iters_max": max(its),
                  "iters_mean": float(np.mean(its)), "relres_true_max": max(r.relres_true for r in resm),
                  "speedup_vs_fp64_column_by_column": fp64_ms * kall / (mt * 1e3),
@@ -565,7 +649,9 @@ def run_ours(args):
                                        flags=bt.BTTB_GMRES_GLOBAL)
         torch.cuda.synchronize()
         gt = time.perf_counter() - t0
+        glob_oracle = oracle_relres_sampled(gen, vm_h, im.cpu().numpy().T, cols)
         multi["global_gmres_ir"] = {"solve_ms": gt * 1e3, "iters": resg[0].iters,
+                                    "oracle_relres_max_sampled": max(glob_oracle),
                                     "status_ok": sum(r.status == bt.BTTB_OK for r in resg),
                                     "relres_true_max": max(r.relres_true for r in resg),
                                     "speedup_vs_fp64_column_by_column": fp64_ms * kall / (gt * 1e3)}
@@ -589,24 +675,39 @@ def run_ours(args):
         batch.solve(vs, tol=tol, restart=restart, inner=bt.BTTB_MV_FP32, max_iters=2)     # graphs + buffers
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, rcu, resu = batch.solve(vs, tol=tol, restart=restart, inner=bt.BTTB_MV_FP32)
+        Is_u, rcu, resu = batch.solve(vs, tol=tol, restart=restart, inner=bt.BTTB_MV_FP32)
         torch.cuda.synchronize()
         ut = time.perf_counter() - t0
-        # the same arrays one after another with plain FP64 GMRES
+        # sampled columns re-measured with the oracle: the first column of three arrays
+        samp = [0, len(specs) // 2, len(specs) - 1]
+        uneven_oracle = []
+        for i in samp:
+            sp = specs[i]
+            gi = arrays.generator_blocks(sp.nx, sp.ny, sp.b, sp.seed)
+            uneven_oracle += oracle_relres_sampled(gi, vs[i].cpu().numpy().T, Is_u[i].cpu().numpy().T, [0])
+        # the same arrays one after another: plain FP64 GMRES, and the batch's own precision (binary32
+        # products, FP64-class refinement) -- the second isolates the gain of running the arrays concurrently
         plans = [bt.bttb_batch_plan(batch.handle, i) for i in range(len(specs))]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(len(specs)):
-            out = torch.zeros_like(vs[i])
-            bt.bttb_gmres_solve(plans[i], vs[i], out, vs[i].shape[0], vs[i].shape[1],
-                                bt.gmres_opts(tol=tol, restart=restart, inner=bt.BTTB_MV_FP64))
-        torch.cuda.synchronize()
-        st = time.perf_counter() - t0
+
+        def sequential(inner):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(len(specs)):
+                out = torch.zeros_like(vs[i])
+                bt.bttb_gmres_solve(plans[i], vs[i], out, vs[i].shape[0], vs[i].shape[1],
+                                    bt.gmres_opts(tol=tol, restart=restart, inner=inner))
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0
+
+        st = sequential(bt.BTTB_MV_FP64)
+        st32 = sequential(bt.BTTB_MV_FP32)
         its = [r.iters for r in resu]
         uneven = {"arrays": len(specs), "columns": len(resu), "solve_ms": ut * 1e3,
                   "status_ok": sum(r.status == bt.BTTB_OK for r in resu), "iters_max": max(its),
                   "iters_mean": float(np.mean(its)), "relres_true_max": max(r.relres_true for r in resu),
+                  "oracle_relres_sampled_arrays": samp, "oracle_relres_max_sampled": max(uneven_oracle),
                   "sequential_fp64_ms": st * 1e3, "speedup_vs_sequential_fp64": st / ut,
+                  "sequential_ir_ms": st32 * 1e3, "speedup_vs_sequential_ir": st32 / ut,
                   "fft_chunk_widths": {str(w): widths.count(w) for w in sorted(set(widths))},
                   "unknowns_total": int(sum(s.nx * s.ny * s.b * s.nrhs for s in specs))}
         del vs
@@ -642,6 +743,8 @@ def run_ours(args):
         cpu = {"value": b64 / t_cpu / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
                "sample": f"{reps} brute-force O(N^2) FP64 products of the same matrix ({t_cpu:.2f} s each); "
                          "bytes counted as for one FFT product"}
+        cpu["mlfft_host"] = host_mlfft_baseline(gen, nx, ny, b, mx, my, fp64_res.iters + fp64_res.cycles + 1,
+                                                os.cpu_count() or 1)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -657,10 +760,16 @@ def run_ours(args):
                 "ms_per_step": e2e_s * 1e3 / args.steps},
         "gpu_launches": stall.launches,
         "clocks": clk,
-        "gmres": {"ir_ms": ir_ms, "fp64_ms": fp64_ms, "speedup_ir_vs_fp64": fp64_ms / ir_ms,
+        "gmres": {"comparator": "fp64_ms is GMRES with double-float (FP64-class) products, Arnoldi and "
+                                "residuals; binary64_products_ms runs the products in IEEE binary64 (DFMA); "
+                                "every speedup_* divides fp64_ms",
+                  "ir_ms": ir_ms, "fp64_ms": fp64_ms, "speedup_ir_vs_fp64": fp64_ms / ir_ms,
+                  "binary64_products_ms": f64n_ms, "binary64_products_iters": f64n_res.iters,
+                  "binary64_products_relres_true": f64n_res.relres_true,
+                  "speedup_ir_vs_binary64_products": f64n_ms / ir_ms,
                   "ir_iters": iters[0], "ir_cycles": cycles[0], "fp64_iters": fp64_res.iters,
                   "ir_relres_true": max(relres), "fp64_relres_true": fp64_res.relres_true,
-                  "block_jacobi_ir_ms": bj_ms, "block_jacobi_ir_iters": bj_res.iters,
+                  "ir_oracle_relres": ir_oracle, "block_jacobi_ir_ms": bj_ms, "block_jacobi_ir_iters": bj_res.iters,
                   "speedup_bj_ir_vs_fp64": fp64_ms / bj_ms},
         "matvec": mv,
         "step_breakdown_host_driven": breakdown,
@@ -673,61 +782,8 @@ def run_ours(args):
     plan.close()
 
 
-def learned_probe():
-    """A short, fixed launch sequence of the learned correction for kernel profilers."""
-    import torch
-
-    import paper_2506_20350_gb300 as bt
-    from workloads import arrays
-
-    if not torch.cuda.is_available():
-        raise SystemExit("the learned probe needs a CUDA GPU")
-    c = arrays.CONFIGS["learned"]
-    nx, ny, b = c["nx"], c["ny"], c["b"]
-    plan = bt.Plan(nx, ny, b, max_rhs=64)
-    plan.set_generators(arrays.generator_blocks_torch(nx, ny, b, c["seed"]))
-    lrn = bt.Learned(plan, rank=16, channels=64, max_cols=64, seed=c["seed"])
-    r = torch.from_numpy(arrays.random_vectors(plan.n, 64, seed=0).T.astype(np.complex64)).cuda().contiguous()
-    torch.cuda.synchronize()
-    for _ in range(3):
-        lrn.apply(r[:16].contiguous())
-    for _ in range(2):
-        lrn.train_step(r, r, lr=1e-4, want_loss=False)
-    torch.cuda.synchronize()
-    lrn.close()
-    plan.close()
-
-
-def multi_probe():
-    """A short, fixed launch sequence of the many-column kernels for kernel profilers: 64 columns take the
-    per-bin GEMM, the chunk-major delayed-CGS2 reduction and the multi-column FFT passes."""
-    import torch
-
-    import paper_2506_20350_gb300 as bt
-    from workloads import arrays
-
-    if not torch.cuda.is_available():
-        raise SystemExit("the multi-column probe needs a CUDA GPU")
-    c = arrays.CONFIGS["precision"]
-    nx, ny, b = c["nx"], c["ny"], c["b"]
-    k = 64
-    plan = bt.Plan(nx, ny, b, max_rhs=k, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_FP32))
-    plan.set_generators(arrays.generator_blocks_torch(nx, ny, b, c["seed"]))
-    cells = [(i % nx, i // nx) for i in range(k)]
-    v = torch.from_numpy(arrays.port_excitations(nx, ny, b, cells).T.copy()).cuda()
-    plan.solve(v, tol=1e-8, restart=10, inner=bt.BTTB_MV_FP32, max_iters=4)
-    torch.cuda.synchronize()
-    plan.close()
-
-
 def main():
     args = parse_args()
-    if args.learned_probe:
-        learned_probe()
-        return
-    if args.multi_probe:
-        multi_probe()
-        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -242,9 +242,14 @@ int bttb_profile_read(bttb_plan plan, int which, bttb_kernel_stats *out);
  *     2*(mx*my*b*b*16) + 2*(mx*my*nrhs*b*16) bytes; the 4x4, b=12 array fits,
  *     the 30x30, b=60 array does not).
  *   - All calls on a device share the array and it keeps the last call's
- *     contents; each call rewrites every buffer before reading it and clears
- *     the error word.  Calls that overlap on the GPU (different streams or
- *     host threads) race on the array: serialise them.
+ *     contents; each call rewrites every buffer before reading it.  Calls
+ *     that overlap on the GPU (different streams or host threads) race on the
+ *     array: serialise them.
+ *   - The call returns BTTB_OK once its work is queued and never reads
+ *     anything back, so it reports no device-side finding: non-finite
+ *     generators give a non-finite y (bttb_set_generators would reject
+ *     them), and a bounded pipeline wait that runs out leaves y unfinished.
+ *     Check y where that matters.
  *   - The first call on a device looks up the array's address
  *     (cudaGetSymbolAddress, once per device, with that device current):
  *     make that first call before any stream capture begins.
@@ -350,6 +355,27 @@ int bttb_learned_destroy(bttb_learned l);
  * the plan's GMRES workspace (it is rebuilt on the next solve).
  */
 int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out);
+
+/*
+ * Test hooks for the failure paths; the paper has no counterpart.  Nothing
+ * here faults or hangs the GPU: every device pipeline wait is bounded, and the
+ * injected fault is an mbarrier arrival that a kernel withholds, which the
+ * same kernel supplies once its wait has run out, before it drains its copies
+ * in flight and returns.
+ *   BTTB_DEBUG_WAIT_LIMIT_NS (value in ns, 0 = the default of 2 s, at most
+ *     60 s): bound of every pipeline wait in this plan's kernels.  Frees the
+ *     plan's GMRES workspace (its captured cycles hold the old bound).
+ *   BTTB_DEBUG_WITHHOLD_ARRIVAL (value = a count, at most 1000): the next
+ *     `value` launches of the block product for one to eight columns outside
+ *     CUDA graph capture withhold the first arrival of one warp, so that
+ *     warp's first wait runs out after the wait limit; the launch then sets
+ *     the plan's device error word to TIMEOUT (reported by the next
+ *     synchronising call that reads it, e.g. bttb_gmres_solve, as
+ *     BTTB_ERR_TIMEOUT) and leaves the product unfinished.
+ * Returns BTTB_ERR_INVALID_ARG for an unknown hook or a value out of range.
+ */
+enum { BTTB_DEBUG_WAIT_LIMIT_NS = 1, BTTB_DEBUG_WITHHOLD_ARRIVAL = 2 };
+int bttb_plan_debug(bttb_plan plan, int what, long long value);
 
 /* Bytes of device memory the plan holds (spectrum copies and workspace). */
 size_t bttb_plan_workspace_bytes(bttb_plan plan);

@@ -27,6 +27,7 @@ BTTB_ERR_INVALID_ARG, BTTB_ERR_CUDA, BTTB_ERR_OOM = -1, -2, -3
 BTTB_ERR_NO_GENERATORS, BTTB_ERR_TIMEOUT, BTTB_ERR_NONFINITE, BTTB_ERR_SINGULAR = -4, -5, -6, -7
 
 BTTB_K_BLOCK_PRODUCT, BTTB_K_FFT, BTTB_K_ALL, BTTB_K_BLOCK_PRODUCT_PREC = 0, 1, 2, 16
+BTTB_DEBUG_WAIT_LIMIT_NS, BTTB_DEBUG_WITHHOLD_ARRIVAL = 1, 2
 
 EXPORTS = ("bttb_plan_create", "bttb_plan_grid", "bttb_set_generators", "bttb_matvec",
            "bttb_gmres_solve", "bttb_block_jacobi_apply", "bttb_get_spectrum_bin",
@@ -35,7 +36,8 @@ EXPORTS = ("bttb_plan_create", "bttb_plan_grid", "bttb_set_generators", "bttb_ma
            "bttb_batch_gmres_solve", "bttb_batch_destroy",
            "bttb_learned_create", "bttb_learned_param_count", "bttb_learned_params", "bttb_learned_apply",
            "bttb_learned_gradients", "bttb_learned_train_step", "bttb_plan_set_learned", "bttb_learned_destroy",
-           "bttb_plan_autotune", "bttb_plan_workspace_bytes", "bttb_plan_destroy", "bttb_last_error")
+           "bttb_plan_autotune", "bttb_plan_debug", "bttb_plan_workspace_bytes", "bttb_plan_destroy",
+           "bttb_last_error")
 
 
 class BttbError(RuntimeError):
@@ -100,6 +102,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bttb_plan_set_learned.argtypes = [vp, vp]
     lib.bttb_learned_destroy.argtypes = [vp]
     lib.bttb_plan_autotune.argtypes = [vp, ci, ci, pi]
+    lib.bttb_plan_debug.argtypes = [vp, ci, ctypes.c_longlong]
     lib.bttb_plan_workspace_bytes.argtypes = [vp]
     lib.bttb_plan_workspace_bytes.restype = ctypes.c_size_t
     lib.bttb_plan_destroy.argtypes = [vp]
@@ -293,6 +296,11 @@ def bttb_plan_autotune(plan, nrhs: int = 1, reps: int = 5) -> int:
     out = ctypes.c_int(0)
     _check(load_library().bttb_plan_autotune(plan, nrhs, reps, ctypes.byref(out)), plan)
     return out.value
+
+
+def bttb_plan_debug(plan, what: int, value: int) -> None:
+    """Failure-path test hooks (BTTB_DEBUG_WAIT_LIMIT_NS, BTTB_DEBUG_WITHHOLD_ARRIVAL)."""
+    _check(load_library().bttb_plan_debug(plan, what, value), plan)
 
 
 def bttb_plan_workspace_bytes(plan) -> int:

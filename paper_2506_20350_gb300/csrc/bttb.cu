@@ -348,6 +348,25 @@ int bttb_profile_read(bttb_plan plan, int which, bttb_kernel_stats *out) {
 
 size_t bttb_plan_workspace_bytes(bttb_plan plan) { return plan ? plan->p.bytes_held : 0; }
 
+int bttb_plan_debug(bttb_plan plan, int what, long long value) {
+    if (!plan) return set_error(nullptr, BTTB_ERR_INVALID_ARG, "plan is NULL");
+    Plan &p = plan->p;
+    switch (what) {
+        case BTTB_DEBUG_WAIT_LIMIT_NS:
+            if (value < 0 || value > 60000000000ll)
+                return set_error(&p, BTTB_ERR_INVALID_ARG, "wait limit must be in [0, 60 s] (0: the default)");
+            p.wait_ns = value == 0 ? 2000000000ull : (unsigned long long)value;
+            gmres_free(&p);                           // captured cycles hold the old limit
+            return BTTB_OK;
+        case BTTB_DEBUG_WITHHOLD_ARRIVAL:
+            if (value < 0 || value > 1000) return set_error(&p, BTTB_ERR_INVALID_ARG, "count must be in [0, 1000]");
+            p.withhold = (int)value;
+            return BTTB_OK;
+        default:
+            return set_error(&p, BTTB_ERR_INVALID_ARG, "unknown debug hook");
+    }
+}
+
 int bttb_plan_destroy(bttb_plan plan) {
     if (!plan) return BTTB_OK;
     plan_release(plan->p);

@@ -46,6 +46,8 @@ struct ContractArgs {
     int Qc, nchunks, G, nstages;
     uint32_t st_bytes, off_g1, off_u, red_off;
     int *err;
+    unsigned long long wait_ns;   // bound of every pipeline wait
+    int withhold;                 // test hook: warp 0 of CTA 0 withholds the arrival of its first item
 };
 
 template <class A> struct Acc;
@@ -161,12 +163,15 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
         if (NPL == 2)
             bulk_g2s(st + a.off_g1, reinterpret_cast<const GT *>(a.g1) + goff, gbytes, &full[s], pol_stream);
     };
+    // test hook: the first item of warp 0 of CTA 0 gets its bytes but not its arrival, so its wait runs out
+    const bool withheld0 = a.withhold && blockIdx.x == 0 && warp == 0;
     auto issue_u = [&](int it) {
         const int s = it % kWarpStages;
         const int bin = first + step * (it / a.nchunks);
         const uint32_t ubytes = round_up16((uint32_t)(a.kc * b) * (uint32_t)sizeof(C));
         unsigned char *st = stages + (size_t)s * a.st_bytes;
-        mbar_arrive_expect_tx(&full[s], ubytes);
+        if (withheld0 && it == 0) mbar_expect_tx(&full[s], ubytes);
+        else mbar_arrive_expect_tx(&full[s], ubytes);
         bulk_g2s(st + a.off_u, reinterpret_cast<const C *>(a.u) + (long)bin * a.ubs, ubytes, &full[s], pol_keep);
     };
     // The spectrum does not depend on the preceding kernel: start streaming it before the
@@ -194,7 +199,8 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
     Acc<A> acc[KC][R];
     const int p0 = lane * R;
     bool failed = false;
-    for (int it = 0; it < nitems; ++it) {
+    int it = 0;
+    for (; it < nitems; ++it) {
         const int s = it % kWarpStages;
         const uint32_t ph = (uint32_t)(it / kWarpStages) & 1u;
         // keep kWarpStages-1 items in flight: the stage refilled now was released last iteration
@@ -203,9 +209,12 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
             issue_u(it + kWarpStages - 1);
         }
         const int bin = first + step * (it / a.nchunks), ch = it % a.nchunks;
-        if (!failed && !mbar_wait_bounded(&full[s], ph, abort_flag)) {
+        // a wait that ran out (or saw another warp's abort) ends the warp's loop; the decision is uniform
+        // over the warp, so no lane goes on to issue or read a stage the others gave up on
+        const bool ok = mbar_wait_bounded(&full[s], ph, abort_flag, a.wait_ns);
+        if (__any_sync(0xffffffffu, !ok)) {
             failed = true;
-            if (lane == 0) atomicOr(a.err, DEVERR_TIMEOUT);
+            break;
         }
         if (ch == 0) {
 #pragma unroll
@@ -213,7 +222,7 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
 #pragma unroll
                 for (int r = 0; r < R; ++r) acc[c][r].zero();
         }
-        if (!failed) {
+        {
             const int q0 = ch * a.Qc;
             const int qn = min(a.Qc, b - q0);
             const unsigned char *st = stages + (size_t)s * a.st_bytes;
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
         // all lanes are done reading stage s before lane 0 may refill it (next iteration)
         __syncwarp();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (ch == a.nchunks - 1 && !failed) {
+        if (ch == a.nchunks - 1) {
 #pragma unroll
             for (int c = 0; c < KC; ++c)
 #pragma unroll
@@ -264,9 +273,14 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
     }
     pdl_trigger();
     if (failed && lane == 0) {
-        // drain copies that may still be in flight into this warp's stages
-        for (int d = nitems - 1; d >= 0 && d >= nitems - kWarpStages; --d)
+        atomicOr(a.err, DEVERR_TIMEOUT);
+        // Items it .. it+kWarpStages-1 were issued and not consumed, each into its own stage (every earlier
+        // item completed its phase).  A withheld arrival is supplied now; then each item's copies are drained
+        // (bounded) before the CTA's shared memory goes away.
+        for (int d = it; d < nitems && d < it + kWarpStages; ++d) {
+            if (withheld0 && d == 0) mbar_arrive(&full[d % kWarpStages]);
             mbar_wait_drain(&full[d % kWarpStages], (uint32_t)(d / kWarpStages) & 1u);
+        }
     }
 }
 
@@ -288,6 +302,15 @@ static int launch_contract_impl(Plan *p, const void *u, void *v, int k, const in
     a.nbins = (int)p->bins;
     a.b = b;
     a.err = p->d_err;
+    a.wait_ns = p->wait_ns;
+    a.withhold = 0;
+    if (p->withhold > 0) {                                 // test hook, never inside a captured graph
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(p->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            a.withhold = 1;
+            --p->withhold;
+        }
+    }
     if constexpr (A::kind == 0) {
         a.g0 = p->ghat_hi;
         a.g1 = p->ghat_lo;
@@ -339,6 +362,7 @@ static int launch_contract_impl(Plan *p, const void *u, void *v, int k, const in
         a.active = active ? active + c0 : nullptr;
         const int tok = prof_begin(p, BTTB_K_BLOCK_PRODUCT_PREC + prec_of<A>());
         e = launch_pdl(kern, dim3(grid), dim3(kConsumerWarps * 32), smem, p->stream, a);
+        a.withhold = 0;                                    // one launch per injection
         count_launch(p);
         if (e != cudaSuccess) return check_cuda(p, e, "contract launch");
         // algorithmic bytes: spectrum planes once, transformed vectors in and out
@@ -394,7 +418,8 @@ constexpr int kMultiTile = 64;
 
 template <int CPG>
 __global__ void __launch_bounds__(256) contract_multi_kernel(const float2 *g0, long gbs, const float2 *u, float2 *v,
-                                                              long ubs, int b, int k, int *err) {
+                                                              long ubs, int b, int k, int *err,
+                                                              unsigned long long wait_ns) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8);
@@ -417,7 +442,7 @@ __global__ void __launch_bounds__(256) contract_multi_kernel(const float2 *g0, l
         bulk_g2s(gs, g0 + (long)bin * gbs, gb, bar, l2_policy_evict_last());
         bulk_g2s(us, u + (long)bin * ubs + (long)c0 * b, ub, bar, l2_policy_evict_first());
     }
-    const bool ok = mbar_wait_bounded(bar, 0, abort_flag);
+    const bool ok = mbar_wait_bounded(bar, 0, abort_flag, wait_ns);
     if (!ok) {
         if (threadIdx.x == 0) {
             atomicOr(err, DEVERR_TIMEOUT);
@@ -459,7 +484,8 @@ __global__ void __launch_bounds__(256) contract_multi_kernel(const float2 *g0, l
 // is even) and four vector entries (the two column groups of a warp are adjacent columns, on different
 // banks): 6 shared loads per 64 FMAs.
 __global__ void __launch_bounds__(256) contract_multi44_kernel(const float2 *g0, long gbs, const float2 *u,
-                                                                float2 *v, long ubs, int b, int k, int *err) {
+                                                                float2 *v, long ubs, int b, int k, int *err,
+                                                                unsigned long long wait_ns) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8);
@@ -482,7 +508,7 @@ __global__ void __launch_bounds__(256) contract_multi44_kernel(const float2 *g0,
         bulk_g2s(gs, g0 + (long)bin * gbs, gb, bar, l2_policy_evict_last());
         bulk_g2s(us, u + (long)bin * ubs + (long)c0 * b, ub, bar, l2_policy_evict_first());
     }
-    const bool ok = mbar_wait_bounded(bar, 0, abort_flag);
+    const bool ok = mbar_wait_bounded(bar, 0, abort_flag, wait_ns);
     if (!ok) {
         if (threadIdx.x == 0) {
             atomicOr(err, DEVERR_TIMEOUT);
@@ -552,7 +578,7 @@ static int launch_contract_multi(Plan *p, const void *u, void *v, int k) {
     const dim3 grid((k + kMultiTile - 1) / kMultiTile, (unsigned)p->bins);
     const int tok = prof_begin(p, BTTB_K_BLOCK_PRODUCT_PREC + BTTB_MV_FP32);
     e = launch_pdl(kern, grid, dim3(256), smem, p->stream, (const float2 *)p->ghat_hi, p->gbs, (const float2 *)u,
-                   (float2 *)v, p->ubs, b, k, p->d_err);
+                   (float2 *)v, p->ubs, b, k, p->d_err, p->wait_ns);
     count_launch(p);
     prof_end(p, tok, (double)p->bins * ((double)b * b * 8 + 2.0 * k * b * 8));
     if (e != cudaSuccess) return check_cuda(p, e, "multi-RHS launch");

@@ -45,6 +45,7 @@ struct GmresWork {
     float2 *cs = nullptr;
     float4 *hco = nullptr, *ycoef = nullptr, *part = nullptr;
     double *beta2 = nullptr, *vnorm = nullptr, *inv_beta = nullptr, *target = nullptr;
+    unsigned long long *cmax = nullptr;   // per user column: largest |Re|, |Im| of V (binary64 bits)
     int *active = nullptr, *steps = nullptr, *bdown = nullptr, *mlimit = nullptr, *d_j = nullptr, *d_any = nullptr;
     double2 *io = nullptr;        // staging for host_io
     int *h_any = nullptr;         // pinned
@@ -67,16 +68,55 @@ constexpr int kVecThreads = 256;
 
 // ------------------------------------------------------------------ kernels
 
-__global__ void cvt_in_kernel(const double2 *in, long ld, float4 *out, long n) {
+// Input scaling.  Double-float numbers have binary32's exponent range, so a right-hand side whose entries
+// lie far from 1 (below ~1e-19 its squared norm underflows, above ~1e19 it overflows) cannot be solved as
+// given.  Each column c of V (and of the initial guess) is therefore multiplied by 2^-e_c, e_c the binary64
+// exponent of the column's largest |Re| or |Im|, before the conversion, and the solution by 2^e_c after it.
+// Scaling by a power of two is exact and commutes with every rounding of the solver, so the iterates are
+// the same as for the unscaled column whenever that one stays in range; the relative residual does not
+// change.  Global GMRES uses one exponent for all columns (its Frobenius inner products mix them).
+//
+// cmax[c * cstride] = largest |Re|, |Im| of column c as binary64 bits: for non-negative doubles the integer
+// order is the numeric order and a NaN sorts above +Inf, so one NaN makes the column's maximum NaN.
+__global__ void colmax_kernel(const double2 *in, long ld, long n, unsigned long long *cmax, int cstride) {
     const int c = blockIdx.y;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        out[(long)c * n + i] = F64N::to_cdf(in[(long)c * ld + i]);
+    unsigned long long m = 0ull;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double2 v = in[(long)c * ld + i];
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(v.x)));
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(v.y)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0 && m != 0ull) atomicMax(cmax + (long)c * cstride, m);
 }
 
-__global__ void cvt_out_kernel(const float4 *in, double2 *out, long ld, long n) {
+// e_c of a column maximum; zero and non-finite columns stay unscaled (the norm check reports the latter).
+__device__ __forceinline__ int col_exponent(unsigned long long bits) {
+    const double m = __longlong_as_double((long long)bits);
+    return (m > 0.0 && isfinite(m)) ? ilogb(m) : 0;
+}
+
+__global__ void cvt_in_kernel(const double2 *in, long ld, float4 *out, long n, const unsigned long long *cmax,
+                              int cstride) {
     const int c = blockIdx.y;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        out[(long)c * ld + i] = DF64::to_c128(DF64::from_cdf(in[(long)c * n + i]));
+    const int e = col_exponent(cmax[(long)c * cstride]);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double2 v = in[(long)c * ld + i];
+        out[(long)c * n + i] = F64N::to_cdf(make_double2(ldexp(v.x, -e), ldexp(v.y, -e)));
+    }
+}
+
+// I = 2^e_c X; a column whose V is exactly zero has the solution zero, whatever the initial guess.
+__global__ void cvt_out_kernel(const float4 *in, double2 *out, long ld, long n, const unsigned long long *cmax,
+                               int cstride) {
+    const int c = blockIdx.y;
+    const unsigned long long bits = cmax[(long)c * cstride];
+    const int e = col_exponent(bits);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double2 v = DF64::to_c128(DF64::from_cdf(in[(long)c * n + i]));
+        out[(long)c * ld + i] = bits == 0ull ? make_double2(0.0, 0.0) : make_double2(ldexp(v.x, e), ldexp(v.y, e));
+    }
 }
 
 __global__ void fill_zero_kernel(float4 *x, long count) {
@@ -648,6 +688,7 @@ struct DcgsArgs {
     const int *mlimit;
     const double *target;
     int *err;
+    unsigned long long wait_ns;   // bound of every pipeline wait
 };
 
 // Sums four per-lane accumulators over the warp by a reduce-scatter butterfly: at offset 16 each half keeps
@@ -727,7 +768,7 @@ __global__ void __launch_bounds__(kDotIW * 32, CM ? 2 : 3) dcgs_dots_kernel(cons
                         issued = i + 1;
                     }
                     if (!failed) {
-                        if (mbar_wait_bounded(&bar[i & 1], (uint32_t)(i >> 1) & 1u, &s_abort)) {
+                        if (mbar_wait_bounded(&bar[i & 1], (uint32_t)(i >> 1) & 1u, &s_abort, a.wait_ns)) {
                             waited = i;
                         } else {
                             failed = true;
@@ -1118,7 +1159,7 @@ static void free_work(GmresWork *g) {
     cudaFree(g->target); cudaFree(g->active); cudaFree(g->steps); cudaFree(g->bdown); cudaFree(g->mlimit);
     cudaFree(g->d_j); cudaFree(g->d_any); cudaFree(g->io); cudaFree(g->act_cycle);
     cudaFree(g->counters); cudaFree(g->d_any_step); cudaFree(g->act_prod);
-    cudaFree(g->U); cudaFree(g->cco); cudaFree(g->hpre); cudaFree(g->Horig);
+    cudaFree(g->U); cudaFree(g->cco); cudaFree(g->hpre); cudaFree(g->Horig); cudaFree(g->cmax);
     cudaFreeHost(g->h_any);
     delete g;
 }
@@ -1181,6 +1222,7 @@ static int ensure_work(Plan *p, int m, int k, long nv, int kp, bool flex, bool h
     alloc(&g->cs, sizeof(float2) * (size_t)k * m);
     alloc(&g->beta2, sizeof(double) * ks);
     alloc(&g->act_prod, sizeof(int) * kp);
+    alloc(&g->cmax, sizeof(unsigned long long) * kp);
     alloc(&g->vnorm, sizeof(double) * k);
     alloc(&g->inv_beta, sizeof(double) * k);
     alloc(&g->target, sizeof(double) * k);
@@ -1342,6 +1384,7 @@ static DcgsArgs dcgs_args(Plan *p, GmresWork *g, int j) {
     a.mlimit = g->mlimit;
     a.target = g->target;
     a.err = p->d_err;
+    a.wait_ns = p->wait_ns;
     return a;
 }
 
@@ -1519,8 +1562,14 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
         Vd = g->io;
         ldv = n;
     }
-    cvt_in_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(Vd, ldv, g->Vin, n);
-    count_launch(p);
+    // column exponents of V (one for all columns in global GMRES), then V and x0 scaled by them
+    const int cstride = glob ? 0 : 1;
+    if ((e = cudaMemsetAsync(g->cmax, 0, sizeof(unsigned long long) * k, st)) != cudaSuccess)
+        return check_cuda(p, e, "column scale");
+    colmax_kernel<<<dim3(std::min(vgrid, 64), k), kVecThreads, 0, st>>>(Vd, ldv, n, g->cmax, cstride);
+    cvt_in_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(Vd, ldv, g->Vin, n, g->cmax, cstride);
+    count_launch(p, 2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return check_cuda(p, e, "input conversion");
     if (o->use_x0) {
         const double2 *Xd = reinterpret_cast<const double2 *>(I);
         long ldx = ld;
@@ -1531,7 +1580,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
             Xd = g->io;
             ldx = n;
         }
-        cvt_in_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(Xd, ldx, g->X, n);
+        cvt_in_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(Xd, ldx, g->X, n, g->cmax, cstride);
         count_launch(p);
     } else {
         fill_zero_kernel<<<1024, kVecThreads, 0, st>>>(g->X, (long)k * n);
@@ -1569,7 +1618,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
         if (!glob) {
             for (int c = 0; c < k; ++c) {
                 if (done[c]) { act[c] = 0; continue; }
-                relres[c] = vnorm[c] > 0.0 ? std::sqrt(b2[c]) / vnorm[c] : 0.0;
+                relres[c] = vnorm[c] == 0.0 ? 0.0 : std::sqrt(b2[c]) / vnorm[c];   // NaN for a non-finite V
                 if (!std::isfinite(relres[c])) {
                     status[c] = BTTB_ERR_NONFINITE;
                     done[c] = 1;
@@ -1600,7 +1649,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
             double f2 = 0.0;
             bool all_ok = true, bad = false;
             for (int c = 0; c < k; ++c) {
-                relres[c] = vnorm[c] > 0.0 ? std::sqrt(b2[c]) / vnorm[c] : 0.0;
+                relres[c] = vnorm[c] == 0.0 ? 0.0 : std::sqrt(b2[c]) / vnorm[c];   // NaN for a non-finite V
                 if (!std::isfinite(relres[c])) bad = true;
                 if (!(relres[c] <= o->tol) && vnorm[c] != 0.0) all_ok = false;
                 f2 += b2[c];
@@ -1633,13 +1682,14 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
         }
         if (o->history && hist_n < o->history_len) o->history[hist_n++] = relres[0];
         if (!any) break;
-        cudaMemcpyAsync(g->active, act.data(), sizeof(int) * kg, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(g->act_cycle, act.data(), sizeof(int) * kg, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(g->mlimit, mlim.data(), sizeof(int) * kg, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(g->target, tgt.data(), sizeof(double) * kg, cudaMemcpyHostToDevice, st);
-        cudaMemsetAsync(g->bdown, 0, sizeof(int) * kg, st);
-        cudaMemsetAsync(g->steps, 0, sizeof(int) * kg, st);
-        cudaMemsetAsync(g->d_any_step, 0, sizeof(int), st);
+        e = cudaMemcpyAsync(g->active, act.data(), sizeof(int) * kg, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->act_cycle, act.data(), sizeof(int) * kg, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->mlimit, mlim.data(), sizeof(int) * kg, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->target, tgt.data(), sizeof(double) * kg, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->bdown, 0, sizeof(int) * kg, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->steps, 0, sizeof(int) * kg, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->d_any_step, 0, sizeof(int), st);
+        if (e != cudaSuccess) return check_cuda(p, e, "cycle set-up");
         cycle_start_kernel<<<1, 256, 0, st>>>(g->beta2, g->gv, g->inv_beta, m, kg, g->active);
         count_launch(p);
         // the first basis vector r/beta: into the basis (CGS2) or as u_0 (delayed CGS2)
@@ -1695,7 +1745,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
         Id = g->io;
         ldo = n;
     }
-    cvt_out_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(g->X, Id, ldo, n);
+    cvt_out_kernel<<<dim3(vgrid, k), kVecThreads, 0, st>>>(g->X, Id, ldo, n, g->cmax, cstride);
     count_launch(p);
     if (o->host_io) {
         e = cudaMemcpy2DAsync(I, ld * sizeof(double2), g->io, n * sizeof(double2), n * sizeof(double2), k,

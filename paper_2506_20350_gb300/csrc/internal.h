@@ -90,6 +90,11 @@ struct Plan {
     long ubs = 0;                 // bin stride (elements) of the spectral vectors
     size_t ws_bytes = 0;
 
+    // Failure-path test hooks (bttb_plan_debug): bound of the kernels' pipeline waits, and the number of
+    // coming uncaptured one-to-eight-column block products that withhold one mbarrier arrival.
+    unsigned long long wait_ns = 2000000000ull;
+    int withhold = 0;
+
     GmresWork *gw = nullptr;
     Learned *learned = nullptr;   // attached learned preconditioner (learned.cu), not owned
     int *d_err = nullptr;         // device error word

@@ -11,10 +11,12 @@
 // library holds until the process exits.
 //
 // The scratch array is shared by every call on a device and keeps the last
-// call's contents.  Every buffer in it is fully rewritten before it is read,
-// except the error word, which each call clears.  Calls that overlap on the
-// GPU (two streams, or two host threads) race on the array: callers must
-// serialise them.
+// call's contents.  Every buffer in it is fully rewritten before it is read;
+// the device error word the kernels write into (non-finite spectrum entries,
+// a bounded wait that ran out) is cleared by each call but never read back:
+// the call does not synchronise, so it cannot report what the GPU finds.
+// Calls that overlap on the GPU (two streams, or two host threads) race on
+// the array: callers must serialise them.
 //
 // The first call on a device looks up the array's device address with
 // cudaGetSymbolAddress (once per device, with that device current); make that

@@ -4,9 +4,13 @@ CPU oracle (oracle/learned.py), and its use inside flexible GMRES.
 The CUDA path reads bfloat16 copies of B, A and the convolution weights (the
 biases stay binary32) and accumulates in binary32, with binary32 FFTs and a
 binary32 block-Jacobi part.  The oracle therefore gets the same bfloat16-rounded
-parameters and runs in binary64; the remaining difference is binary32 rounding
-through a few dozen accumulation steps, so outputs and gradients are compared
-at 2e-4 relative (norm-wise per parameter group, and max-norm on outputs).
+parameters and runs in binary64; the remaining difference is binary32 rounding.
+An output of M(r) passes through a few dozen accumulation steps, so outputs and
+the loss are compared at TOL = 2e-4 relative (max-norm and 2-norm).  A weight
+gradient sums products over every grid position, column and tap of the
+minibatch (thousands of binary32 terms, in per-chunk partial sums), so the
+gradients are compared at GRAD_TOL = 1e-3 relative, norm-wise per parameter
+group.
 """
 import numpy as np
 import pytest
@@ -20,6 +24,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 TOL = 2e-4
+GRAD_TOL = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -121,7 +126,7 @@ def test_gradients_match_oracle(bt, nx, ny, b, rank, ch, k):
     loss, g = lrn.gradients(rd, ed)
     assert abs(loss - loss_ref) <= TOL * loss_ref, (loss, loss_ref)
     for name in ("B", "A", "W1", "c1", "W2", "c2", "W3", "c3"):
-        assert _rel(g[name], g_ref[name]) <= 1e-3, (name, _rel(g[name], g_ref[name]))
+        assert _rel(g[name], g_ref[name]) <= GRAD_TOL, (name, _rel(g[name], g_ref[name]))
     lrn.close()
     plan.close()
 
@@ -219,8 +224,9 @@ def test_trained_correction_in_fgmres(bt):
     _, rc_bj, res_bj = plan.solve(Vte, tol=tol, restart=50, max_iters=2000, pc=bt.BTTB_PC_BLOCK_JACOBI)
     I_l, rc_l, res_l = plan.solve(Vte, tol=tol, restart=50, max_iters=2000, pc=bt.BTTB_PC_LEARNED)
     assert rc_bj == 0 and rc_l == 0
+    assert all(r.relres_true <= tol for r in res_l)
     rel = oracle.relres(gen, Vte.cpu().numpy().T, I_l.cpu().numpy().T)
-    assert np.all(rel <= tol * 1.01), rel
+    assert np.all(rel <= tol), rel
     it_bj = sum(r.iters for r in res_bj)
     it_l = sum(r.iters for r in res_l)
     assert it_l < it_bj, (it_l, it_bj)

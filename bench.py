@@ -167,23 +167,30 @@ def product_bytes(nx, ny, b, mx, my, prec):
     return bins * b * b * 16 + 2 * n * 16         # double-float planes or binary64 copy
 
 
-def traffic_from_profiles(kernel_key: str):
-    """ncu DRAM bytes per launch recorded in profiles/, if the kernel source is unchanged."""
-    src = os.path.join(ROOT, "paper_2506_20350_gb300", "csrc", "contract.cu")
-    # digest of the code lines (comments excluded) of the block-product kernel template and its
-    # launch configuration: other kernels of the file, and comment edits, keep the capture valid
+def kernel_digest(src_name: str) -> str | None:
+    """Digest of the code lines (comments excluded) of the kernel an ncu capture in profiles/ measured:
+    the block-product kernel template and its launch configuration (contract.cu), or the whole fused
+    level-2 kernel file (ycontract.cu).  Comment edits keep a capture valid; code edits void it."""
+    src = os.path.join(ROOT, "paper_2506_20350_gb300", "csrc", src_name)
     text = open(src).read()
-    try:
-        a = text.index("// KC: right-hand sides per launch")
-        b = text.index("template <class A>\nconstexpr int prec_of()")
-        c = text.index("static int launch_contract_impl(")
-        d = text.index("\n}\n", c)
-    except ValueError:
-        return None
-    code = [ln for ln in (text[a:b] + "\n" + text[c:d]).splitlines() if not ln.strip().startswith("//")]
-    digest = hashlib.sha1("\n".join(code).encode()).hexdigest()[:12]
+    if src_name == "contract.cu":
+        try:
+            a = text.index("// KC: right-hand sides per launch")
+            b = text.index("template <class A>\nconstexpr int prec_of()")
+            c = text.index("static int launch_contract_impl(")
+            d = text.index("\n}\n", c)
+        except ValueError:
+            return None
+        text = text[a:b] + "\n" + text[c:d]
+    code = [ln for ln in text.splitlines() if not ln.strip().startswith("//")]
+    return hashlib.sha1("\n".join(code).encode()).hexdigest()[:12]
+
+
+def traffic_from_profiles(kernel_key: str, src_name: str):
+    """ncu DRAM bytes per launch recorded in profiles/, if the kernel source is unchanged."""
+    digest = kernel_digest(src_name)
     path = os.path.join(ROOT, "profiles", "contract_traffic.txt")
-    if not os.path.exists(path):
+    if digest is None or not os.path.exists(path):
         return None
     for line in open(path):
         f = line.split()
@@ -554,22 +561,35 @@ def run_ours(args):
     x32 = x.to(torch.complex64)
     y32 = torch.empty_like(x32)
     mv = {}
+    route_names = {1: "strided_passes", 2: "fused_fft2", 3: "fused_y"}
     for name, prec, xx, yy, dt, nb in [("fp64_doublefloat", bt.BTTB_MV_FP64, x, y, bt.BTTB_C128, b64),
-                                      ("fp32", bt.BTTB_MV_FP32, x32, y32, bt.BTTB_C64,
-                                       product_bytes(nx, ny, b, mx, my, "fp32")),
+                                      ("fp32", bt.BTTB_MV_FP32, x32, y32, bt.BTTB_C64, b32),
                                       ("fp64_native", bt.BTTB_MV_FP64_NATIVE, x, y, bt.BTTB_C128, b64)]:
-        reps = 30
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                bt.bttb_matvec(plan.handle, xx, yy, 1, n, dt, prec)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                bt.bttb_matvec(plan.handle, xx, yy, 1, n, dt, prec)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / reps
-        mv[name] = {"us": t * 1e3, "gbs": nb / (t / 1e3) / 1e9}
+        entry = {}
+        for route in (0, 1, 2, 3):
+            bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, route)
+            taken = bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_ROUTE_TAKEN, (prec << 8) | 1)
+            if route and taken != route:
+                continue                                    # that form does not apply to this precision
+            reps = 30
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    bt.bttb_matvec(plan.handle, xx, yy, 1, n, dt, prec)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    bt.bttb_matvec(plan.handle, xx, yy, 1, n, dt, prec)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / reps
+            rec = {"us": t * 1e3, "gbs": nb / (t / 1e3) / 1e9, "route": route_names[taken]}
+            if route == 0:
+                entry.update(rec)
+            else:
+                entry.setdefault("by_route", {})[route_names[route]] = rec
+        mv[name] = entry
+    bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, 0)
+    ir_route = route_names[bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_ROUTE_TAKEN, (bt.BTTB_MV_FP32 << 8) | 1)]
 
     # per-kernel breakdown of one host-driven IR solve (CUDA events around every launch)
     bt.bttb_profile(plan.handle, True)
@@ -700,14 +720,14 @@ def run_ours(args):
             return time.perf_counter() - t0
 
         st = sequential(bt.BTTB_MV_FP64)
-        st32 = sequential(bt.BTTB_MV_FP32)
+        seq_ir = sequential(bt.BTTB_MV_FP32)
         its = [r.iters for r in resu]
         uneven = {"arrays": len(specs), "columns": len(resu), "solve_ms": ut * 1e3,
                   "status_ok": sum(r.status == bt.BTTB_OK for r in resu), "iters_max": max(its),
                   "iters_mean": float(np.mean(its)), "relres_true_max": max(r.relres_true for r in resu),
                   "oracle_relres_sampled_arrays": samp, "oracle_relres_max_sampled": max(uneven_oracle),
                   "sequential_fp64_ms": st * 1e3, "speedup_vs_sequential_fp64": st / ut,
-                  "sequential_ir_ms": st32 * 1e3, "speedup_vs_sequential_ir": st32 / ut,
+                  "sequential_ir_ms": seq_ir * 1e3, "speedup_vs_sequential_ir": seq_ir / ut,
                   "fft_chunk_widths": {str(w): widths.count(w) for w in sorted(set(widths))},
                   "unknowns_total": int(sum(s.nx * s.ny * s.b * s.nrhs for s in specs))}
         del vs
@@ -722,10 +742,24 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     ach32 = st32.bytes / (st32.ms / 1e3) / 1e9 if st32.ms > 0 else 0.0
     ach64 = st64.bytes / (st64.ms / 1e3) / 1e9 if st64.ms > 0 else 0.0
-    traffic = traffic_from_profiles("contract_f32_30x30_b60")
-    roofline = {"kernel": "contract_kernel<F32> (binary32 block product, 3600 bins x 60x60)",
+    if ir_route == "fused_y":
+        kname = ("ycontract_kernel<F32,1> (level-2 FFT + binary32 block product of 3600 bins x 60x60 + inverse "
+                 "level-2 FFT, one cluster kernel)")
+        traffic = traffic_from_profiles("ycontract_f32_30x30_b60", "ycontract.cu")
+    else:
+        kname = "contract_kernel<F32> (binary32 block product, 3600 bins x 60x60)"
+        traffic = traffic_from_profiles("contract_f32_30x30_b60", "contract.cu")
+    roofline = {"kernel": kname, "product_route": ir_route,
                 "bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s",
                 "frac": ach32 / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                "whole_product": {
+                    "note": "one whole FFT product (x in, spectrum planes once, y out: 209.1 MB double-float, "
+                            "104.5 MB binary32) / its CUDA-event time, 30 back-to-back products",
+                    "fp64_doublefloat": {"achieved": mv["fp64_doublefloat"]["gbs"],
+                                         "frac": mv["fp64_doublefloat"]["gbs"] / peak,
+                                         "us": mv["fp64_doublefloat"]["us"], "route": mv["fp64_doublefloat"]["route"]},
+                    "fp32": {"achieved": mv["fp32"]["gbs"], "frac": mv["fp32"]["gbs"] / peak,
+                             "us": mv["fp32"]["us"], "route": mv["fp32"]["route"]}},
                 "traffic": traffic, "algorithmic_bytes_per_launch": st32.bytes / max(st32.launches, 1),
                 "avg_launch_us": st32.ms * 1e3 / max(st32.launches, 1), "launches": st32.launches,
                 "share_of_step": st32.ms / ms_prof if ms_prof > 0 else None,

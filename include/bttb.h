@@ -365,6 +365,18 @@ int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out);
  *   BTTB_DEBUG_WAIT_LIMIT_NS (value in ns, 0 = the default of 2 s, at most
  *     60 s): bound of every pipeline wait in this plan's kernels.  Frees the
  *     plan's GMRES workspace (its captured cycles hold the old bound).
+ *   BTTB_DEBUG_PRODUCT_ROUTE (value 0..3): the form of products of one to
+ *     four columns, for comparisons; every form gives the product to the
+ *     precision's tolerance.  0: automatic (the default); 1: four strided FFT
+ *     passes around the block product; 2: the two-level FFT in one cluster
+ *     kernel each way around the block product; 3: the level-1 passes around
+ *     one cluster kernel that runs the level-2 transforms and the block
+ *     product (double-float and binary32 only).  A form that does not fit the
+ *     plan falls back to the automatic choice.  Frees the GMRES workspace.
+ *   BTTB_DEBUG_ROUTE_TAKEN (value = (prec << 8) | nrhs): returns the form
+ *     (1..3 as above) that a product of nrhs columns in precision prec takes
+ *     on this plan; products of more than four columns take the strided
+ *     passes (1).  Changes nothing.
  *   BTTB_DEBUG_WITHHOLD_ARRIVAL (value = a count, at most 1000): the next
  *     `value` launches of the block product for one to eight columns outside
  *     CUDA graph capture withhold the first arrival of one warp, so that
@@ -372,9 +384,11 @@ int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out);
  *     the plan's device error word to TIMEOUT (reported by the next
  *     synchronising call that reads it, e.g. bttb_gmres_solve, as
  *     BTTB_ERR_TIMEOUT) and leaves the product unfinished.
- * Returns BTTB_ERR_INVALID_ARG for an unknown hook or a value out of range.
+ * Returns BTTB_OK (or the route for BTTB_DEBUG_ROUTE_TAKEN), and
+ * BTTB_ERR_INVALID_ARG for an unknown hook or a value out of range.
  */
-enum { BTTB_DEBUG_WAIT_LIMIT_NS = 1, BTTB_DEBUG_WITHHOLD_ARRIVAL = 2 };
+enum { BTTB_DEBUG_WAIT_LIMIT_NS = 1, BTTB_DEBUG_WITHHOLD_ARRIVAL = 2, BTTB_DEBUG_PRODUCT_ROUTE = 3,
+       BTTB_DEBUG_ROUTE_TAKEN = 4 };
 int bttb_plan_debug(bttb_plan plan, int what, long long value);
 
 /* Bytes of device memory the plan holds (spectrum copies and workspace). */

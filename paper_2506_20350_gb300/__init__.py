@@ -27,7 +27,7 @@ BTTB_ERR_INVALID_ARG, BTTB_ERR_CUDA, BTTB_ERR_OOM = -1, -2, -3
 BTTB_ERR_NO_GENERATORS, BTTB_ERR_TIMEOUT, BTTB_ERR_NONFINITE, BTTB_ERR_SINGULAR = -4, -5, -6, -7
 
 BTTB_K_BLOCK_PRODUCT, BTTB_K_FFT, BTTB_K_ALL, BTTB_K_BLOCK_PRODUCT_PREC = 0, 1, 2, 16
-BTTB_DEBUG_WAIT_LIMIT_NS, BTTB_DEBUG_WITHHOLD_ARRIVAL = 1, 2
+BTTB_DEBUG_WAIT_LIMIT_NS, BTTB_DEBUG_WITHHOLD_ARRIVAL, BTTB_DEBUG_PRODUCT_ROUTE, BTTB_DEBUG_ROUTE_TAKEN = 1, 2, 3, 4
 
 EXPORTS = ("bttb_plan_create", "bttb_plan_grid", "bttb_set_generators", "bttb_matvec",
            "bttb_gmres_solve", "bttb_block_jacobi_apply", "bttb_get_spectrum_bin",
@@ -298,9 +298,9 @@ def bttb_plan_autotune(plan, nrhs: int = 1, reps: int = 5) -> int:
     return out.value
 
 
-def bttb_plan_debug(plan, what: int, value: int) -> None:
-    """Failure-path test hooks (BTTB_DEBUG_WAIT_LIMIT_NS, BTTB_DEBUG_WITHHOLD_ARRIVAL)."""
-    _check(load_library().bttb_plan_debug(plan, what, value), plan)
+def bttb_plan_debug(plan, what: int, value: int) -> int:
+    """Test hooks: BTTB_DEBUG_WAIT_LIMIT_NS, _WITHHOLD_ARRIVAL, _PRODUCT_ROUTE, _ROUTE_TAKEN (returns the route)."""
+    return _check(load_library().bttb_plan_debug(plan, what, value), plan, soft_ok=True)
 
 
 def bttb_plan_workspace_bytes(plan) -> int:

@@ -358,6 +358,17 @@ int bttb_plan_debug(bttb_plan plan, int what, long long value) {
             p.wait_ns = value == 0 ? 2000000000ull : (unsigned long long)value;
             gmres_free(&p);                           // captured cycles hold the old limit
             return BTTB_OK;
+        case BTTB_DEBUG_PRODUCT_ROUTE:
+            if (value < 0 || value > 3) return set_error(&p, BTTB_ERR_INVALID_ARG, "route must be in [0, 3]");
+            p.route = (int)value;
+            gmres_free(&p);                           // captured cycles hold the old route
+            return BTTB_OK;
+        case BTTB_DEBUG_ROUTE_TAKEN: {
+            const int prec = (int)(value >> 8), k = (int)(value & 255);
+            if (prec < 0 || prec > BTTB_MV_TC_3XTF32 || k < 1 || k > p.max_rhs)
+                return set_error(&p, BTTB_ERR_INVALID_ARG, "value must be (prec << 8) | nrhs, 1 <= nrhs <= max_rhs");
+            return product_route(&p, k, prec);
+        }
         case BTTB_DEBUG_WITHHOLD_ARRIVAL:
             if (value < 0 || value > 1000) return set_error(&p, BTTB_ERR_INVALID_ARG, "count must be in [0, 1000]");
             p.withhold = (int)value;

@@ -61,6 +61,19 @@ inline int fft_prec_of(int prec) { return prec == PREC_TC ? PREC_F32 : prec; }
 struct GmresWork;
 struct Learned;
 
+// Launch shape of the fused y-level transform + block product (ycontract.cu) for one precision and column
+// count: cluster size, shares, ring, shared-memory offsets.  ok < 0: not decided yet, 0: does not fit.
+struct YcShape {
+    int ok = -1;
+    int Q = 0, pshare = 0, kshare = 0, RH = 0, G = 0, Qc = 0, nchunks = 0, nstages = 0;
+    unsigned stage_bytes = 0, off_g1 = 0, off_tw = 0, off_f0 = 0, off_f1 = 0, off_uh = 0, off_red = 0,
+             off_ring = 0;
+    size_t smem = 0;
+};
+
+// Forms of a product of one to four columns (bttb_plan_debug BTTB_DEBUG_PRODUCT_ROUTE).
+enum ProductRoute { ROUTE_AUTO = 0, ROUTE_PASSES = 1, ROUTE_FUSED_FFT2 = 2, ROUTE_FUSED_Y = 3 };
+
 struct Plan {
     int nx = 0, ny = 0, b = 0, mx = 0, my = 0, max_rhs = 0;
     long n = 0;                   // nx*ny*b
@@ -94,6 +107,8 @@ struct Plan {
     // coming uncaptured one-to-eight-column block products that withhold one mbarrier arrival.
     unsigned long long wait_ns = 2000000000ull;
     int withhold = 0;
+    int route = ROUTE_AUTO;       // form of the few-column product
+    YcShape yc[2][4];             // fused y-level product shapes: [binary32, double-float][columns - 1]
 
     GmresWork *gw = nullptr;
     Learned *learned = nullptr;   // attached learned preconditioner (learned.cu), not owned
@@ -161,11 +176,18 @@ int smallest_5smooth(int n);
 // contract.cu
 int contract_launch(Plan *p, int prec, const void *u, void *v, int k, const int *active = nullptr);
 
+// ycontract.cu: whether the fused y-level transform + block product takes k columns in this precision
+// (decided once per plan), and its launch on the x pass's output U ([c][iy][kx][p]) into V (same layout).
+bool ycontract_fits(Plan *p, int prec, int k);
+int ycontract_launch(Plan *p, int prec, const void *U, void *V, int k, const int *active);
+
 // matvec.cu
 // y[:, c] = Z x[:, c]; xfmt/yfmt are VecFmt values; in_sel/in_scale as in FftPass.
 int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int nrhs, int prec,
                const int *in_sel = nullptr, long in_sel_stride = 0, const double *in_scale = nullptr,
                const int *active = nullptr);
+// ProductRoute a product of nrhs columns in precision prec takes.
+int product_route(Plan *p, int nrhs, int prec);
 int block_jacobi_run(Plan *p, const void *x, int xfmt, long ldx, void *z, int zfmt, long ldz, int nrhs,
                      const int *in_sel = nullptr, long in_sel_stride = 0, const int *active = nullptr);
 int block_jacobi_setup(Plan *p, const double2 *t00_host);

@@ -27,6 +27,28 @@ static int native_of(int prec) {
     return prec == PREC_F64N ? FMT_C128 : ((prec == PREC_F32 || prec == PREC_TC) ? FMT_C64 : FMT_CDF);
 }
 
+// Few columns.  ROUTE_FUSED_Y: the x pass, then the y-level transforms and the block product in one
+// cluster kernel (ycontract.cu: the transformed vectors never leave the chip), then the inverse x pass.
+// ROUTE_FUSED_FFT2: both FFT levels in one cluster kernel each way around the block product (no U / V
+// round trip).  ROUTE_PASSES: four strided passes around the block product (also every product of more
+// than kFusedFftMaxCols columns).  The automatic choice takes the fused y-level form where its shares fit
+// on chip with every cluster resident; otherwise the fused two-level FFT for the double-float and binary64
+// products and for plans that run beside other arrays' kernels in a batch, and the four passes for a lone
+// binary32 product (they overlap better with their neighbours under programmatic dependent launch).
+int product_route(Plan *p, int nrhs, int prec) {
+    const bool few = nrhs <= kFusedFftMaxCols;
+    const int fprec = fft_prec_of(prec);
+    const int yprec = prec == PREC_TC ? PREC_F32 : prec;        // below kTcMinCols the TC form is binary32
+    const bool y_ok = few && (yprec == PREC_DF64 || yprec == PREC_F32) && ycontract_fits(p, yprec, nrhs);
+    const bool f2_ok = few && fft2_fused_smem(p, fprec) <= p->smem_optin / 2;
+    int route = p->route;
+    if (route == ROUTE_FUSED_Y && !y_ok) route = ROUTE_AUTO;
+    if (route == ROUTE_FUSED_FFT2 && !f2_ok) route = ROUTE_AUTO;
+    if (route == ROUTE_AUTO)
+        route = y_ok ? ROUTE_FUSED_Y : ((f2_ok && (fprec != PREC_F32 || p->in_batch)) ? ROUTE_FUSED_FFT2 : ROUTE_PASSES);
+    return route;
+}
+
 int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int nrhs, int prec,
                const int *in_sel, long in_sel_stride, const double *in_scale, const int *active) {
     const int nx = p->nx, ny = p->ny, b = p->b, mx = p->mx, my = p->my;
@@ -34,13 +56,10 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     const int fprec = fft_prec_of(prec);
     const long plane = (long)ny * mx * b;
     int rc;
+    const int route = product_route(p, nrhs, prec);
+    const int yprec = prec == PREC_TC ? PREC_F32 : prec;
 
-    // few columns: both FFT levels in one kernel each way (no U / V round trip, two launches fewer).  Timed
-    // on GB300 it wins for the double-float and binary64 products and for plans that run beside other
-    // arrays' kernels in a batch; a lone binary32 product keeps the four passes, which overlap better with
-    // their neighbours under programmatic dependent launch.
-    if (nrhs <= kFusedFftMaxCols && (fprec != PREC_F32 || p->in_batch) &&
-        fft2_fused_smem(p, fprec) <= p->smem_optin / 2) {
+    if (route == ROUTE_FUSED_FFT2) {
         if ((rc = fft2_fused_launch(p, x, p->wsA, ldx, nrhs, fprec, xfmt, false, in_sel, in_sel_stride, in_scale,
                                     active)) != BTTB_OK)
             return rc;
@@ -56,6 +75,17 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     a.O = ny; a.pdim = b; a.ncols = nrhs;
     a.nin = nx; a.nout = mx; a.M = mx;
     if ((rc = fft_pass_launch(p, a, fprec, xfmt, NF, false)) != BTTB_OK) return rc;
+
+    FftPass e{};
+    e.in = p->wsA; e.out = y;
+    e.in_cs = plane; e.in_os = (long)mx * b; e.in_ns = b;
+    e.out_cs = ldy; e.out_os = (long)nx * b; e.out_ns = b;
+    e.O = ny; e.pdim = b; e.ncols = nrhs; e.active = active;
+    e.nin = mx; e.nout = nx; e.M = mx;
+    if (route == ROUTE_FUSED_Y) {
+        if ((rc = ycontract_launch(p, yprec, p->wsB, p->wsA, nrhs, active)) != BTTB_OK) return rc;
+        return fft_pass_launch(p, e, fprec, NF, yfmt, true);
+    }
 
     FftPass c{};
     c.in = p->wsB; c.out = p->wsA;
@@ -74,13 +104,6 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     d.O = mx; d.pdim = b; d.ncols = nrhs; d.active = active;
     d.nin = my; d.nout = ny; d.M = my;
     if ((rc = fft_pass_launch(p, d, fprec, NF, NF, true)) != BTTB_OK) return rc;
-
-    FftPass e{};
-    e.in = p->wsA; e.out = y;
-    e.in_cs = plane; e.in_os = (long)mx * b; e.in_ns = b;
-    e.out_cs = ldy; e.out_os = (long)nx * b; e.out_ns = b;
-    e.O = ny; e.pdim = b; e.ncols = nrhs; e.active = active;
-    e.nin = mx; e.nout = nx; e.M = mx;
     return fft_pass_launch(p, e, fprec, NF, yfmt, true);
 }
 

@@ -1,0 +1,484 @@
+// The middle of the product y = Z x (Sec. II-C, III-A) in one kernel for one to four columns: the
+// level-2 (y) DFT of the padded vector, the per-bin block product v_k = G_k u_k of Eq. (multL) and the
+// inverse level-2 DFT with the crop to ny rows.  The level-1 (x) transforms before and after it are the
+// strided passes of fft.cu; together they are the 2-level blockwise FFT of App. B.
+//
+// The y transform of one column kx of the cell grid needs every row of that column, and the block
+// product of a bin needs every basis index, so a thread-block cluster of Q CTAs takes one column kx.
+// CTA r of the cluster owns the bases P_r (a share of the b) and the bins K_r (a share of the my values of
+// ky), and
+//   1. loads U[c][iy][kx][p] for p in P_r, iy < ny (the x pass's output), leaves rows iy >= ny zero
+//      (Eq. (xc2)) and transforms along iy: Stockham stages in shared memory;
+//   2. sends bin ky of its bases to the CTA that owns ky, through distributed shared memory;
+//   3. forms v_k = G_k u_k for its bins.  The spectrum blocks (column-major, the binary32 planes the
+//      precision reads) stream through a ring of shared-memory stages: one producer warp issues
+//      cp.async.bulk copies, an mbarrier per stage counts the bytes in and another counts the consumer
+//      warps out.  The spectrum does not depend on the preceding pass, so the first stages are issued
+//      before the programmatic-dependent-launch wait and land while the x pass drains and step 1-2 run.
+//      The eight consumer warps split a block's rows into 32-row blocks (one row per lane) and its
+//      columns q into groups; one reduction over the groups, in group order, ends each bin;
+//   4. sends v_k of each basis back to the CTA that owns the basis;
+//   5. transforms along ky (inverse, unnormalised: the 1/(mx my) is in the spectrum), keeps iy < ny and
+//      stores V[c][iy][kx][p] for the inverse x pass.
+// Every wait is bounded; a wait that runs out sets the plan's error word, the CTA stops computing but
+// keeps taking part in the cluster barriers, and the producer drains its copies in flight before exit.
+#include <algorithm>
+
+#include <cooperative_groups.h>
+
+#include "arith.cuh"
+#include "blockprod.cuh"
+#include "fftcore.cuh"
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace bttb {
+
+constexpr int kYcConsumerWarps = 8;
+constexpr int kYcThreads = (kYcConsumerWarps + 1) * 32;     // eight consumer warps + the producer warp
+constexpr int kYcMaxStages = 8;
+
+struct YcArgs {
+    const void *U;                // x-pass output [c][iy][kx][p] (native format)
+    void *V;                      // output, same layout, for the inverse x pass
+    long plane;                   // column stride of U and V: ny*mx*b
+    const void *g0, *g1;          // spectrum planes (g1: double-float low plane)
+    long gbs;                     // bin stride of a plane
+    const int *active;            // per-column flags of this group (may be null)
+    int nx, ny, mx, my, b, kc;    // kc: columns of this launch
+    int Q, pshare, kshare;        // cluster size, bases and bins per CTA (the last CTA may hold fewer)
+    int RH, G;                    // 32-row blocks of a spectrum block, column groups (RH * G <= 8 warps)
+    int Qc, nchunks, nstages;     // spectrum columns per stage, stages per bin, ring depth
+    uint32_t stage_bytes, off_g1; // bytes of one stage; offset of its low-plane part
+    uint32_t off_tw, off_f0, off_f1, off_uh, off_red, off_ring;
+    Fft2Side sy;
+    const void *twy;
+    int *err;
+    unsigned long long wait_ns;
+    int withhold;                 // test hook: CTA 0 withholds the arrival of its first stage
+};
+
+__host__ __device__ constexpr uint32_t yc_align(uint32_t x) { return (x + 127u) & ~127u; }
+
+template <class A, int KC>
+__global__ void __launch_bounds__(kYcThreads) ycontract_kernel(const YcArgs a) {
+    namespace cg = cooperative_groups;
+    using C = typename A::C;
+    using GT = typename GElem<A>::T;
+    constexpr int NPL = GElem<A>::planes;
+    extern __shared__ __align__(128) unsigned char smem[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = (int)cl.block_rank();
+    const int kx = blockIdx.x / a.Q;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = warp == kYcConsumerWarps;
+    const int b = a.b, my = a.my, kc = a.kc, S = a.nstages;
+
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + kYcMaxStages;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 16 * kYcMaxStages);
+    C *tw = reinterpret_cast<C *>(smem + a.off_tw);
+    C *F0 = reinterpret_cast<C *>(smem + a.off_f0);
+    C *F1 = reinterpret_cast<C *>(smem + a.off_f1);
+    C *Uh = reinterpret_cast<C *>(smem + a.off_uh);          // [kl][c][p]: u^ of my bins, then v^
+    Acc<A> *red = reinterpret_cast<Acc<A> *>(smem + a.off_red);
+    unsigned char *ring = smem + a.off_ring;
+
+    // shares: bases [plo, plo+np), bins [klo, klo+nk) of rank r (and of any rank o)
+    auto p_lo = [&](int o) { return min(b, o * a.pshare); };
+    auto p_n = [&](int o) { return min(b, (o + 1) * a.pshare) - p_lo(o); };
+    auto k_lo = [&](int o) { return min(my, o * a.kshare); };
+    auto k_n = [&](int o) { return min(my, (o + 1) * a.kshare) - k_lo(o); };
+    const int plo = p_lo(r), np = p_n(r), klo = k_lo(r), nk = k_n(r);
+    const int nseq = kc * np;                                 // sequences of this CTA's y transforms
+    const int items = nk * a.nchunks;                         // spectrum stages of this CTA
+
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kYcConsumerWarps);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const uint64_t pol_stream = l2_policy_evict_first();
+    const bool withheld0 = a.withhold && blockIdx.x == 0;
+    auto issue = [&](int it) {
+        const int s = it % S;
+        const int kl = it / a.nchunks, ch = it % a.nchunks;
+        const int q0 = ch * a.Qc, qn = min(a.Qc, b - q0);
+        const uint32_t gbytes = (uint32_t)((qn * b * (int)sizeof(GT) + 15) & ~15);
+        const long bin = (long)(klo + kl) * a.mx + kx;
+        const long goff = bin * a.gbs + (long)q0 * b;
+        unsigned char *st = ring + (size_t)s * a.stage_bytes;
+        if (withheld0 && it == 0) mbar_expect_tx(&full[s], gbytes * NPL);
+        else mbar_arrive_expect_tx(&full[s], gbytes * NPL);
+        bulk_g2s(st, reinterpret_cast<const GT *>(a.g0) + goff, gbytes, &full[s], pol_stream);
+        if (NPL == 2) bulk_g2s(st + a.off_g1, reinterpret_cast<const GT *>(a.g1) + goff, gbytes, &full[s], pol_stream);
+    };
+    // the spectrum does not depend on the x pass: fill the ring before the dependency wait
+    int issued = 0;
+    if (producer && lane == 0)
+        for (; issued < min(S, items); ++issued) issue(issued);
+    __syncwarp();
+    for (int i = threadIdx.x; i < my + 5; i += blockDim.x) tw[i] = reinterpret_cast<const C *>(a.twy)[i];
+    // every CTA of the cluster must have started before another writes into its shared memory: arrive
+    // now, wait before the first exchange
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+    pdl_wait();
+
+    bool any = true;
+    if (a.active) {                                          // uniform over the cluster (same columns)
+        any = false;
+        for (int c = 0; c < kc; ++c) any |= a.active[c] != 0;
+    }
+    bool failed = false;
+    if (any) {
+        // ---- 1. load this CTA's bases of column kx and transform along iy
+        const long ucol = (long)kx * b + plo;
+        for (int idx = threadIdx.x; idx < my * nseq; idx += blockDim.x) {
+            const int iy = idx / nseq, t = idx - iy * nseq;
+            const int c = t / np, pl = t - c * np;
+            C v = A::zero();
+            if (iy < a.ny) v = load_vec<A, native_fmt<A>>(a.U, (long)c * a.plane + (long)iy * a.mx * b + ucol + pl);
+            F0[idx] = v;
+        }
+        __syncthreads();
+        const C *R1 = fft2_level<A, false>(F0, F1, tw, a.sy, nseq, nseq, 1);
+        // ---- 2. bin ky of my bases to the CTA that owns ky
+        asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+        for (int idx = threadIdx.x; idx < my * nseq; idx += blockDim.x) {
+            const int ky = idx / nseq, t = idx - ky * nseq;
+            const int c = t / np, pl = t - c * np;
+            const int o = ky / a.kshare;
+            C *dst = cl.map_shared_rank(Uh, o);
+            dst[(long)(ky - k_lo(o)) * kc * b + c * b + plo + pl] = R1[idx];
+        }
+        cl.sync();
+
+        // ---- 3. block products of my bins
+        if (producer) {
+            if (lane == 0) {
+                for (; issued < items; ++issued) {
+                    const int s = issued % S;
+                    // the stage is free once every consumer warp released its previous item
+                    if (*abort_flag ||
+                        !mbar_wait_bounded(&empty[s], (uint32_t)((issued / S) - 1) & 1u, abort_flag, a.wait_ns))
+                        break;
+                    issue(issued);
+                }
+            }
+            __syncwarp();
+        } else {
+            const int rb = warp % a.RH, g = warp / a.RH;
+            const bool live = warp < a.RH * a.G;
+            const int prow = rb * 32 + lane;
+            const bool rowok = live && prow < b;
+            Acc<A> acc[KC];
+            int buf = 0;
+            for (int it = 0; it < items; ++it) {
+                const int s = it % S;
+                const int kl = it / a.nchunks, ch = it % a.nchunks;
+                if (!failed) {
+                    const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(it / S) & 1u, abort_flag, a.wait_ns);
+                    failed = __any_sync(0xffffffffu, !ok);
+                }
+                if (ch == 0) {
+#pragma unroll
+                    for (int c = 0; c < KC; ++c) acc[c].zero();
+                }
+                if (!failed) {
+                    if (rowok) {
+                        const int q0 = ch * a.Qc, qn = min(a.Qc, b - q0);
+                        const unsigned char *st = ring + (size_t)s * a.stage_bytes;
+                        const GT *gs0 = reinterpret_cast<const GT *>(st) + prow;
+                        const GT *gs1 = reinterpret_cast<const GT *>(st + a.off_g1) + prow;
+                        const C *us = Uh + (long)kl * kc * b + q0;
+                        for (int q = g; q < qn; q += a.G) {
+                            const GT gh = gs0[q * b];
+                            const GT gl = NPL == 2 ? gs1[q * b] : gh;
+#pragma unroll
+                            for (int c = 0; c < KC; ++c)
+                                if (c < kc) acc[c].mac(gh, gl, us[c * b + q]);
+                        }
+                    }
+                    // every lane has read stage s: release it to the producer
+                    __syncwarp();
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                }
+                if (ch == a.nchunks - 1) {
+                    // partial sums of the column groups, then their sum in group order: v_k of bin kl
+                    Acc<A> *rb_ = red + (long)buf * a.G * (a.RH * 32) * KC;
+                    if (rowok)
+#pragma unroll
+                        for (int c = 0; c < KC; ++c) rb_[((long)g * a.RH * 32 + prow) * KC + c] = acc[c];
+                    named_barrier_sync(1, kYcConsumerWarps * 32);
+                    for (int t = threadIdx.x; t < kc * b; t += kYcConsumerWarps * 32) {
+                        const int c = t / b, pr = t - c * b;
+                        Acc<A> sum = rb_[(long)pr * KC + c];
+                        for (int gg = 1; gg < a.G; ++gg) sum.merge(rb_[((long)gg * a.RH * 32 + pr) * KC + c]);
+                        Uh[(long)kl * kc * b + c * b + pr] = sum.result();   // u^ of bin kl is consumed
+                    }
+                    buf ^= 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (failed && lane == 0 && !producer) atomicOr(a.err, DEVERR_TIMEOUT);
+        // ---- 4. v_k of each basis to the CTA that owns the basis (its y buffers are free since step 2)
+        for (int idx = threadIdx.x; idx < nk * kc * b; idx += blockDim.x) {
+            const int kl = idx / (kc * b), rem = idx - kl * kc * b;
+            const int c = rem / b, pr = rem - c * b;
+            const int o = pr / a.pshare;
+            const int npo = p_n(o);
+            C *dst = cl.map_shared_rank(F0, o);
+            dst[(long)(klo + kl) * (kc * npo) + c * npo + (pr - p_lo(o))] = Uh[idx];
+        }
+        cl.sync();
+        // ---- 5. inverse transform along ky, crop to ny rows
+        const C *R2 = fft2_level<A, true>(F0, F1, tw, a.sy, nseq, nseq, 1);
+        pdl_trigger();
+        for (int idx = threadIdx.x; idx < a.ny * nseq; idx += blockDim.x) {
+            const int iy = idx / nseq, t = idx - iy * nseq;
+            const int c = t / np, pl = t - c * np;
+            store_vec<A, native_fmt<A>>(a.V, (long)c * a.plane + (long)iy * a.mx * b + ucol + pl, R2[idx]);
+        }
+    } else {
+        pdl_trigger();
+    }
+    // copies that may still be in flight (a run-out wait, or no active column): the last min(S, issued)
+    // items, each in its own stage; a withheld arrival is supplied first
+    if (producer && lane == 0) {
+        if (*abort_flag || !any) {
+            for (int d = max(0, issued - S); d < issued; ++d) {
+                if (withheld0 && d == 0) mbar_arrive(&full[d % S]);
+                if (!mbar_wait_drain(&full[d % S], (uint32_t)(d / S) & 1u)) atomicOr(a.err, DEVERR_TIMEOUT);
+            }
+        }
+        if (*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+template <class A, int KC>
+static bool yc_layout(const Plan *p, int kc, int Q, YcShape &y) {
+    using C = typename A::C;
+    using GT = typename GElem<A>::T;
+    constexpr int NPL = GElem<A>::planes;
+    const int b = p->b, my = p->my;
+    y.Q = Q;
+    y.pshare = (b + Q - 1) / Q;
+    y.kshare = (my + Q - 1) / Q;
+    y.RH = (b + 31) / 32;
+    if (y.RH > kYcConsumerWarps) return false;
+    y.G = kYcConsumerWarps / y.RH;
+    const uint32_t ce = sizeof(C);
+    uint32_t off = 256;
+    y.off_tw = off;
+    off = yc_align(off + (uint32_t)(my + 8) * ce);
+    const uint32_t fbytes = (uint32_t)my * kc * y.pshare * ce;
+    y.off_f0 = off;
+    off = yc_align(off + fbytes);
+    y.off_f1 = off;
+    off = yc_align(off + fbytes);
+    y.off_uh = off;
+    off = yc_align(off + (uint32_t)y.kshare * kc * b * ce);
+    y.off_red = off;
+    off = yc_align(off + 2u * y.G * (y.RH * 32) * KC * (uint32_t)sizeof(Acc<A>));
+    y.off_ring = off;
+    // ring: spectrum chunks of Qc columns, balanced over the block, about 16 KB a stage, 3..8 stages in
+    // what is left of a budget that lets two CTAs share an SM when the shares are small
+    const size_t optin = p->smem_optin > 0 ? (size_t)p->smem_optin : 227 * 1024;
+    const size_t budget2 = (optin + 1024) / 2 - 1024;            // two CTAs (1 KB reserved each) per SM
+    const size_t budget1 = optin;
+    const size_t colb = (size_t)b * sizeof(GT) * NPL;              // one spectrum column, all planes
+    for (size_t budget : {budget2, budget1}) {
+        if (off + 3 * (colb + 256) > budget) continue;
+        const size_t ring_max = budget - off;
+        // balanced chunks of at most qc columns; with b odd a chunk that is not the whole block holds an
+        // even number of columns, so that every chunk starts on a 16-byte boundary
+        int qc = (int)std::min<size_t>((size_t)b, std::max<size_t>(1, (16 * 1024) / colb));
+        int nch = 0, ns = 0;
+        for (; qc >= 1; --qc) {
+            nch = (b + qc - 1) / qc;
+            int q2 = (b + nch - 1) / nch;
+            if (b % 2 && q2 < b && q2 % 2) --q2;
+            if (q2 < 1) continue;
+            nch = (b + q2 - 1) / q2;
+            ns = (int)std::min<size_t>(kYcMaxStages, ring_max / (yc_align((uint32_t)(q2 * b * sizeof(GT))) * NPL));
+            if (ns >= 3) {
+                qc = q2;
+                break;
+            }
+        }
+        if (qc < 1 || ns < 3) continue;
+        y.Qc = qc;
+        y.nchunks = nch;
+        const uint32_t pb = yc_align((uint32_t)(qc * b * sizeof(GT)));
+        y.off_g1 = pb;
+        y.stage_bytes = pb * NPL;
+        y.nstages = (int)std::min<size_t>(kYcMaxStages, ring_max / y.stage_bytes);
+        y.smem = off + (size_t)y.nstages * y.stage_bytes;
+        return true;
+    }
+    return false;
+}
+
+template <class A, int KC>
+static cudaError_t yc_config(const Plan *p, const YcShape &y, cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr,
+                             int ncols_groups) {
+    cfg = {};
+    cfg.gridDim = dim3(p->mx * y.Q, 1, 1);
+    cfg.blockDim = dim3(kYcThreads);
+    cfg.dynamicSmemBytes = y.smem;
+    cfg.stream = p->stream;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = y.Q;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    (void)ncols_groups;
+    return cudaFuncSetAttribute(ycontract_kernel<A, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)p->smem_optin);
+}
+
+// Largest cluster size whose mx clusters are all resident at once (the occupancy API decides), so that
+// every CTA streams its share of the spectrum from the start; false if none fits.
+template <class A, int KC>
+static bool yc_choose(Plan *p, int kc, YcShape &out) {
+    const int qmax = std::min(8, std::min(p->b, p->my));
+    for (int Q = qmax; Q >= 1; --Q) {
+        YcShape y;
+        if (!yc_layout<A, KC>(p, kc, Q, y)) continue;
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute attr[2];
+        if (yc_config<A, KC>(p, y, cfg, attr, 1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int nclus = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclus, ycontract_kernel<A, KC>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (nclus >= p->mx) {
+            out = y;
+            return true;
+        }
+    }
+    return false;
+}
+
+template <class A, int KC>
+static int yc_launch(Plan *p, const void *U, void *V, int kc, const int *active, const YcShape &y) {
+    using GT = typename GElem<A>::T;
+    constexpr int NPL = GElem<A>::planes;
+    YcArgs a{};
+    a.U = U;
+    a.V = V;
+    a.plane = (long)p->ny * p->mx * p->b;
+    if constexpr (A::kind == 0) {
+        a.g0 = p->ghat_hi;
+        a.g1 = p->ghat_lo;
+    } else {
+        a.g0 = p->ghat_hi;
+        a.g1 = nullptr;
+    }
+    a.gbs = p->gbs;
+    a.active = active;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.mx = p->mx;
+    a.my = p->my;
+    a.b = p->b;
+    a.kc = kc;
+    a.Q = y.Q;
+    a.pshare = y.pshare;
+    a.kshare = y.kshare;
+    a.RH = y.RH;
+    a.G = y.G;
+    a.Qc = y.Qc;
+    a.nchunks = y.nchunks;
+    a.nstages = y.nstages;
+    a.stage_bytes = y.stage_bytes;
+    a.off_g1 = y.off_g1;
+    a.off_tw = y.off_tw;
+    a.off_f0 = y.off_f0;
+    a.off_f1 = y.off_f1;
+    a.off_uh = y.off_uh;
+    a.off_red = y.off_red;
+    a.off_ring = y.off_ring;
+    const FftPlan &fy = p->fy.M == p->my ? p->fy : p->fx;
+    Fft2Side sd;
+    sd.M = fy.M;
+    sd.nst = fy.nst;
+    {
+        int ns = 1;
+        for (int i = 0; i < fy.nst; ++i) {
+            sd.radix[i] = fy.radix[i];
+            sd.nsmagic[i] = ns == 1 ? 0u : (unsigned)((0x100000000ull + ns - 1) / ns);
+            ns *= fy.radix[i];
+        }
+    }
+    a.sy = sd;
+    a.twy = A::kind == 0 ? (const void *)fy.tw_df : (const void *)fy.tw_f32;
+    a.err = p->d_err;
+    a.wait_ns = p->wait_ns;
+    a.withhold = 0;
+    if (p->withhold > 0) {                                 // test hook, never inside a captured graph
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(p->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            a.withhold = 1;
+            --p->withhold;
+        }
+    }
+    if (!a.g0 || (NPL == 2 && !a.g1) || !a.twy)
+        return set_error(p, BTTB_ERR_INVALID_ARG, "plan does not keep the spectrum copy this precision reads");
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    cudaError_t e = yc_config<A, KC>(p, y, cfg, attr, 1);
+    if (e != cudaSuccess) return check_cuda(p, e, "fused y-level product smem attribute");
+    const int tok = prof_begin(p, BTTB_K_BLOCK_PRODUCT_PREC + (A::kind == 0 ? BTTB_MV_FP64 : BTTB_MV_FP32));
+    e = cudaLaunchKernelEx(&cfg, ycontract_kernel<A, KC>, a);
+    count_launch(p);
+    if (e != cudaSuccess) return check_cuda(p, e, "fused y-level product launch");
+    // algorithmic bytes: the spectrum planes once, U in and V out (the intermediates stay on chip)
+    const double bins = (double)p->mx * p->my;
+    prof_end(p, tok, bins * p->b * p->b * sizeof(GT) * NPL +
+                         2.0 * kc * (double)p->ny * p->mx * p->b * sizeof(typename A::C));
+    return check_cuda(p, cudaGetLastError(), "fused y-level product launch");
+}
+
+template <class A, int KC>
+static YcShape &yc_shape(Plan *p, int k) {
+    YcShape &y = p->yc[A::kind == 0 ? 1 : 0][k - 1];
+    if (y.ok < 0) {
+        YcShape t;
+        t.ok = yc_choose<A, KC>(p, k, t) ? 1 : 0;
+        y = t;
+    }
+    return y;
+}
+
+bool ycontract_fits(Plan *p, int prec, int k) {
+    if (k < 1 || k > 4 || p->b > 256) return false;
+    if (prec == PREC_DF64) return (k == 1 ? yc_shape<DF64, 1>(p, k) : yc_shape<DF64, 4>(p, k)).ok == 1;
+    if (prec == PREC_F32) return (k == 1 ? yc_shape<F32, 1>(p, k) : yc_shape<F32, 4>(p, k)).ok == 1;
+    return false;
+}
+
+int ycontract_launch(Plan *p, int prec, const void *U, void *V, int k, const int *active) {
+    if (!ycontract_fits(p, prec, k)) return set_error(p, BTTB_ERR_INVALID_ARG, "fused y-level product does not fit");
+    if (prec == PREC_DF64)
+        return k == 1 ? yc_launch<DF64, 1>(p, U, V, k, active, p->yc[1][0]) : yc_launch<DF64, 4>(p, U, V, k, active, p->yc[1][k - 1]);
+    return k == 1 ? yc_launch<F32, 1>(p, U, V, k, active, p->yc[0][0]) : yc_launch<F32, 4>(p, U, V, k, active, p->yc[0][k - 1]);
+}
+
+}  // namespace bttb

@@ -133,13 +133,16 @@ def test_happy_breakdown_on_an_eigenvector(bt):
     plan.close()
 
 
-def test_timeout_is_reported_and_the_plan_recovers(bt, tiny):
-    """A block-product launch whose warp withholds an mbarrier arrival: the bounded wait (1 ms here) runs
-    out, the kernel drains its copies and returns, and the solve returns BTTB_ERR_TIMEOUT.  The same plan and
-    a fresh plan then solve normally."""
+@pytest.mark.parametrize("route", [1, 3])
+def test_timeout_is_reported_and_the_plan_recovers(bt, tiny, route):
+    """A block-product launch that withholds an mbarrier arrival (the warp-per-bin kernel of the strided
+    route, and the fused level-2 kernel): the bounded wait (1 ms here) runs out, the kernel drains its
+    copies and returns, and the solve returns BTTB_ERR_TIMEOUT.  The same plan and a fresh plan then solve
+    normally."""
     nx, ny, b, gen, v = tiny
     plan = bt.Plan(nx, ny, b, max_rhs=1)
     plan.set_generators(gen)
+    bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, route)
     bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_WAIT_LIMIT_NS, 1_000_000)
     bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_WITHHOLD_ARRIVAL, 1)
     with pytest.raises(bt.BttbError) as e:

@@ -249,6 +249,33 @@ def test_spectrum_matches_oracle(bt):
     assert np.abs(got - ref[1, 2]).max() <= 1e-13 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("route", [1, 2, 3])
+@pytest.mark.parametrize("nx,ny,b,k", [
+    (5, 4, 12, 1),     # grid 9 x 8: clusters of 8, two bases per CTA
+    (6, 5, 16, 2),     # two columns
+    (7, 3, 33, 3),     # odd b: even chunk widths, ragged last chunk; three columns
+    (4, 6, 60, 4),     # four columns, b = 60
+    (9, 8, 96, 1),     # three 32-row blocks of the spectrum block, two column groups
+    (3, 2, 5, 1),      # b < Q: CTAs without bases
+    (12, 2, 24, 2),    # grid 24 x 3: more bins than CTAs of a column
+])
+def test_product_routes(bt, route, nx, ny, b, k):
+    """The three forms of a one-to-four-column product (four strided passes; the two-level FFT in one
+    cluster kernel each way; the level-1 passes around the fused level-2 transform + block product) give
+    the oracle's product to the precision's tolerance; a form that does not fit falls back."""
+    gen = arrays.random_generator_blocks(nx, ny, b, seed=500 + nx + ny + b + k)
+    plan = bt.Plan(nx, ny, b, max_rhs=k)
+    plan.set_generators(gen)
+    bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, route)
+    x = _rand(np.random.default_rng(9), k, plan.n)
+    ref = oracle.matvec(gen, x.T).T
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64).cpu().numpy(), ref, FP64_TOL, f"df64 route {route}")
+    _check(plan.matvec(_dev(x.astype(np.complex64)), prec=bt.BTTB_MV_FP32).cpu().numpy(),
+           oracle.matvec(gen, x.astype(np.complex64).T).T, FP32_TOL, f"binary32 route {route}")
+    _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP32).cpu().numpy(), ref, FP32_TOL, f"binary32 c128 io {route}")
+    plan.close()
+
+
 # ------------------------------------------------------------------ full size
 
 @pytest.fixture(scope="module")
@@ -269,6 +296,18 @@ def test_full_size_product(bt, precision_case):
     e64n = _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64_NATIVE).cpu().numpy(), ref, FP64_TOL, "binary64 30x30")
     e32 = _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP32).cpu().numpy(), ref, FP32_TOL, "binary32 30x30")
     print(f"30x30 b=60 product error vs oracle: df64 {e64:.2e}, binary64 {e64n:.2e}, binary32 {e32:.2e}")
+
+
+@pytest.mark.parametrize("route", [1, 2, 3])
+def test_full_size_product_routes(bt, precision_case, route):
+    """Every form of the 30x30, b=60 product against the O(N^2) oracle, double-float and binary32."""
+    c, gen, plan, x, ref = precision_case
+    bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, route)
+    try:
+        _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64).cpu().numpy(), ref, FP64_TOL, f"df64 route {route}")
+        _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP32).cpu().numpy(), ref, FP32_TOL, f"binary32 route {route}")
+    finally:
+        bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, 0)
 
 
 def test_full_size_sampled_rows(bt, precision_case):

@@ -377,6 +377,15 @@ int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out);
  *     (1..3 as above) that a product of nrhs columns in precision prec takes
  *     on this plan; products of more than four columns take the strided
  *     passes (1).  Changes nothing.
+ *   BTTB_DEBUG_FUSED_SHAPE (value = (Q << 16) | (prec << 8) | nrhs, prec
+ *     FP64 or FP32, nrhs 1..4): with Q = 0 returns the cluster size (bits
+ *     0-7) and ring depth (bits 8-15) of form 3 for that product, 0 if form 3
+ *     does not fit; with Q in 1..8 returns how many clusters of that size the
+ *     occupancy API lets run at once.  Changes nothing.
+ *   BTTB_DEBUG_FUSED_CLUSTER (value 0..8): cluster size of form 3 (0: the
+ *     largest size whose clusters are all resident at once, the default);
+ *     with a size that does not fit, form 3 does not apply.  Frees the GMRES
+ *     workspace.
  *   BTTB_DEBUG_WITHHOLD_ARRIVAL (value = a count, at most 1000): the next
  *     `value` launches of the block product for one to eight columns outside
  *     CUDA graph capture withhold the first arrival of one warp, so that
@@ -388,7 +397,7 @@ int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out);
  * BTTB_ERR_INVALID_ARG for an unknown hook or a value out of range.
  */
 enum { BTTB_DEBUG_WAIT_LIMIT_NS = 1, BTTB_DEBUG_WITHHOLD_ARRIVAL = 2, BTTB_DEBUG_PRODUCT_ROUTE = 3,
-       BTTB_DEBUG_ROUTE_TAKEN = 4 };
+       BTTB_DEBUG_ROUTE_TAKEN = 4, BTTB_DEBUG_FUSED_SHAPE = 5, BTTB_DEBUG_FUSED_CLUSTER = 6 };
 int bttb_plan_debug(bttb_plan plan, int what, long long value);
 
 /* Bytes of device memory the plan holds (spectrum copies and workspace). */

@@ -28,6 +28,7 @@ BTTB_ERR_NO_GENERATORS, BTTB_ERR_TIMEOUT, BTTB_ERR_NONFINITE, BTTB_ERR_SINGULAR 
 
 BTTB_K_BLOCK_PRODUCT, BTTB_K_FFT, BTTB_K_ALL, BTTB_K_BLOCK_PRODUCT_PREC = 0, 1, 2, 16
 BTTB_DEBUG_WAIT_LIMIT_NS, BTTB_DEBUG_WITHHOLD_ARRIVAL, BTTB_DEBUG_PRODUCT_ROUTE, BTTB_DEBUG_ROUTE_TAKEN = 1, 2, 3, 4
+BTTB_DEBUG_FUSED_SHAPE, BTTB_DEBUG_FUSED_CLUSTER = 5, 6
 
 EXPORTS = ("bttb_plan_create", "bttb_plan_grid", "bttb_set_generators", "bttb_matvec",
            "bttb_gmres_solve", "bttb_block_jacobi_apply", "bttb_get_spectrum_bin",

@@ -369,6 +369,20 @@ int bttb_plan_debug(bttb_plan plan, int what, long long value) {
                 return set_error(&p, BTTB_ERR_INVALID_ARG, "value must be (prec << 8) | nrhs, 1 <= nrhs <= max_rhs");
             return product_route(&p, k, prec);
         }
+        case BTTB_DEBUG_FUSED_SHAPE: {
+            const int prec = (int)((value >> 8) & 255), k = (int)(value & 255), Q = (int)((value >> 16) & 255);
+            if ((prec != BTTB_MV_FP64 && prec != BTTB_MV_FP32) || k < 1 || k > 4 || Q > 8)
+                return set_error(&p, BTTB_ERR_INVALID_ARG, "value must be (Q << 16) | (prec << 8) | nrhs");
+            const int r = ycontract_probe(&p, prec, k, Q);
+            return r < 0 ? set_error(&p, BTTB_ERR_INVALID_ARG, "shape does not fit: " + std::to_string(r)) : r;
+        }
+        case BTTB_DEBUG_FUSED_CLUSTER:
+            if (value < 0 || value > 8) return set_error(&p, BTTB_ERR_INVALID_ARG, "cluster size must be in [0, 8]");
+            p.yc_force_q = (int)value;
+            for (auto &row : p.yc)
+                for (auto &y : row) y = YcShape{};
+            gmres_free(&p);
+            return BTTB_OK;
         case BTTB_DEBUG_WITHHOLD_ARRIVAL:
             if (value < 0 || value > 1000) return set_error(&p, BTTB_ERR_INVALID_ARG, "count must be in [0, 1000]");
             p.withhold = (int)value;

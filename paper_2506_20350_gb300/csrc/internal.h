@@ -109,6 +109,7 @@ struct Plan {
     int withhold = 0;
     int route = ROUTE_AUTO;       // form of the few-column product
     YcShape yc[2][4];             // fused y-level product shapes: [binary32, double-float][columns - 1]
+    int yc_force_q = 0;           // cluster size of the fused y-level product (0: the largest resident one)
 
     GmresWork *gw = nullptr;
     Learned *learned = nullptr;   // attached learned preconditioner (learned.cu), not owned
@@ -180,6 +181,7 @@ int contract_launch(Plan *p, int prec, const void *u, void *v, int k, const int 
 // (decided once per plan), and its launch on the x pass's output U ([c][iy][kx][p]) into V (same layout).
 bool ycontract_fits(Plan *p, int prec, int k);
 int ycontract_launch(Plan *p, int prec, const void *U, void *V, int k, const int *active);
+int ycontract_probe(Plan *p, int prec, int k, int Q);
 
 // matvec.cu
 // y[:, c] = Z x[:, c]; xfmt/yfmt are VecFmt values; in_sel/in_scale as in FftPass.

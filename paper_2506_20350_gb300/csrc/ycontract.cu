@@ -355,6 +355,7 @@ template <class A, int KC>
 static bool yc_choose(Plan *p, int kc, YcShape &out) {
     const int qmax = std::min(8, std::min(p->b, p->my));
     for (int Q = qmax; Q >= 1; --Q) {
+        if (p->yc_force_q && Q != p->yc_force_q) continue;
         YcShape y;
         if (!yc_layout<A, KC>(p, kc, Q, y)) continue;
         cudaLaunchConfig_t cfg;
@@ -368,7 +369,7 @@ static bool yc_choose(Plan *p, int kc, YcShape &out) {
             cudaGetLastError();
             continue;
         }
-        if (nclus >= p->mx) {
+        if (nclus >= p->mx || (p->yc_force_q && nclus >= 1)) {   // a forced size may run in waves
             out = y;
             return true;
         }
@@ -465,6 +466,38 @@ static YcShape &yc_shape(Plan *p, int k) {
         y = t;
     }
     return y;
+}
+
+// Diagnostics (bttb_plan_debug): the cluster size and ring depth chosen, or for a given cluster size Q
+// the number of clusters the occupancy API lets run at once (negative: that shape does not fit).
+template <class A, int KC>
+static int yc_probe(Plan *p, int k, int Q) {
+    if (Q == 0) {
+        const YcShape &y = yc_shape<A, KC>(p, k);
+        return y.ok == 1 ? (y.Q | (y.nstages << 8)) : 0;
+    }
+    YcShape y;
+    if (!yc_layout<A, KC>(p, k, Q, y)) return -1;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    if (yc_config<A, KC>(p, y, cfg, attr, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return -2;
+    }
+    int nclus = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclus, ycontract_kernel<A, KC>, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return -1000 - (int)e;
+    }
+    return nclus;
+}
+
+int ycontract_probe(Plan *p, int prec, int k, int Q) {
+    if (k < 1 || k > 4) return -1;
+    if (prec == PREC_DF64) return k == 1 ? yc_probe<DF64, 1>(p, k, Q) : yc_probe<DF64, 4>(p, k, Q);
+    if (prec == PREC_F32) return k == 1 ? yc_probe<F32, 1>(p, k, Q) : yc_probe<F32, 4>(p, k, Q);
+    return -1;
 }
 
 bool ycontract_fits(Plan *p, int prec, int k) {

@@ -365,16 +365,19 @@ int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out);
  *   BTTB_DEBUG_WAIT_LIMIT_NS (value in ns, 0 = the default of 2 s, at most
  *     60 s): bound of every pipeline wait in this plan's kernels.  Frees the
  *     plan's GMRES workspace (its captured cycles hold the old bound).
- *   BTTB_DEBUG_PRODUCT_ROUTE (value 0..3): the form of products of one to
+ *   BTTB_DEBUG_PRODUCT_ROUTE (value 0..4): the form of products of one to
  *     four columns, for comparisons; every form gives the product to the
  *     precision's tolerance.  0: automatic (the default); 1: four strided FFT
  *     passes around the block product; 2: the two-level FFT in one cluster
  *     kernel each way around the block product; 3: the level-1 passes around
  *     one cluster kernel that runs the level-2 transforms and the block
- *     product (double-float and binary32 only).  A form that does not fit the
- *     plan falls back to the automatic choice.  Frees the GMRES workspace.
+ *     product; 4: all five steps as phases of one persistent kernel (one CTA
+ *     per SM, cooperative launch, bounded grid barriers; the same bits as 1).
+ *     Forms 3 and 4 are double-float and binary32 only.  A form that does
+ *     not fit the plan falls back to the automatic choice.  Frees the GMRES
+ *     workspace.
  *   BTTB_DEBUG_ROUTE_TAKEN (value = (prec << 8) | nrhs): returns the form
- *     (1..3 as above) that a product of nrhs columns in precision prec takes
+ *     (1..4 as above) that a product of nrhs columns in precision prec takes
  *     on this plan; products of more than four columns take the strided
  *     passes (1).  Changes nothing.
  *   BTTB_DEBUG_FUSED_SHAPE (value = (Q << 16) | (prec << 8) | nrhs, prec

@@ -93,6 +93,7 @@ static void plan_release(Plan &p) {
     p.bj_inv = nullptr;
     p.wsA = p.wsB = nullptr;
     p.d_err = nullptr;
+    p.d_gbar = nullptr;
 }
 
 }  // namespace bttb
@@ -166,8 +167,9 @@ int bttb_plan_create(bttb_plan *out, int nx, int ny, int b, int max_rhs, unsigne
     p.ws_bytes = (size_t)p.bins * p.ubs * 16;
     if ((rc = alloc(&p.wsA, p.ws_bytes, "product workspace")) != BTTB_OK) return bail(rc);
     if ((rc = alloc(&p.wsB, p.ws_bytes, "product workspace")) != BTTB_OK) return bail(rc);
-    if ((rc = alloc((void **)&p.d_err, sizeof(int), "error word")) != BTTB_OK) return bail(rc);
-    if ((e = cudaMemset(p.d_err, 0, sizeof(int))) != cudaSuccess) return bail(check_cuda(&p, e, "error word"));
+    if ((rc = alloc((void **)&p.d_err, 64, "error word")) != BTTB_OK) return bail(rc);
+    if ((e = cudaMemset(p.d_err, 0, 64)) != cudaSuccess) return bail(check_cuda(&p, e, "error word"));
+    p.d_gbar = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(p.d_err) + 16);
     *out = h;
     return BTTB_OK;
 }
@@ -359,7 +361,7 @@ int bttb_plan_debug(bttb_plan plan, int what, long long value) {
             gmres_free(&p);                           // captured cycles hold the old limit
             return BTTB_OK;
         case BTTB_DEBUG_PRODUCT_ROUTE:
-            if (value < 0 || value > 3) return set_error(&p, BTTB_ERR_INVALID_ARG, "route must be in [0, 3]");
+            if (value < 0 || value > 4) return set_error(&p, BTTB_ERR_INVALID_ARG, "route must be in [0, 4]");
             p.route = (int)value;
             gmres_free(&p);                           // captured cycles hold the old route
             return BTTB_OK;

@@ -27,6 +27,7 @@
 
 #include "arith.cuh"
 #include "blockprod.cuh"
+#include "fftcore.cuh"
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -226,6 +227,286 @@ __global__ void __launch_bounds__(kConsumerWarps * 32, 1) contract_kernel(const 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The whole product in one persistent kernel (one CTA per SM, cooperative launch): the four strided FFT
+// passes (x forward, y forward, y inverse, x inverse: App. B) and the block product above run as phases,
+// separated by grid-wide barriers.  Each warp's spectrum ring is filled at kernel start, so the first
+// spectrum stages land while the forward transforms run, and no launch gap separates the phases.  The
+// phases run the same stages and the same per-lane accumulation as the separate kernels, so the result is
+// bit for bit the one of the strided-pass route.  Every CTA arrives at every barrier (a CTA whose wait ran
+// out skips its work but keeps arriving), and every wait is bounded.
+// ---------------------------------------------------------------------------
+struct ProdArgs {
+    FftPass px, py, pyi, pxi;     // x forward (x -> U), y forward (U -> u^), y inverse (v^ -> V), x inverse (V -> y)
+    int fmt_x, fmt_y;             // formats of x and y
+    ContractArgs c;               // the block product (u = u^, v = v^)
+    unsigned long long *gbar;     // arrival counter: monotonic, 4 * gridDim.x arrivals per launch
+    uint32_t off_tw, off_b0, off_b1, off_ring;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier k (0..3) of this launch.  Thread 0 arrives and waits (bounded) until every CTA has arrived;
+// the launch's first arrival value fixes the base of its four barriers.
+__device__ __forceinline__ void prod_grid_barrier(unsigned long long *gbar, int k, unsigned long long *base_s,
+                                                  volatile int *abort, int *err, unsigned long long limit) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");   // generic writes before later bulk-copy reads
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long old = atomicAdd(gbar, 1ull);
+        const unsigned long long per = 4ull * gridDim.x;
+        if (k == 0) *base_s = old - old % per;
+        const unsigned long long target = *base_s + (unsigned long long)(k + 1) * gridDim.x;
+        if (old + 1 < target) {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u64(gbar) < target) {
+                if (global_ns() - t0 > limit) {
+                    *abort = 1;
+                    atomicOr(err, DEVERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+template <class A>
+__device__ __forceinline__ typename A::C prod_load(const void *base, long idx, int fmt) {
+    if (fmt == FMT_C128) return A::from_c128(__ldcg(reinterpret_cast<const double2 *>(base) + idx));
+    if (fmt == FMT_C64) return A::from_c64(__ldcg(reinterpret_cast<const float2 *>(base) + idx));
+    return A::from_cdf(__ldcg(reinterpret_cast<const float4 *>(base) + idx));
+}
+template <class A>
+__device__ __forceinline__ void prod_store(void *base, long idx, typename A::C v, int fmt) {
+    if (fmt == FMT_C128) reinterpret_cast<double2 *>(base)[idx] = A::to_c128(v);
+    else if (fmt == FMT_C64) reinterpret_cast<float2 *>(base)[idx] = A::to_c64(v);
+    else reinterpret_cast<float4 *>(base)[idx] = A::to_cdf(v);
+}
+
+// One strided pass as a phase: the CTAs take its (outer index, basis chunk, column) items in turn.  Inputs
+// are read through L2 (other CTAs wrote them in this launch).
+template <class A, bool INV>
+__device__ void prod_fft_phase(const FftPass &a, int infmt, int outfmt, typename A::C *tw, typename A::C *b0,
+                               typename A::C *b1, bool skip) {
+    using C = typename A::C;
+    const int M = a.M, P = a.P, lP = a.log2P, tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < M + 5; i += nt) tw[i] = reinterpret_cast<const C *>(a.tw)[i];
+    __syncthreads();
+    const int npc = (a.pdim + P - 1) / P;
+    const long items = (long)a.O * npc * a.ncols;
+    const long sel = a.in_sel ? (long)(*a.in_sel) * a.in_sel_stride : 0;
+    for (long it = blockIdx.x; it < items && !skip; it += gridDim.x) {
+        const int o = (int)(it % a.O);
+        const long rest = it / a.O;
+        const int pc = (int)(rest % npc), c = (int)(rest / npc);
+        if (a.active && !a.active[c]) continue;              // uniform per CTA
+        const int p0 = pc * P;
+        const long ibase = (long)c * a.in_cs + (long)o * a.in_os + sel;
+        const double scl = a.in_scale ? a.in_scale[c] : 1.0;
+        for (int idx = tid; idx < M * P; idx += nt) {
+            const int n = idx >> lP, q = idx & (P - 1), pi = p0 + q;
+            C v = A::zero();
+            if (n < a.nin && pi < a.pdim) {
+                v = prod_load<A>(a.in, ibase + (long)n * a.in_ns + pi, infmt);
+                if (a.in_scale) v = scale_by<A>(v, scl);
+            }
+            b0[idx] = v;
+        }
+        __syncthreads();
+        const C *res = fft_pass_stages<A, INV>(a, b0, b1, tw);
+        const long obase = (long)c * a.out_cs + (long)o * a.out_os;
+        for (int idx = tid; idx < a.nout * P; idx += nt) {
+            const int n = idx >> lP, q = idx & (P - 1), pi = p0 + q;
+            if (pi < a.pdim) prod_store<A>(a.out, obase + (long)n * a.out_ns + pi, res[idx], outfmt);
+        }
+        __syncthreads();
+    }
+}
+
+template <class A, int KC, int R, bool VEC>
+__global__ void __launch_bounds__(kConsumerWarps * 32, 1) product_kernel(const ProdArgs pa) {
+    using C = typename A::C;
+    using GT = typename GElem<A>::T;
+    constexpr int NPL = GElem<A>::planes;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const ContractArgs &a = pa.c;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem) + warp * kWarpStages;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8 * kConsumerWarps * kWarpStages);
+    unsigned long long *base_s = reinterpret_cast<unsigned long long *>(smem + 8 * kConsumerWarps * kWarpStages + 16);
+    C *tw = reinterpret_cast<C *>(smem + pa.off_tw);
+    C *b0 = reinterpret_cast<C *>(smem + pa.off_b0);
+    C *b1 = reinterpret_cast<C *>(smem + pa.off_b1);
+    unsigned char *stages = smem + pa.off_ring + (size_t)warp * kWarpStages * a.st_bytes;
+    if (threadIdx.x == 0) *abort_flag = 0;
+    if (lane == 0) {
+        for (int s = 0; s < kWarpStages; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const int b = a.b;
+    const int first = blockIdx.x + gridDim.x * warp;
+    const int step = gridDim.x * kConsumerWarps;
+    const int nbw = first < a.nbins ? (a.nbins - 1 - first) / step + 1 : 0;
+    const int nitems = nbw * a.nchunks;
+    const uint64_t pol_stream = l2_policy_evict_first();
+    const uint64_t pol_keep = l2_policy_evict_last();
+    const bool withheld0 = a.withhold && blockIdx.x == 0 && warp == 0;
+    auto issue_g = [&](int it) {
+        const int s = it % kWarpStages;
+        const int bin = first + step * (it / a.nchunks), ch = it % a.nchunks;
+        const int q0 = ch * a.Qc;
+        const int qn = min(a.Qc, b - q0);
+        const uint32_t gbytes = round_up16((uint32_t)(qn * b) * (uint32_t)sizeof(GT));
+        unsigned char *st = stages + (size_t)s * a.st_bytes;
+        mbar_expect_tx(&full[s], gbytes * NPL);
+        const long goff = (long)bin * a.gbs + (long)q0 * b;
+        bulk_g2s(st, reinterpret_cast<const GT *>(a.g0) + goff, gbytes, &full[s], pol_stream);
+        if (NPL == 2)
+            bulk_g2s(st + a.off_g1, reinterpret_cast<const GT *>(a.g1) + goff, gbytes, &full[s], pol_stream);
+    };
+    auto issue_u = [&](int it) {
+        const int s = it % kWarpStages;
+        const int bin = first + step * (it / a.nchunks);
+        const uint32_t ubytes = round_up16((uint32_t)(a.kc * b) * (uint32_t)sizeof(C));
+        unsigned char *st = stages + (size_t)s * a.st_bytes;
+        if (withheld0 && it == 0) mbar_expect_tx(&full[s], ubytes);
+        else mbar_arrive_expect_tx(&full[s], ubytes);
+        bulk_g2s(st + a.off_u, reinterpret_cast<const C *>(a.u) + (long)bin * a.ubs, ubytes, &full[s], pol_keep);
+    };
+    // the spectrum does not depend on x: fill both stages of every warp's ring now
+    const int npre = min(kWarpStages, nitems);
+    if (lane == 0)
+        for (int it = 0; it < npre; ++it) issue_g(it);
+    pdl_wait();
+    bool any = true;
+    if (a.active) {
+        any = false;
+        for (int c = 0; c < a.kc; ++c) any |= a.active[c] != 0;
+    }
+    if (!any) {                                           // uniform over the grid: no barrier is entered
+        if (lane == 0)
+            for (int it = 0; it < npre; ++it) {
+                mbar_arrive(&full[it % kWarpStages]);
+                mbar_wait_drain(&full[it % kWarpStages], 0u);
+            }
+        pdl_trigger();
+        return;
+    }
+    // ---- forward transforms: level 1 (x -> U), level 2 (U -> u^)
+    prod_fft_phase<A, false>(pa.px, pa.fmt_x, native_fmt<A>, tw, b0, b1, *abort_flag != 0);
+    prod_grid_barrier(pa.gbar, 0, base_s, abort_flag, a.err, a.wait_ns);
+    prod_fft_phase<A, false>(pa.py, native_fmt<A>, native_fmt<A>, tw, b0, b1, *abort_flag != 0);
+    prod_grid_barrier(pa.gbar, 1, base_s, abort_flag, a.err, a.wait_ns);
+
+    // ---- block product (as contract_kernel); the vectors' part of the pre-filled stages now
+    bool failed = *abort_flag != 0;
+    int issued = npre;
+    if (lane == 0 && !failed)
+        for (int it = 0; it < npre; ++it) issue_u(it);
+    if (failed) issued = 0;                               // the spectrum parts are drained below
+    Acc<A> acc[KC][R];
+    const int p0 = lane * R;
+    int it = 0;
+    for (; it < nitems && !failed; ++it) {
+        const int s = it % kWarpStages;
+        const uint32_t ph = (uint32_t)(it / kWarpStages) & 1u;
+        const int bin = first + step * (it / a.nchunks), ch = it % a.nchunks;
+        const bool ok = mbar_wait_bounded(&full[s], ph, abort_flag, a.wait_ns);
+        if (__any_sync(0xffffffffu, !ok)) {
+            failed = true;
+            break;
+        }
+        if (ch == 0) {
+#pragma unroll
+            for (int c = 0; c < KC; ++c)
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[c][r].zero();
+        }
+        {
+            const int q0 = ch * a.Qc;
+            const int qn = min(a.Qc, b - q0);
+            const unsigned char *st = stages + (size_t)s * a.st_bytes;
+            const GT *gs0 = reinterpret_cast<const GT *>(st) + p0;
+            const GT *gs1 = reinterpret_cast<const GT *>(st + a.off_g1) + p0;
+            const C *us = reinterpret_cast<const C *>(st + a.off_u) + q0;
+            if (p0 < b) {
+#pragma unroll 2
+                for (int q = 0; q < qn; ++q) {
+                    if constexpr (R == 2 && VEC) {
+                        using PV = typename Pair<GT>::V;
+                        const PV v0 = *reinterpret_cast<const PV *>(gs0 + q * b);
+                        const PV v1 = NPL == 2 ? *reinterpret_cast<const PV *>(gs1 + q * b) : v0;
+#pragma unroll
+                        for (int c = 0; c < KC; ++c) {
+                            const C u = us[c * b + q];
+                            acc[c][0].mac(Pair<GT>::lo(v0), Pair<GT>::lo(v1), u);
+                            acc[c][1].mac(Pair<GT>::hi(v0), Pair<GT>::hi(v1), u);
+                        }
+                    } else {
+                        GT v0[R], v1[R];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            v0[r] = p0 + r < b ? gs0[q * b + r] : GT{};
+                            v1[r] = NPL == 2 && p0 + r < b ? gs1[q * b + r] : v0[r];
+                        }
+#pragma unroll
+                        for (int c = 0; c < KC; ++c) {
+                            const C u = us[c * b + q];
+#pragma unroll
+                            for (int r = 0; r < R; ++r) acc[c][r].mac(v0[r], v1[r], u);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (ch == a.nchunks - 1) {
+#pragma unroll
+            for (int c = 0; c < KC; ++c)
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (c < a.kc && p0 + r < b)
+                        store_vec<A, native_fmt<A>>(a.v, (long)bin * a.ubs + (long)c * b + p0 + r, acc[c][r].result());
+        }
+        // stage s is free: refill it with the item kWarpStages ahead
+        if (lane == 0 && it + kWarpStages < nitems) {
+            issue_g(it + kWarpStages);
+            issue_u(it + kWarpStages);
+            ++issued;
+        }
+    }
+    if (lane == 0) {
+        if (failed) {
+            atomicOr(a.err, DEVERR_TIMEOUT);
+            *abort_flag = 1;
+            // items it .. issued-1 are outstanding (each in its own stage); before the block product started
+            // only the spectrum parts of the first npre were issued: supply their arrivals and drain them
+            const int lo = issued == 0 ? 0 : it, hi = issued == 0 ? npre : issued;
+            for (int d = lo; d < hi && d < lo + kWarpStages; ++d) {
+                if (issued == 0 || (withheld0 && d == 0)) mbar_arrive(&full[d % kWarpStages]);
+                mbar_wait_drain(&full[d % kWarpStages], (uint32_t)(d / kWarpStages) & 1u);
+            }
+        }
+    }
+    prod_grid_barrier(pa.gbar, 2, base_s, abort_flag, a.err, a.wait_ns);
+    // ---- inverse transforms: level 2 (v^ -> V), level 1 (V -> y)
+    prod_fft_phase<A, true>(pa.pyi, native_fmt<A>, native_fmt<A>, tw, b0, b1, *abort_flag != 0);
+    prod_grid_barrier(pa.gbar, 3, base_s, abort_flag, a.err, a.wait_ns);
+    pdl_trigger();
+    prod_fft_phase<A, true>(pa.pxi, native_fmt<A>, pa.fmt_y, tw, b0, b1, *abort_flag != 0);
+}
+
 template <class A>
 constexpr int prec_of() { return A::kind == 0 ? BTTB_MV_FP64 : (A::kind == 1 ? BTTB_MV_FP32 : BTTB_MV_FP64_NATIVE); }
 
@@ -313,6 +594,197 @@ static int launch_contract_impl(Plan *p, const void *u, void *v, int k, const in
         if (e != cudaSuccess) return check_cuda(p, e, "contract launch");
     }
     return BTTB_OK;
+}
+
+// ---------------------------------------------------------------- whole-product kernel: host side
+
+constexpr size_t kProdFftBytes = 32 * 1024;   // shared-memory area of the transform phases
+
+// The four strided passes of matvec_run, with one column per item (the items are dealt out over the CTAs).
+static int prod_passes(Plan *p, int fprec, int P, const void *x, long ldx, void *y, long ldy, int k,
+                       const int *in_sel, long in_sel_stride, const double *in_scale, const int *active,
+                       ProdArgs &pa) {
+    const int nx = p->nx, ny = p->ny, b = p->b, mx = p->mx, my = p->my;
+    const long plane = (long)ny * mx * b;
+    FftPass &a = pa.px, &c = pa.py, &d = pa.pyi, &e = pa.pxi;
+    a = FftPass{};
+    a.in = x; a.out = p->wsB;
+    a.in_cs = ldx; a.in_os = (long)nx * b; a.in_ns = b;
+    a.out_cs = plane; a.out_os = (long)mx * b; a.out_ns = b;
+    a.in_sel = in_sel; a.in_sel_stride = in_sel_stride; a.in_scale = in_scale; a.active = active;
+    a.O = ny; a.pdim = b; a.ncols = k; a.nin = nx; a.nout = mx; a.M = mx;
+    c = FftPass{};
+    c.in = p->wsB; c.out = p->wsA;
+    c.in_cs = plane; c.in_os = b; c.in_ns = (long)mx * b;
+    c.out_cs = b; c.out_os = p->ubs; c.out_ns = (long)mx * p->ubs;
+    c.O = mx; c.pdim = b; c.ncols = k; c.active = active; c.nin = ny; c.nout = my; c.M = my;
+    d = FftPass{};
+    d.in = p->wsB; d.out = p->wsA;
+    d.in_cs = b; d.in_os = p->ubs; d.in_ns = (long)mx * p->ubs;
+    d.out_cs = plane; d.out_os = b; d.out_ns = (long)mx * b;
+    d.O = mx; d.pdim = b; d.ncols = k; d.active = active; d.nin = my; d.nout = ny; d.M = my;
+    e = FftPass{};
+    e.in = p->wsA; e.out = y;
+    e.in_cs = plane; e.in_os = (long)mx * b; e.in_ns = b;
+    e.out_cs = ldy; e.out_os = (long)nx * b; e.out_ns = b;
+    e.O = ny; e.pdim = b; e.ncols = k; e.active = active; e.nin = mx; e.nout = nx; e.M = mx;
+    for (FftPass *q : {&a, &c, &d, &e}) {
+        q->cpb = 1;
+        const int rc = fft_pass_prepare(p, *q, fprec, P);
+        if (rc != BTTB_OK) return rc;
+        if (q->P != P) return set_error(p, BTTB_ERR_INVALID_ARG, "whole-product kernel: pass chunk mismatch");
+    }
+    return BTTB_OK;
+}
+
+// Shared-memory layout of the whole-product kernel; false if the ring does not fit.
+template <class A, int KC>
+static bool prod_layout(const Plan *p, int &P, ContractArgs &a, ProdArgs &pa, size_t &smem) {
+    using C = typename A::C;
+    using GT = typename GElem<A>::T;
+    constexpr int NPL = GElem<A>::planes;
+    const int b = p->b, Mmax = std::max(p->mx, p->my);
+    P = 1;
+    while (P < 16 && P < b) P <<= 1;
+    while (P > 1 && ((size_t)Mmax + 8 + 2 * (size_t)Mmax * P) * sizeof(C) > kProdFftBytes) P >>= 1;
+    pa.off_tw = 256;
+    pa.off_b0 = round_up16(256 + (uint32_t)(Mmax + 8) * sizeof(C));
+    pa.off_b1 = pa.off_b0 + (uint32_t)(Mmax * P) * sizeof(C);
+    pa.off_ring = round_up128(pa.off_b1 + (uint32_t)(Mmax * P) * sizeof(C));
+    const size_t optin = p->smem_optin > 0 ? p->smem_optin : 200 * 1024;
+    if (pa.off_ring >= optin) return false;
+    const size_t budget = optin - pa.off_ring;
+    const uint32_t ubytes_max = round_up128((uint32_t)(KC * b) * sizeof(C));
+    int Qc = b;
+    for (; Qc >= 1; --Qc) {
+        if (Qc < b && (Qc * b) % 2) continue;
+        const size_t st = (size_t)round_up128((uint32_t)(Qc * b) * sizeof(GT)) * NPL + ubytes_max;
+        if (st * kConsumerWarps * kWarpStages <= budget) break;
+    }
+    if (Qc < 1) return false;
+    {
+        const int nch = (b + Qc - 1) / Qc;
+        int q2 = (b + nch - 1) / nch;
+        if (q2 < b && (q2 * b) % 2) ++q2;
+        if (q2 <= Qc) Qc = q2;
+    }
+    const uint32_t gbytes = round_up128((uint32_t)(Qc * b) * sizeof(GT));
+    a.Qc = Qc;
+    a.nchunks = (b + Qc - 1) / Qc;
+    a.nstages = kWarpStages;
+    a.off_g1 = gbytes;
+    a.off_u = gbytes * NPL;
+    a.st_bytes = gbytes * NPL + ubytes_max;
+    smem = pa.off_ring + (size_t)a.st_bytes * kConsumerWarps * kWarpStages;
+    return smem <= optin;
+}
+
+template <class A> constexpr int prod_kc(int k) { return k == 1 ? 1 : (A::kind == 1 ? 4 : 2); }
+
+template <class A, int KC, int R>
+static int launch_product(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int k,
+                          const int *in_sel, long in_sel_stride, const double *in_scale, const int *active) {
+    using GT = typename GElem<A>::T;
+    constexpr int NPL = GElem<A>::planes;
+    constexpr bool VEC = R == 2;
+    ProdArgs pa{};
+    ContractArgs &a = pa.c;
+    int P = 0;
+    size_t smem = 0;
+    if (!prod_layout<A, KC>(p, P, a, pa, smem)) return set_error(p, BTTB_ERR_INVALID_ARG, "whole-product kernel does not fit");
+    int rc = prod_passes(p, A::kind == 0 ? PREC_DF64 : PREC_F32, P, x, ldx, y, ldy, k, in_sel, in_sel_stride, in_scale,
+                         active, pa);
+    if (rc != BTTB_OK) return rc;
+    pa.fmt_x = xfmt;
+    pa.fmt_y = yfmt;
+    pa.gbar = p->d_gbar;
+    a.gbs = p->gbs;
+    a.ubs = p->ubs;
+    a.nbins = (int)p->bins;
+    a.b = p->b;
+    a.kc = k;
+    a.err = p->d_err;
+    a.wait_ns = p->wait_ns;
+    a.withhold = 0;
+    if (p->withhold > 0) {                                 // test hook, never inside a captured graph
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(p->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            a.withhold = 1;
+            --p->withhold;
+        }
+    }
+    a.g0 = p->ghat_hi;
+    a.g1 = A::kind == 0 ? p->ghat_lo : nullptr;
+    a.u = p->wsA;
+    a.v = p->wsB;
+    a.active = active;
+    if (!a.g0 || (NPL == 2 && !a.g1))
+        return set_error(p, BTTB_ERR_INVALID_ARG, "plan does not keep the spectrum copy this precision reads");
+    auto kern = product_kernel<A, KC, R, VEC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
+    if (e != cudaSuccess) return check_cuda(p, e, "whole-product smem attribute");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p->nsm);
+    cfg.blockDim = dim3(kConsumerWarps * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = p->stream;
+    // Cooperative launch: every CTA is resident before any reaches a grid barrier.  No programmatic early
+    // launch: the kernel starts once its predecessor has finished, so co-residency needs no other guarantee.
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int tok = prof_begin(p, BTTB_K_BLOCK_PRODUCT_PREC + (A::kind == 0 ? BTTB_MV_FP64 : BTTB_MV_FP32));
+    e = cudaLaunchKernelEx(&cfg, kern, pa);
+    count_launch(p);
+    if (e != cudaSuccess) return check_cuda(p, e, "whole-product launch");
+    // algorithmic bytes of the whole product: spectrum planes once, x in, y out
+    auto esz = [](int f) { return f == FMT_C64 ? 8.0 : 16.0; };
+    prof_end(p, tok, (double)p->bins * p->b * p->b * sizeof(GT) * NPL + (double)k * p->n * (esz(xfmt) + esz(yfmt)));
+    return check_cuda(p, cudaGetLastError(), "whole-product launch");
+}
+
+bool product_persistent_fits(Plan *p, int prec, int k) {
+    if (!p->d_gbar || p->in_batch || p->b > 128 || (p->b > 32 && p->b <= 64 && p->b % 2)) return false;
+    if (prec != PREC_DF64 && prec != PREC_F32) return false;
+    if (k < 1 || k > (prec == PREC_DF64 ? 2 : 4)) return false;
+    static thread_local int coop = -1, coop_dev = -1;
+    if (coop < 0 || coop_dev != p->dev) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, p->dev) != cudaSuccess) v = 0;
+        coop = v;
+        coop_dev = p->dev;
+    }
+    if (!coop) return false;
+    int P = 0;
+    size_t smem = 0;
+    ContractArgs a{};
+    ProdArgs pa{};
+    return prec == PREC_DF64 ? (k == 1 ? prod_layout<DF64, 1>(p, P, a, pa, smem) : prod_layout<DF64, 2>(p, P, a, pa, smem))
+                             : (k == 1 ? prod_layout<F32, 1>(p, P, a, pa, smem) : prod_layout<F32, 4>(p, P, a, pa, smem));
+}
+
+template <class A, int KC>
+static int launch_product_r(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int k,
+                            const int *in_sel, long in_sel_stride, const double *in_scale, const int *active) {
+    switch ((p->b + 31) / 32) {
+        case 1: return launch_product<A, KC, 1>(p, x, xfmt, ldx, y, yfmt, ldy, k, in_sel, in_sel_stride, in_scale, active);
+        case 2: return launch_product<A, KC, 2>(p, x, xfmt, ldx, y, yfmt, ldy, k, in_sel, in_sel_stride, in_scale, active);
+        case 3: return launch_product<A, KC, 3>(p, x, xfmt, ldx, y, yfmt, ldy, k, in_sel, in_sel_stride, in_scale, active);
+        default: return launch_product<A, KC, 4>(p, x, xfmt, ldx, y, yfmt, ldy, k, in_sel, in_sel_stride, in_scale, active);
+    }
+}
+
+int product_persistent_launch(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int k,
+                              int prec, const int *in_sel, long in_sel_stride, const double *in_scale,
+                              const int *active) {
+    if (!product_persistent_fits(p, prec, k)) return set_error(p, BTTB_ERR_INVALID_ARG, "whole-product kernel does not fit");
+    if (prec == PREC_DF64)
+        return k == 1 ? launch_product_r<DF64, 1>(p, x, xfmt, ldx, y, yfmt, ldy, k, in_sel, in_sel_stride, in_scale, active)
+                      : launch_product_r<DF64, 2>(p, x, xfmt, ldx, y, yfmt, ldy, k, in_sel, in_sel_stride, in_scale, active);
+    return k == 1 ? launch_product_r<F32, 1>(p, x, xfmt, ldx, y, yfmt, ldy, k, in_sel, in_sel_stride, in_scale, active)
+                  : launch_product_r<F32, 4>(p, x, xfmt, ldx, y, yfmt, ldy, k, in_sel, in_sel_stride, in_scale, active);
 }
 
 template <class A, int KC, int R>

@@ -96,40 +96,6 @@ void fft_plan_free(FftPlan &f) {
     f.tw_f32 = nullptr;
 }
 
-constexpr int kFftThreads = 256;
-
-// One Stockham stage of radix R over the P interleaved sequences: thread (pp, j0) takes the butterflies
-// j = j0, j0 + jstep, ... of batch index pp.  With Ns the product of the earlier radices, butterfly j reads
-// src[j + r m] (m = M/R), twiddles inputs r >= 1 by w^(r k tstep) (k = j mod Ns) and writes
-// dst[(j div Ns) Ns R + k + r Ns].  j div Ns is one high multiply by nsmagic = ceil(2^32 / Ns), exact for
-// j, Ns < 2^16.
-template <class A, int R, bool INV>
-__device__ __forceinline__ void fft_stage(const typename A::C *__restrict__ src, typename A::C *__restrict__ dst,
-                                          const typename A::C *tw, int m, int Ns, unsigned nsmagic, int tstep,
-                                          int lP, int pp, int j0, int jstep, typename A::K s3, typename A::K c1,
-                                          typename A::K c2, typename A::K s1, typename A::K s2) {
-    using C = typename A::C;
-    constexpr int sg = INV ? 1 : -1;
-    for (int j = j0; j < m; j += jstep) {
-        const int q = Ns == 1 ? j : (int)__umulhi((unsigned)j, nsmagic);
-        const int k = j - q * Ns;
-        C v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[((j + r * m) << lP) + pp];
-        if (k != 0) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = A::cmul(v[r], tw[r * k * tstep], INV);
-        }
-        if constexpr (R == 2) Butterfly<A>::r2(v);
-        else if constexpr (R == 3) Butterfly<A>::r3(v, sg, s3);
-        else if constexpr (R == 4) Butterfly<A>::r4(v, sg);
-        else Butterfly<A>::r5(v, sg, c1, c2, s1, s2);
-        const int dbase = q * Ns * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) dst[((dbase + r * Ns) << lP) + pp] = v[r];
-    }
-}
-
 // Whether an input format is the number system's own element or its leading part, so that the load is a
 // plain copy (8 bytes for binary32, 16 for the others): then it can be an asynchronous copy.
 template <class A, int INF>
@@ -195,30 +161,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPass a) 
         cp_async_commit();
     };
     // (called after a barrier that follows the twiddle staging)
-    auto stages = [&](C *src, C *dst) -> C * {
-        const K s3 = real_const<A>(tw[M + 4]);
-        const K c1 = real_const<A>(tw[M + 0]), c2 = real_const<A>(tw[M + 1]);
-        const K s1 = real_const<A>(tw[M + 2]), s2 = real_const<A>(tw[M + 3]);
-        int Ns = 1;
-        for (int s = 0; s < a.nst; ++s) {
-            const int R = a.radix[s];
-            const int m = M / R;
-            const int tstep = M / (Ns * R);
-            const unsigned mg = a.nsmagic[s];
-            switch (R) {
-                case 2: fft_stage<A, 2, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
-                case 3: fft_stage<A, 3, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
-                case 4: fft_stage<A, 4, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
-                default: fft_stage<A, 5, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
-            }
-            __syncthreads();
-            C *t = src;
-            src = dst;
-            dst = t;
-            Ns *= R;
-        }
-        return src;
-    };
+    auto stages = [&](C *src, C *dst) -> C * { return fft_pass_stages<A, INV>(a, src, dst, tw); };
     auto store = [&](int c, const C *res) {
         const long obase = (long)c * a.out_cs + (long)o * a.out_os;
         for (int idx = tid; idx < a.nout * P; idx += nt) {
@@ -311,7 +254,7 @@ static int choose_P(int M, int pdim, size_t elem, int pmax, int nbuf) {
 constexpr int kFftMultiCols = 4;
 constexpr int kFftMultiMinCols = 32;
 
-int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool inverse) {
+int fft_pass_prepare(Plan *p, FftPass &a, int prec, int pmax) {
     const FftPlan &f = (a.M == p->fx.M) ? p->fx : p->fy;
     if (f.M != a.M) return set_error(p, BTTB_ERR_INVALID_ARG, "no FFT plan for this length");
     a.nst = f.nst;
@@ -324,15 +267,27 @@ int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool in
         }
     }
     size_t elem = prec == PREC_F32 ? 8 : 16;
-    a.cpb = a.ncols >= kFftMultiMinCols ? kFftMultiCols : 1;
-    a.P = choose_P(a.M, a.pdim, elem, p->fft_pmax, a.cpb > 1 ? 3 : 2);
+    if (a.cpb < 1) a.cpb = a.ncols >= kFftMultiMinCols ? kFftMultiCols : 1;
+    a.P = choose_P(a.M, a.pdim, elem, pmax, a.cpb > 1 ? 3 : 2);
     a.log2P = 0;
     while ((1 << a.log2P) < a.P) ++a.log2P;
+    switch (prec) {
+        case PREC_F64N: a.tw = f.tw_f64; break;
+        case PREC_F32: a.tw = f.tw_f32; break;
+        default: a.tw = f.tw_df; break;
+    }
+    return BTTB_OK;
+}
+
+int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool inverse) {
+    a.cpb = 0;
+    const int rc = fft_pass_prepare(p, a, prec, p->fft_pmax);
+    if (rc != BTTB_OK) return rc;
     if (a.O <= 0 || a.ncols <= 0 || a.pdim <= 0) return BTTB_OK;
     switch (prec) {
-        case PREC_F64N: a.tw = f.tw_f64; return dispatch_fmt<F64N>(p, a, infmt, outfmt, inverse);
-        case PREC_F32: a.tw = f.tw_f32; return dispatch_fmt<F32>(p, a, infmt, outfmt, inverse);
-        default: a.tw = f.tw_df; return dispatch_fmt<DF64>(p, a, infmt, outfmt, inverse);
+        case PREC_F64N: return dispatch_fmt<F64N>(p, a, infmt, outfmt, inverse);
+        case PREC_F32: return dispatch_fmt<F32>(p, a, infmt, outfmt, inverse);
+        default: return dispatch_fmt<DF64>(p, a, infmt, outfmt, inverse);
     }
 }
 

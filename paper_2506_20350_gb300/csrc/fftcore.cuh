@@ -147,4 +147,72 @@ __device__ typename A::C *fft2_level(typename A::C *src, typename A::C *dst, con
     return src;
 }
 
+constexpr int kFftThreads = 256;
+
+// One Stockham stage of radix R over the P interleaved sequences: thread (pp, j0) takes the butterflies
+// j = j0, j0 + jstep, ... of batch index pp.  With Ns the product of the earlier radices, butterfly j reads
+// src[j + r m] (m = M/R), twiddles inputs r >= 1 by w^(r k tstep) (k = j mod Ns) and writes
+// dst[(j div Ns) Ns R + k + r Ns].  j div Ns is one high multiply by nsmagic = ceil(2^32 / Ns), exact for
+// j, Ns < 2^16.
+template <class A, int R, bool INV>
+__device__ __forceinline__ void fft_stage(const typename A::C *__restrict__ src, typename A::C *__restrict__ dst,
+                                          const typename A::C *tw, int m, int Ns, unsigned nsmagic, int tstep,
+                                          int lP, int pp, int j0, int jstep, typename A::K s3, typename A::K c1,
+                                          typename A::K c2, typename A::K s1, typename A::K s2) {
+    using C = typename A::C;
+    constexpr int sg = INV ? 1 : -1;
+    for (int j = j0; j < m; j += jstep) {
+        const int q = Ns == 1 ? j : (int)__umulhi((unsigned)j, nsmagic);
+        const int k = j - q * Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[((j + r * m) << lP) + pp];
+        if (k != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = A::cmul(v[r], tw[r * k * tstep], INV);
+        }
+        if constexpr (R == 2) Butterfly<A>::r2(v);
+        else if constexpr (R == 3) Butterfly<A>::r3(v, sg, s3);
+        else if constexpr (R == 4) Butterfly<A>::r4(v, sg);
+        else Butterfly<A>::r5(v, sg, c1, c2, s1, s2);
+        const int dbase = q * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[((dbase + r * Ns) << lP) + pp] = v[r];
+    }
+}
+
+// All stages of one strided pass over the P interleaved sequences of a CTA (buffers [n][P], n < M),
+// called after a barrier that follows the twiddle staging; returns the buffer that holds the result.
+template <class A, bool INV>
+__device__ __forceinline__ typename A::C *fft_pass_stages(const FftPass &a, typename A::C *src, typename A::C *dst,
+                                                          const typename A::C *tw) {
+    using C = typename A::C;
+    using K = typename A::K;
+    const int M = a.M, lP = a.log2P;
+    const int tid = threadIdx.x, nt = kFftThreads;
+    const int pp = tid & (a.P - 1), j0 = tid >> lP, jstep = nt >> lP;
+    const K s3 = real_const<A>(tw[M + 4]);
+    const K c1 = real_const<A>(tw[M + 0]), c2 = real_const<A>(tw[M + 1]);
+    const K s1 = real_const<A>(tw[M + 2]), s2 = real_const<A>(tw[M + 3]);
+    int Ns = 1;
+    for (int s = 0; s < a.nst; ++s) {
+        const int R = a.radix[s];
+        const int m = M / R;
+        const int tstep = M / (Ns * R);
+        const unsigned mg = a.nsmagic[s];
+        switch (R) {
+            case 2: fft_stage<A, 2, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+            case 3: fft_stage<A, 3, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+            case 4: fft_stage<A, 4, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+            default: fft_stage<A, 5, INV>(src, dst, tw, m, Ns, mg, tstep, lP, pp, j0, jstep, s3, c1, c2, s1, s2); break;
+        }
+        __syncthreads();
+        C *t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
 }  // namespace bttb

@@ -72,7 +72,7 @@ struct YcShape {
 };
 
 // Forms of a product of one to four columns (bttb_plan_debug BTTB_DEBUG_PRODUCT_ROUTE).
-enum ProductRoute { ROUTE_AUTO = 0, ROUTE_PASSES = 1, ROUTE_FUSED_FFT2 = 2, ROUTE_FUSED_Y = 3 };
+enum ProductRoute { ROUTE_AUTO = 0, ROUTE_PASSES = 1, ROUTE_FUSED_FFT2 = 2, ROUTE_FUSED_Y = 3, ROUTE_PERSISTENT = 4 };
 
 struct Plan {
     int nx = 0, ny = 0, b = 0, mx = 0, my = 0, max_rhs = 0;
@@ -113,7 +113,8 @@ struct Plan {
 
     GmresWork *gw = nullptr;
     Learned *learned = nullptr;   // attached learned preconditioner (learned.cu), not owned
-    int *d_err = nullptr;         // device error word
+    int *d_err = nullptr;         // device error word (first word of a 64-byte block)
+    unsigned long long *d_gbar = nullptr;   // grid-barrier arrival counter of the whole-product kernel (d_err + 16 B)
     size_t bytes_held = 0;
 
     // Profiling (bttb_profile): event pairs around timed launches, launch count.
@@ -164,6 +165,8 @@ int check_cuda(Plan *p, cudaError_t e, const char *what);
 int fft_plan_init(Plan *p, FftPlan &f, int M);
 void fft_plan_free(FftPlan &f);
 int fft_pass_launch(Plan *p, FftPass a, int prec, int infmt, int outfmt, bool inverse);
+// Radix plan, batch chunk P (at most pmax) and twiddles of a pass, without launching it (a.cpb = 0: choose).
+int fft_pass_prepare(Plan *p, FftPass &a, int prec, int pmax);
 // Both FFT levels of a product in one kernel (few columns): forward cell-ordered x (cellfmt) -> u^, or
 // inverse v^ -> cell-ordered y (cellfmt); ld is the cell-ordered vector's column stride.
 int fft2_fused_launch(Plan *p, const void *in, void *out, long ld, int ncols, int prec, int cellfmt, bool inverse,
@@ -176,6 +179,13 @@ int smallest_5smooth(int n);
 
 // contract.cu
 int contract_launch(Plan *p, int prec, const void *u, void *v, int k, const int *active = nullptr);
+
+// contract.cu: the whole product (the four strided passes and the block product as phases of one
+// persistent kernel); whether it takes k columns of this precision, and its launch (formats as matvec_run).
+bool product_persistent_fits(Plan *p, int prec, int k);
+int product_persistent_launch(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, long ldy, int k,
+                              int prec, const int *in_sel, long in_sel_stride, const double *in_scale,
+                              const int *active);
 
 // ycontract.cu: whether the fused y-level transform + block product takes k columns in this precision
 // (decided once per plan), and its launch on the x pass's output U ([c][iy][kx][p]) into V (same layout).

@@ -41,11 +41,13 @@ int product_route(Plan *p, int nrhs, int prec) {
     const int yprec = prec == PREC_TC ? PREC_F32 : prec;        // below kTcMinCols the TC form is binary32
     const bool y_ok = few && (yprec == PREC_DF64 || yprec == PREC_F32) && ycontract_fits(p, yprec, nrhs);
     const bool f2_ok = few && fft2_fused_smem(p, fprec) <= p->smem_optin / 2;
+    const bool pk_ok = few && product_persistent_fits(p, yprec, nrhs);
     int route = p->route;
+    if (route == ROUTE_PERSISTENT && !pk_ok) route = ROUTE_AUTO;
     if (route == ROUTE_FUSED_Y && !y_ok) route = ROUTE_AUTO;
     if (route == ROUTE_FUSED_FFT2 && !f2_ok) route = ROUTE_AUTO;
     if (route == ROUTE_AUTO)
-        route = y_ok ? ROUTE_FUSED_Y : ((f2_ok && (fprec != PREC_F32 || p->in_batch)) ? ROUTE_FUSED_FFT2 : ROUTE_PASSES);
+        route = (f2_ok && (fprec != PREC_F32 || p->in_batch)) ? ROUTE_FUSED_FFT2 : ROUTE_PASSES;
     return route;
 }
 
@@ -59,6 +61,9 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     const int route = product_route(p, nrhs, prec);
     const int yprec = prec == PREC_TC ? PREC_F32 : prec;
 
+    if (route == ROUTE_PERSISTENT)
+        return product_persistent_launch(p, x, xfmt, ldx, y, yfmt, ldy, nrhs, yprec, in_sel, in_sel_stride, in_scale,
+                                         active);
     if (route == ROUTE_FUSED_FFT2) {
         if ((rc = fft2_fused_launch(p, x, p->wsA, ldx, nrhs, fprec, xfmt, false, in_sel, in_sel_stride, in_scale,
                                     active)) != BTTB_OK)

@@ -176,6 +176,7 @@ extern "C" int bttb_matvec_noalloc(int nx, int ny, int b, const void *gen, const
 
     unsigned char *cur = static_cast<unsigned char *>(base);
     p.d_err = reinterpret_cast<int *>(cur);
+    p.d_gbar = reinterpret_cast<unsigned long long *>(cur + 16);   // monotonic: never cleared
     cur += 256;
     fill_fft_plan(p.fx, p.mx, cur);
     if (p.my == p.mx) {

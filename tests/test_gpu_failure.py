@@ -133,12 +133,12 @@ def test_happy_breakdown_on_an_eigenvector(bt):
     plan.close()
 
 
-@pytest.mark.parametrize("route", [1, 3])
+@pytest.mark.parametrize("route", [1, 3, 4])
 def test_timeout_is_reported_and_the_plan_recovers(bt, tiny, route):
     """A block-product launch that withholds an mbarrier arrival (the warp-per-bin kernel of the strided
-    route, and the fused level-2 kernel): the bounded wait (1 ms here) runs out, the kernel drains its
-    copies and returns, and the solve returns BTTB_ERR_TIMEOUT.  The same plan and a fresh plan then solve
-    normally."""
+    route, the fused level-2 kernel, and the whole-product persistent kernel, whose other CTAs then also
+    pass its later grid barriers): the bounded wait (1 ms here) runs out, the kernel drains its copies and
+    returns, and the solve returns BTTB_ERR_TIMEOUT.  The same plan and a fresh plan then solve normally."""
     nx, ny, b, gen, v = tiny
     plan = bt.Plan(nx, ny, b, max_rhs=1)
     plan.set_generators(gen)

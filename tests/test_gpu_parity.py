@@ -249,7 +249,7 @@ def test_spectrum_matches_oracle(bt):
     assert np.abs(got - ref[1, 2]).max() <= 1e-13 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("route", [1, 2, 3])
+@pytest.mark.parametrize("route", [1, 2, 3, 4])
 @pytest.mark.parametrize("nx,ny,b,k", [
     (5, 4, 12, 1),     # grid 9 x 8: clusters of 8, two bases per CTA
     (6, 5, 16, 2),     # two columns
@@ -260,9 +260,10 @@ def test_spectrum_matches_oracle(bt):
     (12, 2, 24, 2),    # grid 24 x 3: more bins than CTAs of a column
 ])
 def test_product_routes(bt, route, nx, ny, b, k):
-    """The three forms of a one-to-four-column product (four strided passes; the two-level FFT in one
-    cluster kernel each way; the level-1 passes around the fused level-2 transform + block product) give
-    the oracle's product to the precision's tolerance; a form that does not fit falls back."""
+    """The four forms of a one-to-four-column product (four strided passes; the two-level FFT in one
+    cluster kernel each way; the level-1 passes around the fused level-2 transform + block product; all of
+    it as phases of one persistent kernel) give the oracle's product to the precision's tolerance; a form
+    that does not fit falls back.  The persistent kernel gives the strided route's bits."""
     gen = arrays.random_generator_blocks(nx, ny, b, seed=500 + nx + ny + b + k)
     plan = bt.Plan(nx, ny, b, max_rhs=k)
     plan.set_generators(gen)
@@ -273,6 +274,13 @@ def test_product_routes(bt, route, nx, ny, b, k):
     _check(plan.matvec(_dev(x.astype(np.complex64)), prec=bt.BTTB_MV_FP32).cpu().numpy(),
            oracle.matvec(gen, x.astype(np.complex64).T).T, FP32_TOL, f"binary32 route {route}")
     _check(plan.matvec(_dev(x), prec=bt.BTTB_MV_FP32).cpu().numpy(), ref, FP32_TOL, f"binary32 c128 io {route}")
+    if route == 4:
+        ys = {}
+        for r in (1, 4):
+            bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, r)
+            ys[r] = (plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64).cpu().numpy(),
+                     plan.matvec(_dev(x.astype(np.complex64)), prec=bt.BTTB_MV_FP32).cpu().numpy())
+        assert np.array_equal(ys[1][0], ys[4][0]) and np.array_equal(ys[1][1], ys[4][1])
     plan.close()
 
 
@@ -298,7 +306,7 @@ def test_full_size_product(bt, precision_case):
     print(f"30x30 b=60 product error vs oracle: df64 {e64:.2e}, binary64 {e64n:.2e}, binary32 {e32:.2e}")
 
 
-@pytest.mark.parametrize("route", [1, 2, 3])
+@pytest.mark.parametrize("route", [1, 2, 3, 4])
 def test_full_size_product_routes(bt, precision_case, route):
     """Every form of the 30x30, b=60 product against the O(N^2) oracle, double-float and binary32."""
     c, gen, plan, x, ref = precision_case

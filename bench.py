@@ -561,12 +561,12 @@ def run_ours(args):
     x32 = x.to(torch.complex64)
     y32 = torch.empty_like(x32)
     mv = {}
-    route_names = {1: "strided_passes", 2: "fused_fft2", 3: "fused_y"}
+    route_names = {1: "strided_passes", 2: "fused_fft2", 3: "fused_y", 4: "persistent"}
     for name, prec, xx, yy, dt, nb in [("fp64_doublefloat", bt.BTTB_MV_FP64, x, y, bt.BTTB_C128, b64),
                                       ("fp32", bt.BTTB_MV_FP32, x32, y32, bt.BTTB_C64, b32),
                                       ("fp64_native", bt.BTTB_MV_FP64_NATIVE, x, y, bt.BTTB_C128, b64)]:
         entry = {}
-        for route in (0, 1, 2, 3):
+        for route in (0, 1, 2, 3, 4):
             bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, route)
             taken = bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_ROUTE_TAKEN, (prec << 8) | 1)
             if route and taken != route:

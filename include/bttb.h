@@ -57,11 +57,17 @@ typedef enum {
     BTTB_MV_FP64 = 0,        /* double-float spectrum (hi+lo planes) and arithmetic  */
     BTTB_MV_FP32 = 1,        /* binary32 spectrum (the hi plane) and arithmetic      */
     BTTB_MV_FP64_NATIVE = 2, /* binary64 spectrum copy, binary64 (DFMA) arithmetic   */
-    BTTB_MV_TC_3XTF32 = 3    /* binary32 FFT passes; with >= 16 columns and b <= 64 the
-                                per-bin GEMM runs on the tensor cores in 3xTF32 (TF32
-                                head + tail of each factor, binary32 accumulation:
-                                binary32-level accuracy), otherwise as BTTB_MV_FP32.
-                                Reads the binary32 spectrum (hi plane).               */
+    BTTB_MV_TC_3XTF32 = 3,   /* binary32 FFT passes; with >= 16 columns the per-bin
+                                GEMM runs on the tensor cores in 3xTF32 (each factor
+                                split into a TF32 head and tail, three MMAs, binary32
+                                accumulation: binary32-level accuracy): tcgen05 MMAs
+                                with TMA-fed tiles for even b <= 64, warp-level MMAs
+                                for odd b <= 64; otherwise as BTTB_MV_FP32.  Reads the
+                                binary32 spectrum (hi plane).                         */
+    BTTB_MV_TC_BF16X3 = 4    /* as BTTB_MV_TC_3XTF32 with each factor split into two
+                                bfloat16 terms (split-BF16x3, tcgen05 for even b <= 64,
+                                else as BTTB_MV_FP32): about 2^-17 relative error per
+                                product term                                          */
 } bttb_mv_prec;
 
 typedef enum {
@@ -132,7 +138,7 @@ typedef struct {
     int max_iters;       /* total Arnoldi steps per column                         */
     bttb_precond pc;     /* right preconditioner (the residual stays the true one) */
     bttb_mv_prec inner;  /* precision of the products inside a restart cycle:
-                            FP64 = plain GMRES; FP32 or TC_3XTF32 = GMRES-IR (each
+                            FP64 = plain GMRES; FP32 or TC_* = GMRES-IR (each
                             cycle's starting residual is recomputed with the FP64
                             product, Arnoldi/Givens stay FP64)                    */
     int use_x0;          /* nonzero: I holds the initial guess on entry            */

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbttb.so")
 
 BTTB_C64, BTTB_C128 = 0, 1
-BTTB_MV_FP64, BTTB_MV_FP32, BTTB_MV_FP64_NATIVE, BTTB_MV_TC_3XTF32 = 0, 1, 2, 3
+BTTB_MV_FP64, BTTB_MV_FP32, BTTB_MV_FP64_NATIVE, BTTB_MV_TC_3XTF32, BTTB_MV_TC_BF16X3 = 0, 1, 2, 3, 4
 BTTB_PC_NONE, BTTB_PC_BLOCK_JACOBI, BTTB_PC_LEARNED = 0, 1, 2
 BTTB_GMRES_NO_GRAPH, BTTB_GMRES_GLOBAL, BTTB_GMRES_CGS2 = 1, 2, 4
 BTTB_OK, BTTB_NOT_CONVERGED, BTTB_BREAKDOWN = 0, 1, 2

@@ -70,7 +70,8 @@ static bool prec_enabled(const Plan &p, int prec) {
         case BTTB_MV_FP64: return p.ghat_hi && p.ghat_lo;
         case BTTB_MV_FP32: return p.ghat_hi != nullptr;
         case BTTB_MV_FP64_NATIVE: return p.ghat_f64 != nullptr;
-        case BTTB_MV_TC_3XTF32: return p.ghat_hi != nullptr;
+        case BTTB_MV_TC_3XTF32:
+        case BTTB_MV_TC_BF16X3: return p.ghat_hi != nullptr;
         default: return false;
     }
 }
@@ -110,7 +111,7 @@ int bttb_plan_create(bttb_plan *out, int nx, int ny, int b, int max_rhs, unsigne
                          "sizes must satisfy 1 <= nx, ny <= 1024, 1 <= b <= 256, 1 <= max_rhs <= 4096");
     if (prec_mask == 0) prec_mask = (1u << BTTB_MV_FP64) | (1u << BTTB_MV_FP32);
     if (prec_mask & ~((1u << BTTB_MV_FP64) | (1u << BTTB_MV_FP32) | (1u << BTTB_MV_FP64_NATIVE) |
-                      (1u << BTTB_MV_TC_3XTF32)))
+                      (1u << BTTB_MV_TC_3XTF32) | (1u << BTTB_MV_TC_BF16X3)))
         return set_error(nullptr, BTTB_ERR_INVALID_ARG, "unknown bit in prec_mask");
     bttb_plan h = new (std::nothrow) bttb_plan_s();
     if (!h) return set_error(nullptr, BTTB_ERR_OOM, "host allocation failed");
@@ -156,7 +157,7 @@ int bttb_plan_create(bttb_plan *out, int nx, int ny, int b, int max_rhs, unsigne
         p.bytes_held += bytes;
         return BTTB_OK;
     };
-    if (prec_mask & ((1u << BTTB_MV_FP64) | (1u << BTTB_MV_FP32) | (1u << BTTB_MV_TC_3XTF32)))
+    if (prec_mask & ((1u << BTTB_MV_FP64) | (1u << BTTB_MV_FP32) | (1u << BTTB_MV_TC_3XTF32) | (1u << BTTB_MV_TC_BF16X3)))
         if ((rc = alloc((void **)&p.ghat_hi, gplane * sizeof(float2), "spectrum hi plane")) != BTTB_OK) return bail(rc);
     if (prec_mask & (1u << BTTB_MV_FP64))
         if ((rc = alloc((void **)&p.ghat_lo, gplane * sizeof(float2), "spectrum lo plane")) != BTTB_OK) return bail(rc);
@@ -367,7 +368,7 @@ int bttb_plan_debug(bttb_plan plan, int what, long long value) {
             return BTTB_OK;
         case BTTB_DEBUG_ROUTE_TAKEN: {
             const int prec = (int)(value >> 8), k = (int)(value & 255);
-            if (prec < 0 || prec > BTTB_MV_TC_3XTF32 || k < 1 || k > p.max_rhs)
+            if (prec < 0 || prec > BTTB_MV_TC_BF16X3 || k < 1 || k > p.max_rhs)
                 return set_error(&p, BTTB_ERR_INVALID_ARG, "value must be (prec << 8) | nrhs, 1 <= nrhs <= max_rhs");
             return product_route(&p, k, prec);
         }

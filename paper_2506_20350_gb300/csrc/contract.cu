@@ -1161,8 +1161,11 @@ static int launch_contract_tc(Plan *p, const void *u, void *v, int k) {
 
 int contract_launch(Plan *p, int prec, const void *u, void *v, int k, const int *active) {
     // Tensor cores for a real per-bin GEMM (many columns, b <= 64); a GEMV (few columns) has no reuse.
-    if (prec == PREC_TC) {
-        if (k >= kTcMinCols && p->b <= 64) return launch_contract_tc(p, u, v, k);
+    // Tensor cores for a real per-bin GEMM (many columns); a GEMV (few columns) has no reuse.  tcgen05 with
+    // TMA-fed tiles when b is even and at most 64; the warp-level 3xTF32 form for odd b; binary32 otherwise.
+    if (is_tc_prec(prec)) {
+        if (tcgemm_fits(p, k)) return tcgemm_launch(p, prec == PREC_TCB ? 1 : 0, u, v, k);
+        if (prec == PREC_TC && k >= kTcMinCols && p->b <= 64) return launch_contract_tc(p, u, v, k);
         prec = PREC_F32;
     }
     // Many right-hand sides in binary32: a tiled per-bin GEMM instead of k/4 passes over the spectrum.

@@ -1638,7 +1638,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
                     mlim[c] = std::min(m, max_iters - total[c]);
                     const double b0 = std::sqrt(b2[c]);
                     double t = 0.9 * o->tol * vnorm[c];
-                    if (inner == BTTB_MV_FP32 || inner == BTTB_MV_TC_3XTF32) t = std::max(t, 1e-5 * b0);
+                    if (inner == BTTB_MV_FP32 || inner == BTTB_MV_TC_3XTF32 || inner == BTTB_MV_TC_BF16X3) t = std::max(t, 1e-5 * b0);
                     tgt[c] = t;
                     cycles[c] += 1;
                 }
@@ -1672,7 +1672,7 @@ int gmres_solve(Plan *p, const void *V, void *I, int k, long ld, const bttb_gmre
                 act[0] = 1;
                 mlim[0] = std::min(m, max_iters - total[0]);
                 double t = 0.9 * o->tol * (std::isfinite(vmin) ? vmin : 0.0);
-                if (inner == BTTB_MV_FP32 || inner == BTTB_MV_TC_3XTF32) t = std::max(t, 1e-5 * std::sqrt(f2));
+                if (inner == BTTB_MV_FP32 || inner == BTTB_MV_TC_3XTF32 || inner == BTTB_MV_TC_BF16X3) t = std::max(t, 1e-5 * std::sqrt(f2));
                 tgt[0] = t;
                 for (int c = 0; c < k; ++c) cycles[c] += 1;
                 e = cudaMemcpyAsync(g->beta2, &f2, sizeof(double), cudaMemcpyHostToDevice, st);

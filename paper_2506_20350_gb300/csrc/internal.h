@@ -52,11 +52,12 @@ struct FftPass {
 };
 
 enum Prec { PREC_DF64 = BTTB_MV_FP64, PREC_F32 = BTTB_MV_FP32, PREC_F64N = BTTB_MV_FP64_NATIVE,
-            PREC_TC = BTTB_MV_TC_3XTF32 };
+            PREC_TC = BTTB_MV_TC_3XTF32, PREC_TCB = BTTB_MV_TC_BF16X3 };
 // Columns from which BTTB_MV_TC_3XTF32 runs the block product on the tensor cores.
 constexpr int kTcMinCols = 16;
 // FFT passes and vector format of a product precision (the tensor-core product is binary32 around the GEMM).
-inline int fft_prec_of(int prec) { return prec == PREC_TC ? PREC_F32 : prec; }
+inline bool is_tc_prec(int prec) { return prec == PREC_TC || prec == PREC_TCB; }
+inline int fft_prec_of(int prec) { return is_tc_prec(prec) ? PREC_F32 : prec; }
 
 struct GmresWork;
 struct Learned;
@@ -176,6 +177,11 @@ size_t fft2_fused_smem(const Plan *p, int prec);
 constexpr int kFusedFftMaxCols = 4;
 int spectrum_compute(Plan *p, const void *gen, bttb_dtype dtype, int gen_is_host);
 int smallest_5smooth(int n);
+
+// tcgemm.cu: the many-column per-bin GEMM on the tcgen05 tensor cores (3xTF32, or split-BF16x3 with
+// fmt_bf16); fits when b is even and at most 64 and k >= kTcMinCols.
+bool tcgemm_fits(const Plan *p, int k);
+int tcgemm_launch(Plan *p, int fmt_bf16, const void *u, void *v, int k);
 
 // contract.cu
 int contract_launch(Plan *p, int prec, const void *u, void *v, int k, const int *active = nullptr);

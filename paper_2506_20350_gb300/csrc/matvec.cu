@@ -24,7 +24,7 @@
 namespace bttb {
 
 static int native_of(int prec) {
-    return prec == PREC_F64N ? FMT_C128 : ((prec == PREC_F32 || prec == PREC_TC) ? FMT_C64 : FMT_CDF);
+    return prec == PREC_F64N ? FMT_C128 : ((prec == PREC_F32 || is_tc_prec(prec)) ? FMT_C64 : FMT_CDF);
 }
 
 // Few columns.  ROUTE_FUSED_Y: the x pass, then the y-level transforms and the block product in one
@@ -38,7 +38,7 @@ static int native_of(int prec) {
 int product_route(Plan *p, int nrhs, int prec) {
     const bool few = nrhs <= kFusedFftMaxCols;
     const int fprec = fft_prec_of(prec);
-    const int yprec = prec == PREC_TC ? PREC_F32 : prec;        // below kTcMinCols the TC form is binary32
+    const int yprec = is_tc_prec(prec) ? PREC_F32 : prec;       // below kTcMinCols the TC forms are binary32
     const bool y_ok = few && (yprec == PREC_DF64 || yprec == PREC_F32) && ycontract_fits(p, yprec, nrhs);
     const bool f2_ok = few && fft2_fused_smem(p, fprec) <= p->smem_optin / 2;
     const bool pk_ok = few && product_persistent_fits(p, yprec, nrhs);
@@ -59,7 +59,7 @@ int matvec_run(Plan *p, const void *x, int xfmt, long ldx, void *y, int yfmt, lo
     const long plane = (long)ny * mx * b;
     int rc;
     const int route = product_route(p, nrhs, prec);
-    const int yprec = prec == PREC_TC ? PREC_F32 : prec;
+    const int yprec = is_tc_prec(prec) ? PREC_F32 : prec;
 
     if (route == ROUTE_PERSISTENT)
         return product_persistent_launch(p, x, xfmt, ldx, y, yfmt, ldy, nrhs, yprec, in_sel, in_sel_stride, in_scale,

@@ -110,10 +110,12 @@ def test_multi_rhs_product_binary32(bt, nx, ny, b, k):
 
 
 @pytest.mark.parametrize("nx,ny,b,k", [(5, 4, 60, 16), (6, 5, 60, 70), (4, 3, 64, 130), (7, 6, 12, 65),
-                                        (3, 5, 1, 33), (4, 4, 37, 20), (5, 3, 96, 40), (4, 4, 60, 9)])
+                                        (3, 5, 1, 33), (4, 4, 37, 20), (5, 3, 96, 40), (4, 4, 60, 9),
+                                        (3, 3, 2, 17), (4, 2, 30, 31), (6, 4, 24, 97)])
 def test_tensor_core_product(bt, nx, ny, b, k):
-    """BTTB_MV_TC_3XTF32: the per-bin GEMM on the tensor cores (3xTF32) for >= 16 columns and b <= 64,
-    binary32 elsewhere (b = 96, k = 9); binary32-level accuracy either way."""
+    """BTTB_MV_TC_3XTF32: the per-bin GEMM on the tensor cores (3xTF32) for >= 16 columns and b <= 64:
+    tcgen05 MMAs on TMA-fed tiles for even b (one to four K blocks of the 2b-row embedding, partial last
+    column tiles), warp-level MMAs for odd b; binary32 elsewhere (b = 96, k = 9); binary32-level accuracy."""
     gen = arrays.random_generator_blocks(nx, ny, b, seed=400 + b + k)
     plan = bt.Plan(nx, ny, b, max_rhs=k, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_TC_3XTF32))
     plan.set_generators(gen)
@@ -159,14 +161,17 @@ def test_product_every_fft_length(bt, nx):
     plan.close()
 
 
-def test_tensor_core_ir_solve(bt):
-    """GMRES-IR with tensor-core inner products reaches the FP64-class residual on every column."""
+@pytest.mark.parametrize("inner", ["tf32x3", "bf16x3"])
+def test_tensor_core_ir_solve(bt, inner):
+    """GMRES-IR with tensor-core inner products (3xTF32 and split-BF16x3) reaches the FP64-class residual on
+    every column."""
     nx, ny, b = 8, 6, 12
     gen = arrays.generator_blocks(nx, ny, b, seed=32)
     v = arrays.port_excitations(nx, ny, b).T.copy()          # 48 columns
-    plan = bt.Plan(nx, ny, b, max_rhs=v.shape[0], prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_TC_3XTF32))
+    pr = bt.BTTB_MV_TC_3XTF32 if inner == "tf32x3" else bt.BTTB_MV_TC_BF16X3
+    plan = bt.Plan(nx, ny, b, max_rhs=v.shape[0], prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << pr))
     plan.set_generators(gen)
-    sol, rc, res = plan.solve(_dev(v), tol=1e-8, restart=30, inner=bt.BTTB_MV_TC_3XTF32)
+    sol, rc, res = plan.solve(_dev(v), tol=1e-8, restart=30, inner=pr)
     assert rc == bt.BTTB_OK, bt.bttb_last_error()
     rr = oracle.relres(gen, v.T, sol.cpu().numpy().T)
     assert np.all(rr <= 1e-8), rr.max()
@@ -281,6 +286,50 @@ def test_product_routes(bt, route, nx, ny, b, k):
             ys[r] = (plan.matvec(_dev(x), prec=bt.BTTB_MV_FP64).cpu().numpy(),
                      plan.matvec(_dev(x.astype(np.complex64)), prec=bt.BTTB_MV_FP32).cpu().numpy())
         assert np.array_equal(ys[1][0], ys[4][0]) and np.array_equal(ys[1][1], ys[4][1])
+    plan.close()
+
+
+# split-BF16x3: each binary32 factor is h + l with h = bf16(x), l = bf16(x - h) (round to nearest), and the
+# product drops l*l' and the remainders x - h - l (each at most 2^-18 |x|): at most 3 * 2^-18 = 1.1e-5
+# relative per product term, and a sum of such terms with independent rounding has a norm-wise relative
+# error of about 2^-18 * sqrt(3) = 6.6e-6 -- inside the 1e-5 bar of the tensor-core products.
+BF16X3_TOL = 1e-5
+
+
+@pytest.mark.parametrize("nx,ny,b,k", [(5, 4, 60, 16), (6, 5, 60, 70), (4, 3, 64, 130), (7, 6, 12, 65),
+                                        (4, 2, 30, 31), (6, 4, 24, 97), (4, 4, 37, 20)])
+def test_tensor_core_bf16x3_product(bt, nx, ny, b, k):
+    """BTTB_MV_TC_BF16X3: the per-bin GEMM on the tcgen05 tensor cores in split-BF16x3 (kind::f16, bfloat16
+    operands, binary32 accumulation in tensor memory) for even b <= 64 and >= 16 columns; binary32 for odd b."""
+    gen = arrays.random_generator_blocks(nx, ny, b, seed=450 + b + k)
+    plan = bt.Plan(nx, ny, b, max_rhs=k, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_TC_BF16X3))
+    plan.set_generators(gen)
+    x = _rand(np.random.default_rng(18), k, plan.n)
+    ref = oracle.matvec(gen, x.T).T
+    y = plan.matvec(_dev(x.astype(np.complex64)), prec=bt.BTTB_MV_TC_BF16X3).cpu().numpy()
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert err <= BF16X3_TOL, err
+    assert np.abs(y - ref).max() <= 4 * BF16X3_TOL * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_tensor_core_all_ports_product_sampled(bt, prec):
+    """900 columns (every element's port excitation plus random amplitudes) of the 30x30, b=60 array through
+    the tensor-core per-bin GEMM: sampled columns against the oracle's O(N^2) product."""
+    c = arrays.CONFIGS["precision"]
+    nx, ny, b = c["nx"], c["ny"], c["b"]
+    gen = arrays.generator_blocks(nx, ny, b, c["seed"])
+    pr = bt.BTTB_MV_TC_3XTF32 if prec == "tf32x3" else bt.BTTB_MV_TC_BF16X3
+    k = nx * ny
+    plan = bt.Plan(nx, ny, b, max_rhs=k, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << pr))
+    plan.set_generators(gen)
+    rng = np.random.default_rng(19)
+    x = (rng.standard_normal((k, plan.n)) + 1j * rng.standard_normal((k, plan.n))).astype(np.complex64)
+    y = plan.matvec(_dev(x), prec=pr).cpu().numpy()
+    cols = [0, 1, 449, 898, 899]
+    ref = oracle.matvec(gen, x[cols].astype(np.complex128).T).T
+    err = np.linalg.norm(y[cols] - ref) / np.linalg.norm(ref)
+    assert err <= (FP32_TOL if prec == "tf32x3" else BF16X3_TOL), err
     plan.close()
 
 

@@ -610,8 +610,8 @@ def run_ours(args):
         kall = nx * ny
         vm = torch.from_numpy(arrays.port_excitations(nx, ny, b).T.copy()).to(dev)
         im = torch.zeros_like(vm)
-        planm = bt.Plan(nx, ny, b, max_rhs=kall, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_FP32),
-                        stream=stream)
+        planm = bt.Plan(nx, ny, b, max_rhs=kall, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_FP32) |
+                        (1 << bt.BTTB_MV_TC_3XTF32) | (1 << bt.BTTB_MV_TC_BF16X3), stream=stream)
         planm.set_generators(gen)
         torch.cuda.synchronize()
         width = planm.autotune(kall, 3)                       # FFT chunk width for 900-column products
@@ -675,6 +675,49 @@ def run_ours(args):
                                     "status_ok": sum(r.status == bt.BTTB_OK for r in resg),
                                     "relres_true_max": max(r.relres_true for r in resg),
                                     "speedup_vs_fp64_column_by_column": fp64_ms * kall / (gt * 1e3)}
+        # the per-bin GEMM of one 900-column product: binary32 FMA kernel vs the tcgen05 tensor-core kernel
+        # (3xTF32, split-BF16x3); CUDA events around the block-product launches, 5 products each
+        xm = torch.randn(kall, n, dtype=torch.complex64, device=dev)
+        ym = torch.empty_like(xm)
+        gemm = {}
+        for name, pr in (("fp32_fma", bt.BTTB_MV_FP32), ("tc_3xtf32", bt.BTTB_MV_TC_3XTF32),
+                         ("tc_bf16x3", bt.BTTB_MV_TC_BF16X3)):
+            with torch.cuda.stream(stream):
+                bt.bttb_matvec(planm.handle, xm, ym, kall, n, bt.BTTB_C64, pr)
+            torch.cuda.synchronize()
+            bt.bttb_profile(planm.handle, 1)
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                for _ in range(5):
+                    bt.bttb_matvec(planm.handle, xm, ym, kall, n, bt.BTTB_C64, pr)
+            torch.cuda.synchronize()
+            wall = (time.perf_counter() - t0) / 5
+            bt.bttb_profile(planm.handle, 0)
+            st_ = bt.bttb_profile_read(planm.handle, bt.BTTB_K_BLOCK_PRODUCT_PREC + pr)
+            gemm[name] = {"block_product_ms": st_.ms / max(st_.launches, 1), "product_ms": wall * 1e3,
+                          "algorithmic_gbs": st_.bytes / (st_.ms / 1e3) / 1e9 if st_.ms > 0 else None,
+                          "useful_tflops": 8.0 * mx * my * b * b * kall / (st_.ms / max(st_.launches, 1) / 1e3) / 1e12
+                          if st_.ms > 0 else None}
+        multi["per_bin_gemm_900_columns"] = gemm
+        del xm, ym
+        # the all-ports solve with tensor-core inner products (the batched per-column GMRES-IR)
+        for name, pr in (("tc_3xtf32_ir", bt.BTTB_MV_TC_3XTF32), ("tc_bf16x3_ir", bt.BTTB_MV_TC_BF16X3)):
+            with torch.cuda.stream(stream):
+                planm.solve(vm, im, tol=tol, restart=restart, inner=pr, max_iters=2)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                im.zero_()
+                _, rct, rest = planm.solve(vm, im, tol=tol, restart=restart, inner=pr)
+            torch.cuda.synchronize()
+            tt = time.perf_counter() - t0
+            tco = oracle_relres_sampled(gen, vm_h, im.cpu().numpy().T, cols)
+            multi[name] = {"solve_ms": tt * 1e3, "status_ok": sum(r.status == bt.BTTB_OK for r in rest),
+                           "iters_max": max(r.iters for r in rest),
+                           "relres_true_max": max(r.relres_true for r in rest),
+                           "oracle_relres_max_sampled": max(tco),
+                           "speedup_vs_fp32_ir": mt / tt,
+                           "speedup_vs_fp64_column_by_column": fp64_ms * kall / (tt * 1e3)}
         del vm, im
         planm.close()
         torch.cuda.empty_cache()

@@ -674,6 +674,7 @@ struct DcgsArgs {
     int m, k;
     int dot_sub, nblk_dot, ich, nblk_vec;
     int cmajor;           // 1: a CTA covers its chunks for every vector (u, x read once; many columns)
+    int vgrp;             // vector-major: basis vectors per CTA
     int dsm_last;         // float4 slots of dynamic shared memory used by the last CTA (stages follow)
     float4 *part;
     long pstride;
@@ -710,10 +711,10 @@ __device__ __forceinline__ dacc warp_reduce_scatter4(dacc a, dacc b, dacc c, dac
     return k;
 }
 
-// CM: the chunk-major layout (a.cmajor), a separate instance so that the vector-major one keeps its
-// smaller register count (three CTAs per SM; the chunk-major one holds u and x in registers: two).
+// CM: the chunk-major layout (a.cmajor), a separate instance (the chunk-major one holds u and x in
+// registers).  Both are sized for two CTAs per SM, the vector-major grid's target.
 template <bool CM>
-__global__ void __launch_bounds__(kDotIW * 32, CM ? 2 : 3) dcgs_dots_kernel(const DcgsArgs a, int j, int has_x) {
+__global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArgs a, int j, int has_x) {
     extern __shared__ __align__(16) float4 dsm[];      // s, t: 2(m+1); Givens scratch 4m+4; Hs: m+1; partials
     const int c = blockIdx.y;
     pdl_wait();
@@ -812,11 +813,14 @@ __global__ void __launch_bounds__(kDotIW * 32, CM ? 2 : 3) dcgs_dots_kernel(cons
                 for (int d = waited + 1; d <= issued; ++d) mbar_wait_drain(&bar[d & 1], (uint32_t)(d >> 1) & 1u);
         }
     } else {
-        // vector-major: CTA (vector i, group cb of kDotIW chunks); warp w takes chunk cb*kDotIW + w.  The CTAs
-        // of one chunk group are adjacent (i fastest), so they run together and share u and x through L2
-        const int cb = blockIdx.x / (j + 1), i = blockIdx.x - cb * (j + 1);
+        // vector-major: CTA (group vg of a.vgrp vectors, group cb of kDotIW chunks); warp w takes chunk
+        // cb*kDotIW + w of each vector of its group in turn, so u and x come from L1 after the first one and
+        // the grid stays within about one wave.  The CTAs of one chunk group are adjacent (vg fastest).
+        const int ngrp = (j + 1 + a.vgrp - 1) / a.vgrp;
+        const int cb = blockIdx.x / ngrp, vg = blockIdx.x - cb * ngrp;
         const int blk = cb * kDotIW + warp;
         __shared__ dacc cred[kDotIW][4];
+        for (int i = vg * a.vgrp; i < min(j + 1, (vg + 1) * a.vgrp); ++i) {
         dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
         if (i <= j && blk < a.nblk_dot) {
             // i < j: (q_i, u) and (q_i, x); i == j: (u, u) and (u, x)
@@ -871,6 +875,8 @@ __global__ void __launch_bounds__(kDotIW * 32, CM ? 2 : 3) dcgs_dots_kernel(cons
         if (threadIdx.x == 0 && i <= j) {
             part[(long)i * cpv + cb] = make_float4(cred[0][0].S, cred[0][1].S, cred[0][0].s, cred[0][1].s);
             part[(long)(a.m + 1 + i) * cpv + cb] = make_float4(cred[0][2].S, cred[0][3].S, cred[0][2].s, cred[0][3].s);
+        }
+        __syncthreads();                                  // cred is reused by the group's next vector
         }
     }
     pdl_trigger();
@@ -1031,7 +1037,7 @@ __global__ void __launch_bounds__(kDotIW * 32, CM ? 2 : 3) dcgs_dots_kernel(cons
 // q_j = (u_j - Q s)/nu and u_{j+1} = (x - Q t - q_j c_j)/nu, one entry per thread, the basis
 // entries loaded UB at a time and shared by both sums.
 template <int UB>
-__global__ void __launch_bounds__(kStepNB) dcgs_update_kernel(const DcgsArgs a, int j) {
+__global__ void __launch_bounds__(kStepNB, 2) dcgs_update_kernel(const DcgsArgs a, int j) {
     extern __shared__ __align__(16) float4 csm[];        // -s: j entries, -c: j+1 entries; Givens scratch
     const int c = blockIdx.y, blk = blockIdx.x;
     pdl_wait();
@@ -1359,7 +1365,11 @@ static DcgsArgs dcgs_args(Plan *p, GmresWork *g, int j) {
         // many columns of one-piece chunks: each CTA covers all vectors of its chunk group and keeps u and x
         // in registers; otherwise a CTA per (vector, chunk group) for parallelism
         a.cmajor = a.dot_sub == 1 && cpv * g->k >= 2L * p->nsm;
-        a.ich = (int)(a.cmajor ? cpv : cpv * (j + 1));
+        // vector-major: enough vectors per CTA that the grid is about two CTAs per SM
+        const long want = 2L * p->nsm;
+        const long tot = cpv * (long)(j + 1) * g->k;
+        a.vgrp = a.cmajor ? 1 : (int)std::max<long>(1, std::min<long>(j + 1, (tot + want - 1) / want));
+        a.ich = (int)(a.cmajor ? cpv : cpv * ((j + 1 + a.vgrp - 1) / a.vgrp));
     }
     a.dsm_last = 7 * g->m + 7 + kDotIW * 32 + g->m + 1;
     a.nblk_vec = g->nblk;

@@ -418,6 +418,9 @@ def learned_leg(dev, stream):
     base = res["plain_fp64"]["solve_ms"]
     for v in res.values():
         v["speedup_vs_plain_fp64"] = base / v["solve_ms"]
+    # what the network must save to pay back its pairs and training: solves of 50 excitations until the
+    # learned IR solve's saving over block-Jacobi IR covers them
+    saved_ms = res["block_jacobi_ir"]["solve_ms"] - res["learned_ir"]["solve_ms"]
     bt.bttb_plan_set_learned(plan.handle, None)
     out = {"workload": f"{nx}x{ny} b={b}, N={n}, grid {plan.mx}x{plan.my}; {c['ntest']} held-out random "
                        f"port excitations (seed {c['test_seed']}) to {tol:g}",
@@ -427,6 +430,8 @@ def learned_leg(dev, stream):
            "train_steps": steps, "batch": batch, "lr": lr, "train_s": train_s,
            "train_ms_per_step": train_s * 1e3 / steps, "loss_train_before": loss0, "loss_train_after": loss1,
            "loss_heldout_first_residual": lrn2, "apply_ms_50_columns": apply_ms,
+           "amortised_s": pairs_s + train_s, "saved_ms_per_solve_vs_block_jacobi_ir": saved_ms,
+           "break_even_solves": (pairs_s + train_s) * 1e3 / saved_ms if saved_ms > 0 else None,
            "solves": res, "leg_s": time.perf_counter() - t_all}
     lrn.close()
     plan.close()

@@ -656,7 +656,12 @@ __global__ void __launch_bounds__(kStepNB) step_scale_kernel(const StepArgs a, i
 // are c = [t; (tau - s^H t)/nu], the preliminary column j is (c - H s)/nu, and
 //   u_{j+1} = (x - Q_{j-1} t - q_j c_j)/nu.
 // The update writes q_j and u_{j+1} in one pass over the basis.  A closing
-// reduction without x finalises the last column of the cycle.
+// reduction without x finalises the last column of the cycle.  t (and tau) are
+// first-pass Gram-Schmidt coefficients: the reduction forms them in binary32,
+// and the next step's reorthogonalisation s, formed in double-float like alpha
+// and like the update itself, measures and removes what they miss (the closed
+// Hessenberg column is the coefficients used plus that correction), so the
+// Arnoldi relation holds to double-float accuracy.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ df warp_sum_df(df v) {
 #pragma unroll
@@ -786,18 +791,20 @@ __global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArg
 #pragma unroll
                     for (int r = 0; r < kDotPL; ++r) q[r] = u[r];
                 }
-                dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
+                dacc sr{0.f, 0.f}, si{0.f, 0.f};
+                float ftr = 0.f, fti = 0.f;
 #pragma unroll
                 for (int r = 0; r < kDotPL; ++r) {
                     dacc_mac(sr, q[r].x, q[r].z, u[r].x, u[r].z);
                     dacc_mac(sr, q[r].y, q[r].w, u[r].y, u[r].w);
                     dacc_mac(si, q[r].x, q[r].z, u[r].y, u[r].w);
                     dacc_mac(si, -q[r].y, -q[r].w, u[r].x, u[r].z);
-                    dacc_mac(tr, q[r].x, q[r].z, x[r].x, x[r].z);
-                    dacc_mac(tr, q[r].y, q[r].w, x[r].y, x[r].w);
-                    dacc_mac(ti, q[r].x, q[r].z, x[r].y, x[r].w);
-                    dacc_mac(ti, -q[r].y, -q[r].w, x[r].x, x[r].z);
+                    ftr = fmaf(q[r].x, x[r].x, ftr);             // t: first-pass coefficients, binary32
+                    ftr = fmaf(q[r].y, x[r].y, ftr);
+                    fti = fmaf(q[r].x, x[r].y, fti);
+                    fti = fmaf(-q[r].y, x[r].x, fti);
                 }
+                dacc tr{ftr, 0.f}, ti{fti, 0.f};
                 // every lane has read stage i&1 before lane 0 refills it (next step)
                 __syncwarp();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -839,18 +846,21 @@ __global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArg
                     u[r] = in ? uv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
                     x[r] = in && has_x ? xv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
+                float ftr = 0.f, fti = 0.f;
     #pragma unroll
                 for (int r = 0; r < kDotPL; ++r) {
-                    // conj(q) u and conj(q) x, compensated
+                    // conj(q) u compensated; conj(q) x (first-pass coefficients t) in binary32
                     dacc_mac(sr, q[r].x, q[r].z, u[r].x, u[r].z);
                     dacc_mac(sr, q[r].y, q[r].w, u[r].y, u[r].w);
                     dacc_mac(si, q[r].x, q[r].z, u[r].y, u[r].w);
                     dacc_mac(si, -q[r].y, -q[r].w, u[r].x, u[r].z);
-                    dacc_mac(tr, q[r].x, q[r].z, x[r].x, x[r].z);
-                    dacc_mac(tr, q[r].y, q[r].w, x[r].y, x[r].w);
-                    dacc_mac(ti, q[r].x, q[r].z, x[r].y, x[r].w);
-                    dacc_mac(ti, -q[r].y, -q[r].w, x[r].x, x[r].z);
+                    ftr = fmaf(q[r].x, x[r].x, ftr);
+                    ftr = fmaf(q[r].y, x[r].y, ftr);
+                    fti = fmaf(q[r].x, x[r].y, fti);
+                    fti = fmaf(-q[r].y, x[r].x, fti);
                 }
+                dacc_add(tr, dacc{ftr, 0.f});
+                dacc_add(ti, dacc{fti, 0.f});
             }
             warp_reduce_dacc(sr);
             warp_reduce_dacc(si);
@@ -965,6 +975,7 @@ __global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArg
         if (has_x && tt >= 0 && tt < R * G) {
             const int r = tt % R, gq = tt / R;
             dfc acc{df{0.f, 0.f}, df{0.f, 0.f}};
+#pragma unroll 4
             for (int q = max(r - 1, 0) + ((gq - max(r - 1, 0) % G) % G + G) % G; q < j; q += G)
                 acc = dfc_add(acc, dfc_mul(dfc_load(*reinterpret_cast<const cdf *>(&Hoc[(long)q * (m + 1) + r])),
                                            dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));

@@ -456,7 +456,7 @@ def run_ours(args):
     all_prec = (1 << bt.BTTB_MV_FP64) | (1 << bt.BTTB_MV_FP32) | (1 << bt.BTTB_MV_FP64_NATIVE)
     plan = bt.Plan(nx, ny, b, max_rhs=1, prec_mask=all_prec, stream=stream)
     plan.set_generators(gen)
-    fft_width = plan.autotune(1, 10)          # FFT batch-chunk width for one-column products
+    fft_width = plan.autotune(1, 10)          # product form and FFT batch-chunk width for one-column products
     n, mx, my = plan.n, plan.mx, plan.my
     v_host = arrays.centre_excitation(nx, ny, b)[None, :].copy()
     V = torch.from_numpy(v_host).to(dev)
@@ -593,8 +593,9 @@ def run_ours(args):
             else:
                 entry.setdefault("by_route", {})[route_names[route]] = rec
         mv[name] = entry
-    bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, 0)
+    plan.autotune(1, 10)                      # the sweep forced each form: restore the tuned ones
     ir_route = route_names[bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_ROUTE_TAKEN, (bt.BTTB_MV_FP32 << 8) | 1)]
+    df_route = route_names[bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_ROUTE_TAKEN, (bt.BTTB_MV_FP64 << 8) | 1)]
 
     # per-kernel breakdown of one host-driven IR solve (CUDA events around every launch)
     bt.bttb_profile(plan.handle, True)
@@ -833,7 +834,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32 products + df64 (double-float) residual/Arnoldi",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "b": b, "grid": [mx, my], "seed": c["seed"],
-                   "fft_chunk_width": fft_width,
+                   "fft_chunk_width": fft_width, "product_forms": {"fp32": ir_route, "fp64": df_route},
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: every product streams the 104-207 MB spectrum"},
         "roofline": roofline,

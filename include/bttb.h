@@ -284,10 +284,11 @@ int bttb_batch_plan(bttb_batch batch, int index, bttb_plan *out);
 int bttb_batch_set_generators(bttb_batch batch, int index, const void *gen, bttb_dtype dtype, int gen_is_host);
 /*
  * Autotuner: for every distinct FFT grid and block size (mx, my, b) in the
- * batch, time `reps` one-column binary32 products with each FFT batch-chunk
- * width in {2, 4, 8, 16, 32, 64} on the array's stream and keep the fastest for every array
- * of that shape.  chosen_out (host, count entries, may be NULL) receives the
- * width per array.  Needs the generators of the arrays to tune.
+ * batch, tune one array of that shape as bttb_plan_autotune does for one
+ * column (the form of the product and the FFT batch-chunk width, forms that
+ * do not apply to plans in a batch left out) and give every array of that
+ * shape the result.  chosen_out (host, count entries, may be NULL) receives
+ * the width per array.  Needs the generators of the arrays to tune.
  */
 int bttb_batch_autotune(bttb_batch batch, int reps, int *chosen_out);
 /*
@@ -353,12 +354,16 @@ int bttb_plan_set_learned(bttb_plan plan, bttb_learned l);
 int bttb_learned_destroy(bttb_learned l);
 
 /*
- * Autotuner for one plan: times `reps` binary32 products of `nrhs` columns
- * with each FFT batch-chunk width in {2, 4, 8, 16, 32, 64} on the plan's
- * stream and keeps the fastest for every later call of the plan (all
- * precisions; the width only changes the launch shape, not the result).
- * chosen_out (host, may be NULL) receives it.  Needs the generators; frees
- * the plan's GMRES workspace (it is rebuilt on the next solve).
+ * Autotuner for one plan: times `reps` binary32 products of `nrhs` columns in
+ * every form that applies (the forms of BTTB_DEBUG_PRODUCT_ROUTE; with the
+ * strided passes and the fused level-2 kernel, each FFT batch-chunk width in
+ * {2, 4, 8, 16, 32, 64}) on the plan's stream and keeps the fastest form and
+ * width for every later call of the plan; then, if the plan keeps the
+ * double-float spectrum, the fastest form of the double-float product.
+ * Forms and widths change the launch shapes only; every one gives the
+ * product to its precision's tolerance.  chosen_out (host, may be NULL)
+ * receives the width.  Needs the generators; frees the plan's GMRES
+ * workspace (it is rebuilt on the next solve).
  */
 int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out);
 

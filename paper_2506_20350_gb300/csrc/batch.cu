@@ -2,9 +2,10 @@
 // right-hand sides).  Every array has its own plan on its own CUDA stream;
 // a batch solve runs the arrays' restarted-GMRES drivers concurrently (one
 // host thread per array), so the GPU executes the arrays' captured cycle
-// graphs side by side.  An autotuner picks, per distinct (mx, my, b), the FFT
-// batch-chunk width by timing binary32 products on the plan's stream (the
-// same tuner serves single plans through bttb_plan_autotune).
+// graphs side by side.  An autotuner picks, per distinct (mx, my, b), the form
+// of the product and the FFT batch-chunk width by timing products on the
+// plan's stream (the same tuner serves single plans through
+// bttb_plan_autotune).
 #include <algorithm>
 #include <map>
 #include <string>
@@ -79,12 +80,29 @@ int bttb_batch_set_generators(bttb_batch batch, int index, const void *gen, bttb
     return bttb_set_generators(batch->plans[index], gen, dtype, gen_is_host);
 }
 
-// Times `reps` binary32 products of `nrhs` columns with each FFT batch-chunk
-// width and leaves the fastest in p.fft_pmax; returns it (or a negative status).
+// Times `reps` products of `nrhs` columns of precision `prec` on the plan's stream (after one warm-up).
+static float time_products(Plan &p, void *x, void *y, int nrhs, int prec, int reps, cudaEvent_t e0, cudaEvent_t e1) {
+    const int fmt = prec == PREC_F32 ? FMT_C64 : FMT_C128;
+    if (matvec_run(&p, x, fmt, p.n, y, fmt, p.n, nrhs, prec) != BTTB_OK) return 1e30f;
+    cudaEventRecord(e0, p.stream);
+    for (int r = 0; r < reps; ++r)
+        if (matvec_run(&p, x, fmt, p.n, y, fmt, p.n, nrhs, prec) != BTTB_OK) return 1e30f;
+    cudaEventRecord(e1, p.stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+}
+
+// Autotuner: for products of `nrhs` columns, times every form of the product that applies to the plan
+// (ROUTE_PASSES with each FFT batch-chunk width in {2, 4, ..., 64}; the fused two-level FFT; the fused
+// level-2 kernel with each width of its level-1 passes; the persistent kernel) in binary32 and keeps the
+// fastest form and width; then times the forms of the double-float product (FP64 plans) with that width
+// and keeps the fastest.  Returns the width (or a negative status).
 static int autotune_plan(Plan &p, int nrhs, int reps) {
-    const int candidates[6] = {2, 4, 8, 16, 32, 64};
+    const int widths[6] = {2, 4, 8, 16, 32, 64};
     void *x = nullptr, *y = nullptr;
-    const size_t bytes = (size_t)nrhs * p.n * sizeof(float2);
+    const size_t bytes = (size_t)nrhs * p.n * sizeof(double2);
     cudaError_t e = cudaMalloc(&x, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&y, bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, bytes, p.stream);
@@ -97,29 +115,45 @@ static int autotune_plan(Plan &p, int nrhs, int reps) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
-    int best_p = p.fft_pmax;
-    for (int cand : candidates) {
-        p.fft_pmax = cand;
-        matvec_run(&p, x, FMT_C64, p.n, y, FMT_C64, p.n, nrhs, PREC_F32);        // warm
-        cudaEventRecord(e0, p.stream);
-        for (int r = 0; r < reps; ++r) matvec_run(&p, x, FMT_C64, p.n, y, FMT_C64, p.n, nrhs, PREC_F32);
-        cudaEventRecord(e1, p.stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-            best_ms = ms;
-            best_p = cand;
+    int best_w = p.fft_pmax, best_r = ROUTE_PASSES;
+    for (int route : {ROUTE_PASSES, ROUTE_FUSED_FFT2, ROUTE_FUSED_Y, ROUTE_PERSISTENT}) {
+        p.route_f32 = route;
+        if (product_route(&p, nrhs, PREC_F32) != route) continue;          // this form does not apply here
+        const bool uses_width = route == ROUTE_PASSES || route == ROUTE_FUSED_Y;
+        for (int w : widths) {
+            if (!uses_width && w != widths[0]) break;
+            p.fft_pmax = w;
+            const float ms = time_products(p, x, y, nrhs, PREC_F32, reps, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_w = w;
+                best_r = route;
+            }
         }
     }
-    p.fft_pmax = best_p;
+    p.fft_pmax = best_w;
+    p.route_f32 = best_r;
+    if (p.ghat_lo) {                                                     // the double-float product's form
+        float best_df = 1e30f;
+        int best_rd = ROUTE_AUTO;
+        for (int route : {ROUTE_PASSES, ROUTE_FUSED_FFT2, ROUTE_FUSED_Y, ROUTE_PERSISTENT}) {
+            p.route_df = route;
+            if (product_route(&p, nrhs, PREC_DF64) != route) continue;
+            const float ms = time_products(p, x, y, nrhs, PREC_DF64, reps, e0, e1);
+            if (ms < best_df) {
+                best_df = ms;
+                best_rd = route;
+            }
+        }
+        p.route_df = best_rd;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(x);
     cudaFree(y);
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(&p, e, "autotune");
-    return best_p;
+    return best_w;
 }
 
 int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out) {
@@ -137,7 +171,7 @@ int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out) {
 int bttb_batch_autotune(bttb_batch batch, int reps, int *chosen_out) {
     if (!batch) return set_error(nullptr, BTTB_ERR_INVALID_ARG, "batch is NULL");
     if (reps < 1) reps = 1;
-    std::map<std::tuple<int, int, int>, int> best;
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> best;   // shape -> (width, tuned plan)
     for (int i = 0; i < batch->count; ++i) {
         Plan &p = batch->plans[i]->p;
         if (!p.have_gen || !p.ghat_hi) continue;
@@ -145,14 +179,20 @@ int bttb_batch_autotune(bttb_batch batch, int reps, int *chosen_out) {
         if (best.count(key)) continue;
         const int r = autotune_plan(p, 1, reps);
         if (r < 0) return r;
-        best[key] = r;
+        best[key] = std::make_pair(r, i);
+        gmres_free(&p);
     }
     for (int i = 0; i < batch->count; ++i) {
         Plan &p = batch->plans[i]->p;
         const auto it = best.find(std::make_tuple(p.mx, p.my, p.b));
-        if (it != best.end() && it->second != p.fft_pmax) {
-            p.fft_pmax = it->second;
-            gmres_free(&p);
+        if (it != best.end()) {
+            const Plan &src = batch->plans[it->second.second]->p;
+            if (it->second.first != p.fft_pmax || src.route_f32 != p.route_f32 || src.route_df != p.route_df) {
+                p.fft_pmax = it->second.first;
+                p.route_f32 = src.route_f32;
+                p.route_df = src.route_df;
+                gmres_free(&p);
+            }
         }
         if (chosen_out) chosen_out[i] = p.fft_pmax;
     }

@@ -363,7 +363,7 @@ int bttb_plan_debug(bttb_plan plan, int what, long long value) {
             return BTTB_OK;
         case BTTB_DEBUG_PRODUCT_ROUTE:
             if (value < 0 || value > 4) return set_error(&p, BTTB_ERR_INVALID_ARG, "route must be in [0, 4]");
-            p.route = (int)value;
+            p.route_f32 = p.route_df = (int)value;
             gmres_free(&p);                           // captured cycles hold the old route
             return BTTB_OK;
         case BTTB_DEBUG_ROUTE_TAKEN: {

@@ -108,7 +108,8 @@ struct Plan {
     // coming uncaptured one-to-eight-column block products that withhold one mbarrier arrival.
     unsigned long long wait_ns = 2000000000ull;
     int withhold = 0;
-    int route = ROUTE_AUTO;       // form of the few-column product
+    int route_f32 = ROUTE_AUTO;   // form of the few-column binary32 / tensor-core product (autotuned or forced)
+    int route_df = ROUTE_AUTO;    // form of the few-column double-float / binary64 product
     YcShape yc[2][4];             // fused y-level product shapes: [binary32, double-float][columns - 1]
     int yc_force_q = 0;           // cluster size of the fused y-level product (0: the largest resident one)
 

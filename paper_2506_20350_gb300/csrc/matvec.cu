@@ -42,7 +42,7 @@ int product_route(Plan *p, int nrhs, int prec) {
     const bool y_ok = few && (yprec == PREC_DF64 || yprec == PREC_F32) && ycontract_fits(p, yprec, nrhs);
     const bool f2_ok = few && fft2_fused_smem(p, fprec) <= p->smem_optin / 2;
     const bool pk_ok = few && product_persistent_fits(p, yprec, nrhs);
-    int route = p->route;
+    int route = (prec == PREC_DF64 || prec == PREC_F64N) ? p->route_df : p->route_f32;
     if (route == ROUTE_PERSISTENT && !pk_ok) route = ROUTE_AUTO;
     if (route == ROUTE_FUSED_Y && !y_ok) route = ROUTE_AUTO;
     if (route == ROUTE_FUSED_FFT2 && !f2_ok) route = ROUTE_AUTO;

@@ -355,13 +355,13 @@ int bttb_learned_destroy(bttb_learned l);
 
 /*
  * Autotuner for one plan: times `reps` binary32 products of `nrhs` columns in
- * every form that applies (the forms of BTTB_DEBUG_PRODUCT_ROUTE; with the
- * strided passes and the fused level-2 kernel, each FFT batch-chunk width in
- * {2, 4, 8, 16, 32, 64}) on the plan's stream and keeps the fastest form and
- * width for every later call of the plan; then, if the plan keeps the
- * double-float spectrum, the fastest form of the double-float product.
- * Forms and widths change the launch shapes only; every one gives the
- * product to its precision's tolerance.  chosen_out (host, may be NULL)
+ * every form that applies and gives the same bits (forms 1, 2 and 4 of
+ * BTTB_DEBUG_PRODUCT_ROUTE; with the strided passes, each FFT batch-chunk
+ * width in {2, 4, 8, 16, 32, 64}) on the plan's stream and keeps the fastest
+ * form and width for every later call of the plan; then, if the plan keeps
+ * the double-float spectrum, the fastest of those forms of the double-float
+ * product.  They change the launch shapes only, not the result.
+ * chosen_out (host, may be NULL)
  * receives the width.  Needs the generators; frees the plan's GMRES
  * workspace (it is rebuilt on the next solve).
  */

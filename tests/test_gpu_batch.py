@@ -71,7 +71,7 @@ def test_autotune_keeps_results(bt):
     after, rc, _ = batch.solve(vs, tol=1e-9, restart=20, inner=bt.BTTB_MV_FP32)
     assert rc == bt.BTTB_OK
     for a, c in zip(before, after):
-        assert torch.equal(a, c)          # the chunk width changes scheduling, not arithmetic
+        assert torch.equal(a, c)          # the tuned form and chunk width change scheduling, not arithmetic
     batch.close()
 
 

@@ -32,7 +32,7 @@ struct GmresWork {
     int *act_prod = nullptr;      // per product column copy of the global column's active flag
     bool dcgs = false;            // delayed CGS2 (unpreconditioned cycles) instead of CGS2
     float4 *U = nullptr;          // delayed CGS2: the not yet reorthogonalised vector u_j [k][n]
-    float4 *cco = nullptr, *hpre = nullptr;   // [k][m+1]: update coefficients, preliminary column
+    float4 *cco = nullptr, *hpre = nullptr;   // [k][m+1]: update coefficients; [2][k][m+1] preliminary column
     float4 *Horig = nullptr;      // [k][(m+1)*m] Hessenberg columns before the rotations
     bool flex = false;            // Zb allocated
     int pc = BTTB_PC_NONE;        // preconditioner of the current solve
@@ -680,6 +680,7 @@ struct DcgsArgs {
     int dot_sub, nblk_dot, ich, nblk_vec;
     int cmajor;           // 1: a CTA covers its chunks for every vector (u, x read once; many columns)
     int vgrp;             // vector-major: basis vectors per CTA
+    int fused;            // vector-major: the update kernel's CTAs sum the partials and close the column
     int dsm_last;         // float4 slots of dynamic shared memory used by the last CTA (stages follow)
     float4 *part;
     long pstride;
@@ -714,6 +715,209 @@ __device__ __forceinline__ dacc warp_reduce_scatter4(dacc a, dacc b, dacc c, dac
     for (int off = 4; off > 0; off >>= 1)
         dacc_add(k, dacc{__shfl_xor_sync(0xffffffffu, k.S, off), __shfl_xor_sync(0xffffffffu, k.s, off)});
     return k;
+}
+
+// Roles of the closing work of a delayed-CGS2 step (dcgs_tail).
+enum TailRole : int {
+    TAIL_LAST = 0,     // the reduction's last CTA: all of it (the update kernel then reads the coefficients)
+    TAIL_COEF = 1,     // an update CTA of the few-column layout: the coefficients s, t, c_j and 1/nu only
+    TAIL_HESS = 2,     // that layout's first extra update CTA: close column j-1, H s, the preliminary column j
+    TAIL_GIVENS = 3,   // its second extra update CTA: close column j-1 in shared memory, its Givens step
+};
+
+// The closing work of step j of column c once every partial sum is in `part` (npart per quantity; slot q
+// holds s_q for q <= j, slot m+1+q holds t_q): the sums, nu and s^H t, then per role c_j = (tau - s^H t)/nu,
+// the close of Hessenberg column j-1 (preliminary entries + s, subdiagonal nu), H s and the preliminary
+// column j, and the Givens step of column j-1.  Every role sums in the same order, so every CTA gets the
+// same bits.  The preliminary column is double-buffered by step parity (step j reads buffer (j-1) mod 2 and
+// writes buffer j mod 2), so the two extra CTAs of the few-column layout need no ordering between them.
+// Shared memory `dsm`: DcgsArgs::dsm_last float4 slots; on return s is at dsm[0..j-1] and t at
+// dsm[m+1..m+1+j] with t_j replaced by c_j.
+__device__ void dcgs_tail(const DcgsArgs &a, int c, int j, int has_x, int npart, const float4 *part, float4 *dsm,
+                          int role, df *nu_out, df *inu_out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = a.m;
+    float4 *ssm = dsm, *tsm = dsm + (m + 1);
+    float4 *gscr = dsm + 2 * (m + 1);
+    float4 *hs = gscr + (4 * m + 4);
+    // the 2(j+1) sums (s_q for q <= j, then t): T consecutive lanes per sum (a power of two up to 32, as
+    // many as the block's threads allow), lane t adding the partials t, t+T, ... in order (eight loads in
+    // flight; a partial past the end adds an exact zero), then a fixed xor tree over the T lanes
+    {
+        const int nsum = 2 * (j + 1);
+        int T = 1;
+        while (T < 32 && 2 * T * nsum <= (int)blockDim.x) T <<= 1;
+        const int spp = (int)blockDim.x / T, t = lane & (T - 1);
+        for (int q0 = 0; q0 < nsum; q0 += spp) {
+            const int q = q0 + (int)threadIdx.x / T;
+            dacc re{0.f, 0.f}, im{0.f, 0.f};
+            if (q < nsum) {
+                const float4 *pp = part + (long)(q <= j ? q : (m + 1) + (q - j - 1)) * npart;
+                for (int e = t; e < npart; e += 8 * T) {
+                    float4 v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        v[u] = e + u * T < npart ? __ldcg(pp + e + u * T) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        dacc_add(re, dacc{v[u].x, v[u].z});
+                        dacc_add(im, dacc{v[u].y, v[u].w});
+                    }
+                }
+            }
+            for (int off = T >> 1; off > 0; off >>= 1) {
+                const dacc ro{__shfl_xor_sync(0xffffffffu, re.S, off), __shfl_xor_sync(0xffffffffu, re.s, off)};
+                const dacc io{__shfl_xor_sync(0xffffffffu, im.S, off), __shfl_xor_sync(0xffffffffu, im.s, off)};
+                dacc_add(re, ro);
+                dacc_add(im, io);
+            }
+            if (t == 0 && q < nsum) {
+                const df r = dacc_result(re), z = dacc_result(im);
+                (q <= j ? ssm[q] : tsm[q - j - 1]) = make_float4(r.hi, z.hi, r.lo, z.lo);
+            }
+        }
+    }
+    __syncthreads();
+    // nu^2 = alpha - |s|^2 (alpha = u^H u is the real part of slot j) by warp 0, and
+    // s^H t for c_j by warp 1, each a strided sum and a fixed-order warp reduction
+    __shared__ float4 s_nu;                               // {nu.hi, 1/nu.hi, nu.lo, 1/nu.lo}
+    __shared__ float4 s_sht;                              // s^H t
+    if (warp == 0) {
+        df acc{0.f, 0.f};
+        for (int q = lane; q < j; q += 32) acc = df_add(acc, dfc_abs2(dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
+        acc = warp_sum_df(acc);
+        if (lane == 0) {
+            df nu2 = df_sub(df{ssm[j].x, ssm[j].z}, acc);
+            if (!(nu2.hi > 0.f)) nu2 = df{0.f, 0.f};
+            const df nu = df_sqrt(nu2);
+            const df inu = nu.hi > 0.f ? df_recip(nu) : df{0.f, 0.f};
+            s_nu = make_float4(nu.hi, inu.hi, nu.lo, inu.lo);
+        }
+    } else if (warp == 1 && has_x && role != TAIL_GIVENS) {
+        dfc acc{df{0.f, 0.f}, df{0.f, 0.f}};
+        for (int q = lane; q < j; q += 32)
+            acc = dfc_add(acc, dfc_mul(dfc_conj(dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))),
+                                       dfc_load(*reinterpret_cast<const cdf *>(&tsm[q]))));
+        acc = warp_sum_dfc(acc);
+        if (lane == 0) {
+            const cdf st = dfc_store(acc);
+            s_sht = make_float4(st.rh, st.ih, st.rl, st.il);
+        }
+    }
+    __syncthreads();
+    const df nu{s_nu.x, s_nu.z}, inu{s_nu.y, s_nu.w};
+    *nu_out = nu;
+    *inu_out = inu;
+    // c_j = (tau - s^H t)/nu in place of t_j
+    auto put_cj = [&]() {
+        const dfc cj = dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&tsm[j])),
+                               dfc_load(*reinterpret_cast<const cdf *>(&s_sht)));
+        const cdf st = dfc_store(dfc_scale(cj, inu));
+        tsm[j] = make_float4(st.rh, st.ih, st.rl, st.il);
+    };
+    if (role == TAIL_COEF) {
+        if (threadIdx.x == 0 && has_x) put_cj();
+        __syncthreads();
+        return;
+    }
+    const float4 *hp = a.hpre + ((long)((j + 1) & 1) * a.k + c) * (m + 1);   // step j-1's preliminary column
+    float4 *hw = a.hpre + ((long)(j & 1) * a.k + c) * (m + 1);               // this step's
+    float4 *Hoc = a.Horig + (long)c * (m + 1) * m;
+    if (role == TAIL_GIVENS) {
+        // the closed column j-1 in shared memory only, then its Givens step by warp 0
+        if (j >= 1) {
+            float4 *fc = hs;
+            for (int q = threadIdx.x; q < j; q += blockDim.x) {
+                const cdf st = dfc_store(dfc_add(dfc_load(*reinterpret_cast<const cdf *>(&hp[q])),
+                                                 dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
+                fc[q] = make_float4(st.rh, st.ih, st.rl, st.il);
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const int cont = givens_column(c, j - 1, m, gscr, a.H, fc, df_to_double(df_mul(nu, nu)), a.cs, a.sn,
+                                               a.gv, a.active, a.steps, a.bdown, a.mlimit, a.target, nullptr, a.err);
+                if (lane == 0 && cont) atomicMax(a.d_any_step, j + 1);
+            }
+        } else if (threadIdx.x == 0) {
+            atomicMax(a.d_any_step, 1);
+        }
+        return;
+    }
+    // H s (rows 0..j) from the unrotated columns 0..j-1 (column q has rows 0..q+1): thread (row r, group g)
+    // sums the columns q = g, g+G, ... of row r; the G partial sums of a row are added in group order after
+    const int R = j + 1;
+    const int G = max(1, min(j, (int)blockDim.x / R));   // no more groups than columns
+    float4 *hpart = hs + (m + 1);                         // R*G partial sums (hs itself holds column j-1 first)
+    auto hs_partials = [&]() {
+        const int tt = (int)threadIdx.x;
+        if (tt < R * G) {
+            const int r = tt % R, gq = tt / R;
+            dfc acc{df{0.f, 0.f}, df{0.f, 0.f}};
+#pragma unroll 4
+            for (int q = max(r - 1, 0) + ((gq - max(r - 1, 0) % G) % G + G) % G; q < j; q += G)
+                acc = dfc_add(acc, dfc_mul(dfc_load(*reinterpret_cast<const cdf *>(&Hoc[(long)q * (m + 1) + r])),
+                                           dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
+            const cdf st = dfc_store(acc);
+            hpart[gq * R + r] = make_float4(st.rh, st.ih, st.rl, st.il);
+        }
+        if (threadIdx.x == 0) put_cj();
+    };
+    if (j >= 1) {
+        // close column j-1: entries hpre + s (rows 0..j-1), subdiagonal nu
+        float4 *fc = hs;                                  // the closed column, rows 0..j-1
+        for (int q = threadIdx.x; q < j; q += blockDim.x) {
+            const cdf st = dfc_store(dfc_add(dfc_load(*reinterpret_cast<const cdf *>(&hp[q])),
+                                             dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
+            fc[q] = make_float4(st.rh, st.ih, st.rl, st.il);
+            Hoc[(long)(j - 1) * (m + 1) + q] = fc[q];
+        }
+        if (threadIdx.x == 0) Hoc[(long)(j - 1) * (m + 1) + j] = make_float4(nu.hi, 0.f, nu.lo, 0.f);
+        if (!has_x) {
+            // the cycle's last close (role TAIL_LAST): its Givens step here
+            __syncthreads();
+            if (warp == 0) {
+                const double nu2d = df_to_double(df_mul(nu, nu));
+                givens_column(c, j - 1, m, gscr, a.H, fc, nu2d, a.cs, a.sn, a.gv, a.active, a.steps, a.bdown,
+                              a.mlimit, a.target, a.inv_beta, a.err);
+            }
+            return;
+        }
+        if (role == TAIL_LAST) {
+            // the Givens step of column j-1 runs in the update kernel's extra CTA, beside the update
+            float4 *hc = a.hcol + (long)c * (m + 1);
+            for (int q = threadIdx.x; q < j; q += blockDim.x) hc[q] = fc[q];
+            if (threadIdx.x == 0) {
+                a.nu2[c] = df_to_double(df_mul(nu, nu));
+                a.inv_beta[c] = df_to_double(inu);
+            }
+        }
+        __syncthreads();
+        hs_partials();
+        __syncthreads();
+    } else {
+        if (threadIdx.x == 0) a.inv_beta[c] = df_to_double(inu);
+        if (!has_x) return;
+        hs_partials();
+        __syncthreads();
+    }
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        dfc acc = dfc_load(*reinterpret_cast<const cdf *>(&hpart[r]));
+        for (int gq = 1; gq < G; ++gq) acc = dfc_add(acc, dfc_load(*reinterpret_cast<const cdf *>(&hpart[gq * R + r])));
+        const cdf st = dfc_store(acc);
+        hs[r] = make_float4(st.rh, st.ih, st.rl, st.il);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r <= j; r += blockDim.x) {
+        const long o = (long)c * (m + 1) + r;
+        if (role == TAIL_LAST) {
+            if (r < j) a.sco[o] = ssm[r];
+            a.cco[o] = tsm[r];
+        }
+        const dfc hpj = dfc_scale(dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&tsm[r])),
+                                          dfc_load(*reinterpret_cast<const cdf *>(&hs[r]))), inu);
+        const cdf st = dfc_store(hpj);
+        hw[r] = make_float4(st.rh, st.ih, st.rl, st.il);
+    }
 }
 
 // CM: the chunk-major layout (a.cmajor), a separate instance (the chunk-major one holds u and x in
@@ -890,170 +1094,43 @@ __global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArg
         }
     }
     pdl_trigger();
+    // few-column layout: the update kernel closes the column (its CTAs sum the partials themselves)
+    if (a.fused && has_x) return;
     if (!arrive_last(a.cnt + c, (int)gridDim.x)) return;
-    // ---- last CTA of the column: sums in chunk order
-    const int m = a.m;
-    float4 *ssm = dsm, *tsm = dsm + (m + 1);
-    float4 *gscr = dsm + 2 * (m + 1);
-    float4 *hs = gscr + (4 * m + 4);
-    // sums q < 2(j+1) (s_q for q <= j, then t): warp w takes q = w, w+8, ...; for up to kSumB of its sums
-    // at a time a lane loads its partials of all of them before adding (same per-sum order as one at a time)
-    {
-        constexpr int kSumB = 4;
-        const int nsum = 2 * (j + 1);
-        for (int q0 = warp; q0 < nsum; q0 += kDotIW * kSumB) {
-            dacc re[kSumB], im[kSumB];
-#pragma unroll
-            for (int u = 0; u < kSumB; ++u) re[u] = im[u] = dacc{0.f, 0.f};
-            for (int e0 = lane; e0 < npart; e0 += 32) {
-                float4 v[kSumB];
-#pragma unroll
-                for (int u = 0; u < kSumB; ++u) {
-                    const int q = q0 + u * kDotIW;
-                    const int slot = q <= j ? q : (m + 1) + (q - j - 1);
-                    v[u] = q < nsum ? __ldcg(part + (long)slot * npart + e0) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < kSumB; ++u) {
-                    dacc_add(re[u], dacc{v[u].x, v[u].z});
-                    dacc_add(im[u], dacc{v[u].y, v[u].w});
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kSumB; ++u) {
-                warp_reduce_dacc(re[u]);
-                warp_reduce_dacc(im[u]);
-                const int q = q0 + u * kDotIW;
-                if (lane == 0 && q < nsum) {
-                    const df r = dacc_result(re[u]), z = dacc_result(im[u]);
-                    (q <= j ? ssm[q] : tsm[q - j - 1]) = make_float4(r.hi, z.hi, r.lo, z.lo);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    // nu^2 = alpha - |s|^2 (alpha = u^H u is the real part of slot j) by warp 0, and
-    // s^H t for c_j by warp 1, each a strided sum and a fixed-order warp reduction
-    __shared__ float4 s_nu;                               // {nu.hi, 1/nu.hi, nu.lo, 1/nu.lo}
-    __shared__ float4 s_sht;                              // s^H t
-    __shared__ int s_cont;
-    if (warp == 0) {
-        df acc{0.f, 0.f};
-        for (int q = lane; q < j; q += 32) acc = df_add(acc, dfc_abs2(dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
-        acc = warp_sum_df(acc);
-        if (lane == 0) {
-            df nu2 = df_sub(df{ssm[j].x, ssm[j].z}, acc);
-            if (!(nu2.hi > 0.f)) nu2 = df{0.f, 0.f};
-            const df nu = df_sqrt(nu2);
-            const df inu = nu.hi > 0.f ? df_recip(nu) : df{0.f, 0.f};
-            s_nu = make_float4(nu.hi, inu.hi, nu.lo, inu.lo);
-        }
-    } else if (warp == 1 && has_x) {
-        dfc acc{df{0.f, 0.f}, df{0.f, 0.f}};
-        for (int q = lane; q < j; q += 32)
-            acc = dfc_add(acc, dfc_mul(dfc_conj(dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))),
-                                       dfc_load(*reinterpret_cast<const cdf *>(&tsm[q]))));
-        acc = warp_sum_dfc(acc);
-        if (lane == 0) {
-            const cdf st = dfc_store(acc);
-            s_sht = make_float4(st.rh, st.ih, st.rl, st.il);
-        }
-    }
-    __syncthreads();
-    const df nu{s_nu.x, s_nu.z}, inu{s_nu.y, s_nu.w};
-    float4 *Hoc = a.Horig + (long)c * (m + 1) * m;
-    // H s (rows 0..j) from the unrotated columns 0..j-1 (column q has rows 0..q+1) and c_j = (tau - s^H t)/nu
-    // do not depend on the Givens step of column j-1: warps 1.. compute them while warp 0 runs it (all
-    // warps when j = 0).  Thread (row r, group g) sums the columns q = g, g+G, ... of row r; the G partial
-    // sums of a row are added in group order afterwards.
-    const int R = j + 1;
-    const int hs_t0 = j >= 1 ? 32 : 0;
-    const int G = max(1, min(j, ((int)blockDim.x - hs_t0) / R));   // no more groups than columns
-    float4 *hpart = hs + (m + 1);                         // R*G partial sums (hs itself holds column j-1 first)
-    auto hs_partials = [&]() {
-        const int tt = (int)threadIdx.x - hs_t0;
-        if (has_x && tt >= 0 && tt < R * G) {
-            const int r = tt % R, gq = tt / R;
-            dfc acc{df{0.f, 0.f}, df{0.f, 0.f}};
-#pragma unroll 4
-            for (int q = max(r - 1, 0) + ((gq - max(r - 1, 0) % G) % G + G) % G; q < j; q += G)
-                acc = dfc_add(acc, dfc_mul(dfc_load(*reinterpret_cast<const cdf *>(&Hoc[(long)q * (m + 1) + r])),
-                                           dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
-            const cdf st = dfc_store(acc);
-            hpart[gq * R + r] = make_float4(st.rh, st.ih, st.rl, st.il);
-        }
-        if (has_x && (int)threadIdx.x == hs_t0) {
-            const dfc cj = dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&tsm[j])),
-                                   dfc_load(*reinterpret_cast<const cdf *>(&s_sht)));
-            const cdf st = dfc_store(dfc_scale(cj, inu));
-            tsm[j] = make_float4(st.rh, st.ih, st.rl, st.il);
-        }
-    };
-    if (j >= 1) {
-        // close column j-1: entries hpre + s (rows 0..j-1), subdiagonal nu
-        float4 *fc = hs;                                  // the closed column, rows 0..j-1
-        const float4 *hp = a.hpre + (long)c * (m + 1);
-        for (int q = threadIdx.x; q < j; q += blockDim.x) {
-            const dfc v = dfc_add(dfc_load(*reinterpret_cast<const cdf *>(&hp[q])),
-                                  dfc_load(*reinterpret_cast<const cdf *>(&ssm[q])));
-            const cdf st = dfc_store(v);
-            fc[q] = make_float4(st.rh, st.ih, st.rl, st.il);
-            Hoc[(long)(j - 1) * (m + 1) + q] = fc[q];
-        }
-        if (threadIdx.x == 0) Hoc[(long)(j - 1) * (m + 1) + j] = make_float4(nu.hi, 0.f, nu.lo, 0.f);
-        if (has_x) {
-            // the Givens step of column j-1 runs in an extra CTA of the update kernel, beside the update
-            float4 *hc = a.hcol + (long)c * (m + 1);
-            for (int q = threadIdx.x; q < j; q += blockDim.x) hc[q] = fc[q];
-            if (threadIdx.x == 0) {
-                a.nu2[c] = df_to_double(df_mul(nu, nu));
-                a.inv_beta[c] = df_to_double(inu);
-            }
-            __syncthreads();
-            hs_partials();
-            __syncthreads();
-        } else {
-            __syncthreads();
-            if (warp == 0) {
-                const double nu2d = df_to_double(df_mul(nu, nu));
-                givens_column(c, j - 1, m, gscr, a.H, fc, nu2d, a.cs, a.sn, a.gv, a.active, a.steps, a.bdown,
-                              a.mlimit, a.target, a.inv_beta, a.err);
-            }
-            return;
-        }
-    } else {
-        if (threadIdx.x == 0) a.inv_beta[c] = df_to_double(inu);
-        hs_partials();
-        __syncthreads();
-    }
-    if (!has_x) return;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) {
-        dfc acc = dfc_load(*reinterpret_cast<const cdf *>(&hpart[r]));
-        for (int gq = 1; gq < G; ++gq) acc = dfc_add(acc, dfc_load(*reinterpret_cast<const cdf *>(&hpart[gq * R + r])));
-        const cdf st = dfc_store(acc);
-        hs[r] = make_float4(st.rh, st.ih, st.rl, st.il);
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r <= j; r += blockDim.x) {
-        const long o = (long)c * (m + 1) + r;
-        if (r < j) a.sco[o] = ssm[r];
-        a.cco[o] = tsm[r];
-        const dfc hp = dfc_scale(dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&tsm[r])),
-                                         dfc_load(*reinterpret_cast<const cdf *>(&hs[r]))), inu);
-        const cdf st = dfc_store(hp);
-        a.hpre[o] = make_float4(st.rh, st.ih, st.rl, st.il);
-    }
+    df nu_, inu_;
+    dcgs_tail(a, c, j, has_x, npart, part, dsm, TAIL_LAST, &nu_, &inu_);
 }
 
 // q_j = (u_j - Q s)/nu and u_{j+1} = (x - Q t - q_j c_j)/nu, one entry per thread, the basis
 // entries loaded UB at a time and shared by both sums.
+static_assert(kStepNB == kDotIW * 32, "the update kernel's CTAs run the reduction tail with its warp count");
 template <int UB>
 __global__ void __launch_bounds__(kStepNB, 2) dcgs_update_kernel(const DcgsArgs a, int j) {
     extern __shared__ __align__(16) float4 csm[];        // -s: j entries, -c: j+1 entries; Givens scratch
     const int c = blockIdx.y, blk = blockIdx.x;
     pdl_wait();
     if (!a.active[c]) return;
-    if (blk == a.nblk_vec) {
+    df inu_f{0.f, 0.f};
+    if (a.fused) {
+        // few-column layout: every CTA sums the column's partials itself (the same order everywhere, so
+        // every CTA gets the same coefficients); the two extra CTAs close column j-1 and write the
+        // preliminary column j, and run the Givens step of column j-1 -- both off the update's path
+        const int cpv = (a.nblk_dot + kDotIW - 1) / kDotIW;
+        const int role = blk < a.nblk_vec ? TAIL_COEF : blk == a.nblk_vec ? TAIL_HESS : TAIL_GIVENS;
+        df nu_;
+        dcgs_tail(a, c, j, 1, cpv, a.part + (long)c * a.pstride, csm, role, &nu_, &inu_f);
+        if (role != TAIL_COEF) return;
+        // -s and -c in place of s and t
+        for (int q = threadIdx.x; q <= j; q += blockDim.x) {
+            if (q < j) {
+                const float4 v = csm[q];
+                csm[q] = make_float4(-v.x, -v.y, -v.z, -v.w);
+            }
+            const float4 w = csm[a.m + 1 + q];
+            csm[a.m + 1 + q] = make_float4(-w.x, -w.y, -w.z, -w.w);
+        }
+        __syncthreads();
+    } else if (blk == a.nblk_vec) {
         // the extra CTA: Givens step of column j-1 (closed by the reduction), off the update's path
         if (j >= 1 && threadIdx.x < 32) {
             const int cont = givens_column(c, j - 1, a.m, csm, a.H, a.hcol + (long)c * (a.m + 1), a.nu2[c], a.cs,
@@ -1066,16 +1143,18 @@ __global__ void __launch_bounds__(kStepNB, 2) dcgs_update_kernel(const DcgsArgs 
         return;
     }
     float4 *sn_ = csm, *cn_ = csm + (a.m + 1);
-    for (int q = threadIdx.x; q <= j; q += blockDim.x) {
-        const long o = (long)c * (a.m + 1) + q;
-        if (q < j) {
-            const float4 v = a.sco[o];
-            sn_[q] = make_float4(-v.x, -v.y, -v.z, -v.w);
+    if (!a.fused) {
+        for (int q = threadIdx.x; q <= j; q += blockDim.x) {
+            const long o = (long)c * (a.m + 1) + q;
+            if (q < j) {
+                const float4 v = a.sco[o];
+                sn_[q] = make_float4(-v.x, -v.y, -v.z, -v.w);
+            }
+            const float4 w = a.cco[o];
+            cn_[q] = make_float4(-w.x, -w.y, -w.z, -w.w);
         }
-        const float4 w = a.cco[o];
-        cn_[q] = make_float4(-w.x, -w.y, -w.z, -w.w);
+        __syncthreads();
     }
-    __syncthreads();
     const long e = (long)blk * kStepNB + threadIdx.x;
     if (e < a.n) {
         const float4 u = a.U[(long)c * a.n + e], x = a.X[(long)c * a.n + e];
@@ -1101,7 +1180,7 @@ __global__ void __launch_bounds__(kStepNB, 2) dcgs_update_kernel(const DcgsArgs 
                 }
             }
         }
-        const df inu = df_from_double(a.inv_beta[c]);
+        const df inu = a.fused ? inu_f : df_from_double(a.inv_beta[c]);
         const df q0 = df_mul(dacc_result(qr), inu), q1 = df_mul(dacc_result(qi), inu);
         const float4 g = cn_[j];
         dacc_mac(xr, q0.hi, q0.lo, g.x, g.z);
@@ -1231,7 +1310,7 @@ static int ensure_work(Plan *p, int m, int k, long nv, int kp, bool flex, bool h
     alloc(&g->sn, sizeof(float4) * (size_t)k * m);
     alloc(&g->hco, sizeof(float4) * (size_t)k * (m + 1));
     alloc(&g->cco, sizeof(float4) * (size_t)k * (m + 1));
-    alloc(&g->hpre, sizeof(float4) * (size_t)k * (m + 1));
+    alloc(&g->hpre, sizeof(float4) * 2 * (size_t)k * (m + 1));   // two buffers, by step parity
     alloc(&g->Horig, sizeof(float4) * (size_t)k * (m + 1) * m);
     alloc(&g->U, sizeof(float4) * k * n);
     alloc(&g->ycoef, sizeof(float4) * (size_t)k * (m + 1));
@@ -1381,6 +1460,7 @@ static DcgsArgs dcgs_args(Plan *p, GmresWork *g, int j) {
         const long tot = cpv * (long)(j + 1) * g->k;
         a.vgrp = a.cmajor ? 1 : (int)std::max<long>(1, std::min<long>(j + 1, (tot + want - 1) / want));
         a.ich = (int)(a.cmajor ? cpv : cpv * ((j + 1 + a.vgrp - 1) / a.vgrp));
+        a.fused = a.cmajor ? 0 : 1;
     }
     a.dsm_last = 7 * g->m + 7 + kDotIW * 32 + g->m + 1;
     a.nblk_vec = g->nblk;
@@ -1409,23 +1489,29 @@ static DcgsArgs dcgs_args(Plan *p, GmresWork *g, int j) {
     return a;
 }
 
+// Dynamic shared memory above 48 KB needs the kernel's opt-in; the limit covers static and dynamic
+// shared memory together, so a restart length whose scratch does not fit is an argument error.
+template <typename K>
+static int dcgs_smem_optin(Plan *p, K kern, size_t smem, const char *what) {
+    if (smem <= 48 * 1024) return BTTB_OK;
+    cudaFuncAttributes fa{};
+    cudaError_t ea = cudaFuncGetAttributes(&fa, kern);
+    if (ea == cudaSuccess && smem + fa.sharedSizeBytes > p->smem_optin)
+        return set_error(p, BTTB_ERR_INVALID_ARG, "restart length too large for the delayed CGS2 shared memory");
+    if (ea == cudaSuccess)
+        ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(p->smem_optin - fa.sharedSizeBytes));
+    return ea == cudaSuccess ? BTTB_OK : check_cuda(p, ea, what);
+}
+
 static int dcgs_dots_launch(Plan *p, GmresWork *g, int j, int has_x) {
     const DcgsArgs a = dcgs_args(p, g, j);
     // last-CTA scratch, then (chunk-major) two basis stages per warp and their mbarriers
     const size_t smem = (size_t)a.dsm_last * sizeof(float4) +
                         (a.cmajor ? (size_t)kDotIW * 2 * kDotNE * sizeof(float4) + kDotIW * 2 * sizeof(uint64_t) : 0);
-    if (smem > 48 * 1024) {
-        // the opt-in limit covers static and dynamic shared memory together
-        cudaFuncAttributes fa{};
-        auto kern = a.cmajor ? dcgs_dots_kernel<true> : dcgs_dots_kernel<false>;
-        cudaError_t ea = cudaFuncGetAttributes(&fa, kern);
-        if (ea == cudaSuccess && smem + fa.sharedSizeBytes > p->smem_optin)
-            return set_error(p, BTTB_ERR_INVALID_ARG, "restart length too large for the reduction's shared memory");
-        if (ea == cudaSuccess)
-            ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(p->smem_optin - fa.sharedSizeBytes));
-        if (ea != cudaSuccess) return check_cuda(p, ea, "delayed CGS2 reduction shared memory");
-    }
+    int rc = a.cmajor ? dcgs_smem_optin(p, dcgs_dots_kernel<true>, smem, "delayed CGS2 reduction shared memory")
+                      : dcgs_smem_optin(p, dcgs_dots_kernel<false>, smem, "delayed CGS2 reduction shared memory");
+    if (rc != BTTB_OK) return rc;
     const int tok = prof_begin(p, 3);
     cudaError_t e = a.cmajor
         ? launch_pdl(dcgs_dots_kernel<true>, dim3(a.ich, g->k), dim3(kDotIW * 32), smem, p->stream, a, j, has_x)
@@ -1460,11 +1546,16 @@ static int arnoldi_step_dcgs(Plan *p, GmresWork *g, int inner, int j) {
     if (rc != BTTB_OK) return rc;
     if ((rc = dcgs_dots_launch(p, g, j, 1)) != BTTB_OK) return rc;
     const DcgsArgs a = dcgs_args(p, g, j);
-    const size_t smem = (size_t)std::max(2 * g->m + 2, 4 * g->m + 4) * sizeof(float4);   // coefficients / Givens
-    const dim3 vgrid(a.nblk_vec + 1, g->k);                                                // + the Givens CTA
+    // coefficients / Givens scratch; with the fused close, the reduction tail's scratch
+    const size_t smem = (size_t)(a.fused ? a.dsm_last : std::max(2 * g->m + 2, 4 * g->m + 4)) * sizeof(float4);
+    const dim3 vgrid(a.nblk_vec + (a.fused ? 2 : 1), g->k);   // + the Givens CTA (+ the Hessenberg CTA)
+    const bool wide = !p->in_batch && (long)a.nblk_vec * g->k < 4L * p->nsm;
+    rc = wide ? dcgs_smem_optin(p, dcgs_update_kernel<16>, smem, "delayed CGS2 update shared memory")
+              : dcgs_smem_optin(p, dcgs_update_kernel<4>, smem, "delayed CGS2 update shared memory");
+    if (rc != BTTB_OK) return rc;
     const int tok = prof_begin(p, 4);
     cudaError_t e;
-    if (!p->in_batch && (long)a.nblk_vec * g->k < 4L * p->nsm)
+    if (wide)
         e = launch_pdl(dcgs_update_kernel<16>, vgrid, dim3(kStepNB), smem, st, a, j);
     else
         e = launch_pdl(dcgs_update_kernel<4>, vgrid, dim3(kStepNB), smem, st, a, j);

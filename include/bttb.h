@@ -355,9 +355,10 @@ int bttb_learned_destroy(bttb_learned l);
 
 /*
  * Autotuner for one plan: times `reps` binary32 products of `nrhs` columns in
- * every form that applies and gives the same bits (forms 1, 2 and 4 of
- * BTTB_DEBUG_PRODUCT_ROUTE; with the strided passes, each FFT batch-chunk
- * width in {2, 4, 8, 16, 32, 64}) on the plan's stream and keeps the fastest
+ * every form that applies (forms 1 to 4 of BTTB_DEBUG_PRODUCT_ROUTE, which
+ * give the same bits; with forms 1 and 3, whose level-1 passes are strided,
+ * each FFT batch-chunk width in {2, 4, 8, 16, 32, 64}) on the plan's stream
+ * and keeps the fastest
  * form and width for every later call of the plan; then, if the plan keeps
  * the double-float spectrum, the fastest of those forms of the double-float
  * product.  They change the launch shapes only, not the result.
@@ -382,9 +383,10 @@ int bttb_plan_autotune(bttb_plan plan, int nrhs, int reps, int *chosen_out);
  *     passes around the block product; 2: the two-level FFT in one cluster
  *     kernel each way around the block product; 3: the level-1 passes around
  *     one cluster kernel that runs the level-2 transforms and the block
- *     product; 4: all five steps as phases of one persistent kernel (one CTA
- *     per SM, cooperative launch, bounded grid barriers; the same bits as 1).
- *     Forms 3 and 4 are double-float and binary32 only.  A form that does
+ *     product (b <= 128; b <= 64 for two to four columns); 4: all five steps
+ *     as phases of one persistent kernel (one CTA per SM, cooperative launch,
+ *     bounded grid barriers).  All four give the same bits.  Forms 3 and 4
+ *     are double-float and binary32 only.  A form that does
  *     not fit the plan falls back to the automatic choice.  Frees the GMRES
  *     workspace.
  *   BTTB_DEBUG_ROUTE_TAKEN (value = (prec << 8) | nrhs): returns the form

@@ -94,12 +94,11 @@ static float time_products(Plan &p, void *x, void *y, int nrhs, int prec, int re
     return ms;
 }
 
-// Autotuner: for products of `nrhs` columns, times every form of the product that applies to the plan and
-// gives the strided passes' bits (ROUTE_PASSES with each FFT batch-chunk width in {2, 4, ..., 64}; the
-// fused two-level FFT; the persistent kernel) in binary32 and keeps the fastest form and width; then times
-// those forms of the double-float product (FP64 plans) with that width and keeps the fastest.  (The fused
-// level-2 kernel sums a block product in another order; it is not a candidate.)  Returns the width (or a
-// negative status).
+// Autotuner: for products of `nrhs` columns, times every form of the product that applies to the plan (all
+// of them give the strided passes' bits): the strided passes and the fused level-2 kernel, whose x passes
+// are strided, with each FFT batch-chunk width in {2, 4, ..., 64}; the fused two-level FFT; the persistent
+// kernel; in binary32, and keeps the fastest form and width; then times those forms of the double-float
+// product (FP64 plans) with that width and keeps the fastest.  Returns the width (or a negative status).
 static int autotune_plan(Plan &p, int nrhs, int reps) {
     const int widths[6] = {2, 4, 8, 16, 32, 64};
     void *x = nullptr, *y = nullptr;
@@ -117,10 +116,10 @@ static int autotune_plan(Plan &p, int nrhs, int reps) {
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
     int best_w = p.fft_pmax, best_r = ROUTE_PASSES;
-    for (int route : {ROUTE_PASSES, ROUTE_FUSED_FFT2, ROUTE_PERSISTENT}) {
+    for (int route : {ROUTE_PASSES, ROUTE_FUSED_Y, ROUTE_FUSED_FFT2, ROUTE_PERSISTENT}) {
         p.route_f32 = route;
         if (product_route(&p, nrhs, PREC_F32) != route) continue;          // this form does not apply here
-        const bool uses_width = route == ROUTE_PASSES;
+        const bool uses_width = route == ROUTE_PASSES || route == ROUTE_FUSED_Y;
         for (int w : widths) {
             if (!uses_width && w != widths[0]) break;
             p.fft_pmax = w;
@@ -137,7 +136,7 @@ static int autotune_plan(Plan &p, int nrhs, int reps) {
     if (p.ghat_lo) {                                                     // the double-float product's form
         float best_df = 1e30f;
         int best_rd = ROUTE_AUTO;
-        for (int route : {ROUTE_PASSES, ROUTE_FUSED_FFT2, ROUTE_PERSISTENT}) {
+        for (int route : {ROUTE_PASSES, ROUTE_FUSED_Y, ROUTE_FUSED_FFT2, ROUTE_PERSISTENT}) {
             p.route_df = route;
             if (product_route(&p, nrhs, PREC_DF64) != route) continue;
             const float ms = time_products(p, x, y, nrhs, PREC_DF64, reps, e0, e1);

@@ -66,9 +66,8 @@ struct Learned;
 // count: cluster size, shares, ring, shared-memory offsets.  ok < 0: not decided yet, 0: does not fit.
 struct YcShape {
     int ok = -1;
-    int Q = 0, pshare = 0, kshare = 0, RH = 0, G = 0, Qc = 0, nchunks = 0, nstages = 0;
-    unsigned stage_bytes = 0, off_g1 = 0, off_tw = 0, off_f0 = 0, off_f1 = 0, off_uh = 0, off_red = 0,
-             off_ring = 0;
+    int Q = 0, pshare = 0, kshare = 0, Qc = 0, nchunks = 0, nstages = 0, nfix = 0;
+    unsigned stage_bytes = 0, off_g1 = 0, off_tw = 0, off_f0 = 0, off_f1 = 0, off_uh = 0, off_ring = 0;
     size_t smem = 0;
 };
 

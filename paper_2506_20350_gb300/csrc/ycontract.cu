@@ -10,18 +10,21 @@
 //   1. loads U[c][iy][kx][p] for p in P_r, iy < ny (the x pass's output), leaves rows iy >= ny zero
 //      (Eq. (xc2)) and transforms along iy: Stockham stages in shared memory;
 //   2. sends bin ky of its bases to the CTA that owns ky, through distributed shared memory;
-//   3. forms v_k = G_k u_k for its bins.  The spectrum blocks (column-major, the binary32 planes the
-//      precision reads) stream through a ring of shared-memory stages: one producer warp issues
-//      cp.async.bulk copies, an mbarrier per stage counts the bytes in and another counts the consumer
-//      warps out.  The spectrum does not depend on the preceding pass, so the first stages are issued
-//      before the programmatic-dependent-launch wait and land while the x pass drains and step 1-2 run.
-//      The eight consumer warps split a block's rows into 32-row blocks (one row per lane) and its
-//      columns q into groups; one reduction over the groups, in group order, ends each bin;
+//   3. forms v_k = G_k u_k for its bins, one warp per bin: lane l accumulates the rows l R .. l R + R - 1
+//      over every column of the block, so a bin needs no reduction across warps.  Each warp streams its
+//      bins' spectrum blocks (column-major chunks, the binary32 planes the precision reads) through a
+//      private ring of shared-memory stages: lane 0 issues cp.async.bulk copies, an mbarrier per stage
+//      counts the bytes in.  The spectrum does not depend on the x pass, so every warp fills the stages
+//      of its ring that lie in the ring area before the programmatic-dependent-launch wait, and those
+//      copies land while the x pass drains and steps 1-2 run; the y-transform buffers, free from the end
+//      of step 2 to the start of step 4, hold the ring's other stages.  The per-lane accumulation is the
+//      one of the block-product kernel (contract.cu), so the product has the bits of the strided-pass
+//      route;
 //   4. sends v_k of each basis back to the CTA that owns the basis;
 //   5. transforms along ky (inverse, unnormalised: the 1/(mx my) is in the spectrum), keeps iy < ny and
 //      stores V[c][iy][kx][p] for the inverse x pass.
-// Every wait is bounded; a wait that runs out sets the plan's error word, the CTA stops computing but
-// keeps taking part in the cluster barriers, and the producer drains its copies in flight before exit.
+// Every wait is bounded; a wait that runs out sets the plan's error word, the warp stops computing but
+// the CTA keeps taking part in the cluster barriers, and every copy in flight is drained before exit.
 #include <algorithm>
 
 #include <cooperative_groups.h>
@@ -34,9 +37,10 @@
 
 namespace bttb {
 
-constexpr int kYcConsumerWarps = 8;
-constexpr int kYcThreads = (kYcConsumerWarps + 1) * 32;     // eight consumer warps + the producer warp
-constexpr int kYcMaxStages = 8;
+constexpr int kYcWarps = 8;
+constexpr int kYcThreads = kYcWarps * 32;
+constexpr int kYcMaxStages = 8;                              // ring depth per warp
+constexpr uint32_t kYcHead = 8u * kYcWarps * kYcMaxStages;   // mbarriers, then the abort flag
 
 struct YcArgs {
     const void *U;                // x-pass output [c][iy][kx][p] (native format)
@@ -47,21 +51,24 @@ struct YcArgs {
     const int *active;            // per-column flags of this group (may be null)
     int nx, ny, mx, my, b, kc;    // kc: columns of this launch
     int Q, pshare, kshare;        // cluster size, bases and bins per CTA (the last CTA may hold fewer)
-    int RH, G;                    // 32-row blocks of a spectrum block, column groups (RH * G <= 8 warps)
-    int Qc, nchunks, nstages;     // spectrum columns per stage, stages per bin, ring depth
+    int Qc, nchunks, nstages;     // spectrum columns per stage, stages per bin, ring depth per warp
+    int nfix;                     // stages per warp in the ring area (the rest in the y-transform buffers)
     uint32_t stage_bytes, off_g1; // bytes of one stage; offset of its low-plane part
-    uint32_t off_tw, off_f0, off_f1, off_uh, off_red, off_ring;
+    uint32_t off_tw, off_f0, off_f1, off_uh, off_ring;
     Fft2Side sy;
     const void *twy;
     int *err;
     unsigned long long wait_ns;
-    int withhold;                 // test hook: CTA 0 withholds the arrival of its first stage
+    int withhold;                 // test hook: warp 0 of CTA 0 withholds the arrival of its first stage
 };
 
 __host__ __device__ constexpr uint32_t yc_align(uint32_t x) { return (x + 127u) & ~127u; }
+__host__ __device__ constexpr uint32_t yc_round16(uint32_t x) { return (x + 15u) & ~15u; }
 
-template <class A, int KC>
-__global__ void __launch_bounds__(kYcThreads) ycontract_kernel(const YcArgs a) {
+// KC: columns per launch (compile time, kc <= KC); R: rows per lane (b <= 32 R); VEC: R = 2 with b even,
+// row pairs loaded as one 16-byte word.
+template <class A, int KC, int R, bool VEC>
+__global__ void __launch_bounds__(kYcThreads, 2) ycontract_kernel(const YcArgs a) {
     namespace cg = cooperative_groups;
     using C = typename A::C;
     using GT = typename GElem<A>::T;
@@ -71,58 +78,56 @@ __global__ void __launch_bounds__(kYcThreads) ycontract_kernel(const YcArgs a) {
     const int r = (int)cl.block_rank();
     const int kx = blockIdx.x / a.Q;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool producer = warp == kYcConsumerWarps;
     const int b = a.b, my = a.my, kc = a.kc, S = a.nstages;
 
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + kYcMaxStages;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 16 * kYcMaxStages);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem) + warp * kYcMaxStages;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kYcHead);
     C *tw = reinterpret_cast<C *>(smem + a.off_tw);
     C *F0 = reinterpret_cast<C *>(smem + a.off_f0);
     C *F1 = reinterpret_cast<C *>(smem + a.off_f1);
     C *Uh = reinterpret_cast<C *>(smem + a.off_uh);          // [kl][c][p]: u^ of my bins, then v^
-    Acc<A> *red = reinterpret_cast<Acc<A> *>(smem + a.off_red);
-    unsigned char *ring = smem + a.off_ring;
+    // stage s of this warp: the first nfix in the ring area, the others in the y-transform buffers
+    // [off_f0, off_uh), which hold no live data during step 3
+    auto stage = [&](int s) -> unsigned char * {
+        return s < a.nfix ? smem + a.off_ring + ((size_t)warp * a.nfix + s) * a.stage_bytes
+                          : smem + a.off_f0 + ((size_t)warp * (S - a.nfix) + (s - a.nfix)) * a.stage_bytes;
+    };
 
     // shares: bases [plo, plo+np), bins [klo, klo+nk) of rank r (and of any rank o)
     auto p_lo = [&](int o) { return min(b, o * a.pshare); };
     auto p_n = [&](int o) { return min(b, (o + 1) * a.pshare) - p_lo(o); };
     auto k_lo = [&](int o) { return min(my, o * a.kshare); };
-    auto k_n = [&](int o) { return min(my, (o + 1) * a.kshare) - k_lo(o); };
-    const int plo = p_lo(r), np = p_n(r), klo = k_lo(r), nk = k_n(r);
+    const int plo = p_lo(r), np = p_n(r), klo = k_lo(r), nk = min(my, (r + 1) * a.kshare) - klo;
     const int nseq = kc * np;                                 // sequences of this CTA's y transforms
-    const int items = nk * a.nchunks;                         // spectrum stages of this CTA
+    // this warp's bins: kl = warp, warp + kYcWarps, ...; an item is one chunk of one of them
+    const int nbw = warp < nk ? (nk - 1 - warp) / kYcWarps + 1 : 0;
+    const int nitems = nbw * a.nchunks;
 
-    if (threadIdx.x == 0) {
-        *abort_flag = 0;
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kYcConsumerWarps);
-        }
+    if (threadIdx.x == 0) *abort_flag = 0;
+    if (lane == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
 
     const uint64_t pol_stream = l2_policy_evict_first();
-    const bool withheld0 = a.withhold && blockIdx.x == 0;
+    const bool withheld0 = a.withhold && blockIdx.x == 0 && warp == 0;
     auto issue = [&](int it) {
         const int s = it % S;
-        const int kl = it / a.nchunks, ch = it % a.nchunks;
+        const int kl = warp + kYcWarps * (it / a.nchunks), ch = it % a.nchunks;
         const int q0 = ch * a.Qc, qn = min(a.Qc, b - q0);
-        const uint32_t gbytes = (uint32_t)((qn * b * (int)sizeof(GT) + 15) & ~15);
-        const long bin = (long)(klo + kl) * a.mx + kx;
-        const long goff = bin * a.gbs + (long)q0 * b;
-        unsigned char *st = ring + (size_t)s * a.stage_bytes;
+        const uint32_t gbytes = yc_round16((uint32_t)(qn * b) * (uint32_t)sizeof(GT));
+        const long goff = ((long)(klo + kl) * a.mx + kx) * a.gbs + (long)q0 * b;
+        unsigned char *st = stage(s);
         if (withheld0 && it == 0) mbar_expect_tx(&full[s], gbytes * NPL);
         else mbar_arrive_expect_tx(&full[s], gbytes * NPL);
         bulk_g2s(st, reinterpret_cast<const GT *>(a.g0) + goff, gbytes, &full[s], pol_stream);
         if (NPL == 2) bulk_g2s(st + a.off_g1, reinterpret_cast<const GT *>(a.g1) + goff, gbytes, &full[s], pol_stream);
     };
-    // the spectrum does not depend on the x pass: fill the ring before the dependency wait
-    int issued = 0;
-    if (producer && lane == 0)
-        for (; issued < min(S, items); ++issued) issue(issued);
-    __syncwarp();
+    // the spectrum does not depend on the x pass: fill the ring area's stages before the dependency wait
+    const int npre = min(a.nfix, nitems);
+    if (lane == 0)
+        for (int it = 0; it < npre; ++it) issue(it);
     for (int i = threadIdx.x; i < my + 5; i += blockDim.x) tw[i] = reinterpret_cast<const C *>(a.twy)[i];
     // every CTA of the cluster must have started before another writes into its shared memory: arrive
     // now, wait before the first exchange
@@ -135,6 +140,7 @@ __global__ void __launch_bounds__(kYcThreads) ycontract_kernel(const YcArgs a) {
         for (int c = 0; c < kc; ++c) any |= a.active[c] != 0;
     }
     bool failed = false;
+    int it = 0;                                               // this warp's first item not consumed
     if (any) {
         // ---- 1. load this CTA's bases of column kx and transform along iy
         const long ucol = (long)kx * b + plo;
@@ -156,79 +162,95 @@ __global__ void __launch_bounds__(kYcThreads) ycontract_kernel(const YcArgs a) {
             C *dst = cl.map_shared_rank(Uh, o);
             dst[(long)(ky - k_lo(o)) * kc * b + c * b + plo + pl] = R1[idx];
         }
+        // the y-transform buffers take bulk copies from here on (async proxy after these generic accesses)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         cl.sync();
+        if (lane == 0)
+            for (int i = npre; i < min(S, nitems); ++i) issue(i);
 
-        // ---- 3. block products of my bins
-        if (producer) {
-            if (lane == 0) {
-                for (; issued < items; ++issued) {
-                    const int s = issued % S;
-                    // the stage is free once every consumer warp released its previous item
-                    if (*abort_flag ||
-                        !mbar_wait_bounded(&empty[s], (uint32_t)((issued / S) - 1) & 1u, abort_flag, a.wait_ns))
-                        break;
-                    issue(issued);
-                }
+        // ---- 3. block products of my bins, one warp per bin
+        Acc<A> acc[KC][R];
+        const int p0 = lane * R;
+        for (; it < nitems; ++it) {
+            const int s = it % S;
+            const int kl = warp + kYcWarps * (it / a.nchunks), ch = it % a.nchunks;
+            // a wait that ran out (or saw another warp's abort) ends the warp's loop; uniform over the warp
+            const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(it / S) & 1u, abort_flag, a.wait_ns);
+            if (__any_sync(0xffffffffu, !ok)) {
+                failed = true;
+                break;
             }
-            __syncwarp();
-        } else {
-            const int rb = warp % a.RH, g = warp / a.RH;
-            const bool live = warp < a.RH * a.G;
-            const int prow = rb * 32 + lane;
-            const bool rowok = live && prow < b;
-            Acc<A> acc[KC];
-            int buf = 0;
-            for (int it = 0; it < items; ++it) {
-                const int s = it % S;
-                const int kl = it / a.nchunks, ch = it % a.nchunks;
-                if (!failed) {
-                    const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(it / S) & 1u, abort_flag, a.wait_ns);
-                    failed = __any_sync(0xffffffffu, !ok);
-                }
-                if (ch == 0) {
+            if (ch == 0) {
 #pragma unroll
-                    for (int c = 0; c < KC; ++c) acc[c].zero();
-                }
-                if (!failed) {
-                    if (rowok) {
-                        const int q0 = ch * a.Qc, qn = min(a.Qc, b - q0);
-                        const unsigned char *st = ring + (size_t)s * a.stage_bytes;
-                        const GT *gs0 = reinterpret_cast<const GT *>(st) + prow;
-                        const GT *gs1 = reinterpret_cast<const GT *>(st + a.off_g1) + prow;
-                        const C *us = Uh + (long)kl * kc * b + q0;
-                        for (int q = g; q < qn; q += a.G) {
-                            const GT gh = gs0[q * b];
-                            const GT gl = NPL == 2 ? gs1[q * b] : gh;
+                for (int c = 0; c < KC; ++c)
 #pragma unroll
-                            for (int c = 0; c < KC; ++c)
-                                if (c < kc) acc[c].mac(gh, gl, us[c * b + q]);
+                    for (int rr = 0; rr < R; ++rr) acc[c][rr].zero();
+            }
+            {
+                const int q0 = ch * a.Qc, qn = min(a.Qc, b - q0);
+                const unsigned char *st = stage(s);
+                const GT *gs0 = reinterpret_cast<const GT *>(st) + p0;
+                const GT *gs1 = reinterpret_cast<const GT *>(st + a.off_g1) + p0;
+                const C *us = Uh + (long)kl * kc * b + q0;
+                if (p0 < b) {
+#pragma unroll 2
+                    for (int q = 0; q < qn; ++q) {
+                        if constexpr (R == 2 && VEC) {
+                            using PV = typename Pair<GT>::V;
+                            const PV v0 = *reinterpret_cast<const PV *>(gs0 + q * b);
+                            const PV v1 = NPL == 2 ? *reinterpret_cast<const PV *>(gs1 + q * b) : v0;
+#pragma unroll
+                            for (int c = 0; c < KC; ++c) {
+                                if (c < kc) {
+                                    const C u = us[c * b + q];
+                                    acc[c][0].mac(Pair<GT>::lo(v0), Pair<GT>::lo(v1), u);
+                                    acc[c][1].mac(Pair<GT>::hi(v0), Pair<GT>::hi(v1), u);
+                                }
+                            }
+                        } else {
+                            GT v0[R], v1[R];
+#pragma unroll
+                            for (int rr = 0; rr < R; ++rr) {
+                                v0[rr] = p0 + rr < b ? gs0[q * b + rr] : GT{};
+                                v1[rr] = NPL == 2 && p0 + rr < b ? gs1[q * b + rr] : v0[rr];
+                            }
+#pragma unroll
+                            for (int c = 0; c < KC; ++c) {
+                                if (c < kc) {
+                                    const C u = us[c * b + q];
+#pragma unroll
+                                    for (int rr = 0; rr < R; ++rr) acc[c][rr].mac(v0[rr], v1[rr], u);
+                                }
+                            }
                         }
                     }
-                    // every lane has read stage s: release it to the producer
-                    __syncwarp();
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    if (lane == 0) mbar_arrive(&empty[s]);
-                }
-                if (ch == a.nchunks - 1) {
-                    // partial sums of the column groups, then their sum in group order: v_k of bin kl
-                    Acc<A> *rb_ = red + (long)buf * a.G * (a.RH * 32) * KC;
-                    if (rowok)
-#pragma unroll
-                        for (int c = 0; c < KC; ++c) rb_[((long)g * a.RH * 32 + prow) * KC + c] = acc[c];
-                    named_barrier_sync(1, kYcConsumerWarps * 32);
-                    for (int t = threadIdx.x; t < kc * b; t += kYcConsumerWarps * 32) {
-                        const int c = t / b, pr = t - c * b;
-                        Acc<A> sum = rb_[(long)pr * KC + c];
-                        for (int gg = 1; gg < a.G; ++gg) sum.merge(rb_[((long)gg * a.RH * 32 + pr) * KC + c]);
-                        Uh[(long)kl * kc * b + c * b + pr] = sum.result();   // u^ of bin kl is consumed
-                    }
-                    buf ^= 1;
                 }
             }
+            // every lane is done with stage s (and, at a bin's end, with u^ of the bin) before the stage is
+            // refilled and v^ overwrites u^
+            __syncwarp();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (ch == a.nchunks - 1) {
+#pragma unroll
+                for (int c = 0; c < KC; ++c)
+#pragma unroll
+                    for (int rr = 0; rr < R; ++rr)
+                        if (c < kc && p0 + rr < b) Uh[(long)kl * kc * b + c * b + p0 + rr] = acc[c][rr].result();
+            }
+            if (lane == 0 && it + S < nitems) issue(it + S);
         }
-        __syncthreads();
-        if (failed && lane == 0 && !producer) atomicOr(a.err, DEVERR_TIMEOUT);
-        // ---- 4. v_k of each basis to the CTA that owns the basis (its y buffers are free since step 2)
+        // a warp whose loop broke off drains its copies in flight (items it .. min(it + S, nitems) - 1, each
+        // in its own stage; every earlier item completed its phase; a withheld arrival is supplied first)
+        // before any CTA of the cluster writes into the y-transform buffers again
+        if (failed && lane == 0) {
+            atomicOr(a.err, DEVERR_TIMEOUT);
+            for (int d = it; d < min(it + S, nitems); ++d) {
+                if (withheld0 && d == 0) mbar_arrive(&full[d % S]);
+                mbar_wait_drain(&full[d % S], (uint32_t)(d / S) & 1u);
+            }
+        }
+        cl.sync();
+        // ---- 4. v_k of each basis to the CTA that owns the basis
         for (int idx = threadIdx.x; idx < nk * kc * b; idx += blockDim.x) {
             const int kl = idx / (kc * b), rem = idx - kl * kc * b;
             const int c = rem / b, pr = rem - c * b;
@@ -249,16 +271,13 @@ __global__ void __launch_bounds__(kYcThreads) ycontract_kernel(const YcArgs a) {
     } else {
         pdl_trigger();
     }
-    // copies that may still be in flight (a run-out wait, or no active column): the last min(S, issued)
-    // items, each in its own stage; a withheld arrival is supplied first
-    if (producer && lane == 0) {
-        if (*abort_flag || !any) {
-            for (int d = max(0, issued - S); d < issued; ++d) {
-                if (withheld0 && d == 0) mbar_arrive(&full[d % S]);
-                if (!mbar_wait_drain(&full[d % S], (uint32_t)(d / S) & 1u)) atomicOr(a.err, DEVERR_TIMEOUT);
-            }
+    // with no active column the prefetched copies are still in flight: let them land (a withheld arrival
+    // is supplied first) before the CTA's shared memory goes away
+    if (!any && lane == 0) {
+        for (int d = 0; d < npre; ++d) {
+            if (withheld0 && d == 0) mbar_arrive(&full[d]);
+            if (!mbar_wait_drain(&full[d], 0u)) atomicOr(a.err, DEVERR_TIMEOUT);
         }
-        if (*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT);
     }
 }
 
@@ -273,11 +292,8 @@ static bool yc_layout(const Plan *p, int kc, int Q, YcShape &y) {
     y.Q = Q;
     y.pshare = (b + Q - 1) / Q;
     y.kshare = (my + Q - 1) / Q;
-    y.RH = (b + 31) / 32;
-    if (y.RH > kYcConsumerWarps) return false;
-    y.G = kYcConsumerWarps / y.RH;
     const uint32_t ce = sizeof(C);
-    uint32_t off = 256;
+    uint32_t off = yc_align(kYcHead + 16);
     y.off_tw = off;
     off = yc_align(off + (uint32_t)(my + 8) * ce);
     const uint32_t fbytes = (uint32_t)my * kc * y.pshare * ce;
@@ -287,45 +303,58 @@ static bool yc_layout(const Plan *p, int kc, int Q, YcShape &y) {
     off = yc_align(off + fbytes);
     y.off_uh = off;
     off = yc_align(off + (uint32_t)y.kshare * kc * b * ce);
-    y.off_red = off;
-    off = yc_align(off + 2u * y.G * (y.RH * 32) * KC * (uint32_t)sizeof(Acc<A>));
     y.off_ring = off;
-    // ring: spectrum chunks of Qc columns, balanced over the block, about 16 KB a stage, 3..8 stages in
-    // what is left of a budget that lets two CTAs share an SM when the shares are small
+    // per-warp rings: the largest chunk of whole spectrum columns (16-byte aligned starts, balanced over the
+    // block) of which two stages per warp fit in what is left of a budget that lets two CTAs share an SM
+    // (if such a stage holds at least 3 KB), else of the whole opt-in limit; then as many stages of that
+    // size as fit there, plus those that fit in the y-transform buffers, kYcMaxStages at most
     const size_t optin = p->smem_optin > 0 ? (size_t)p->smem_optin : 227 * 1024;
     const size_t budget2 = (optin + 1024) / 2 - 1024;            // two CTAs (1 KB reserved each) per SM
-    const size_t budget1 = optin;
-    const size_t colb = (size_t)b * sizeof(GT) * NPL;              // one spectrum column, all planes
-    for (size_t budget : {budget2, budget1}) {
-        if (off + 3 * (colb + 256) > budget) continue;
-        const size_t ring_max = budget - off;
-        // balanced chunks of at most qc columns; with b odd a chunk that is not the whole block holds an
-        // even number of columns, so that every chunk starts on a 16-byte boundary
-        int qc = (int)std::min<size_t>((size_t)b, std::max<size_t>(1, (16 * 1024) / colb));
-        int nch = 0, ns = 0;
+    for (size_t budget : {budget2, optin}) {
+        if (off >= budget) continue;
+        const size_t per_warp = (budget - off) / kYcWarps;
+        int qc = b;
         for (; qc >= 1; --qc) {
-            nch = (b + qc - 1) / qc;
-            int q2 = (b + nch - 1) / nch;
-            if (b % 2 && q2 < b && q2 % 2) --q2;
-            if (q2 < 1) continue;
-            nch = (b + q2 - 1) / q2;
-            ns = (int)std::min<size_t>(kYcMaxStages, ring_max / (yc_align((uint32_t)(q2 * b * sizeof(GT))) * NPL));
-            if (ns >= 3) {
-                qc = q2;
-                break;
-            }
+            if (qc < b && (qc * b) % 2) continue;
+            if (2 * (size_t)yc_align((uint32_t)(qc * b * sizeof(GT))) * NPL <= per_warp) break;
         }
-        if (qc < 1 || ns < 3) continue;
-        y.Qc = qc;
-        y.nchunks = nch;
+        if (qc < 1) continue;
+        {
+            const int nch = (b + qc - 1) / qc;
+            int q2 = (b + nch - 1) / nch;
+            if (q2 < b && (q2 * b) % 2) ++q2;
+            if (q2 <= qc) qc = q2;
+        }
         const uint32_t pb = yc_align((uint32_t)(qc * b * sizeof(GT)));
+        const uint32_t stb = pb * NPL;
+        if (budget == budget2 && stb < 3072 && qc < b) continue;
+        const size_t nfix = std::min<size_t>(kYcMaxStages, per_warp / stb);
+        const size_t per_f = (size_t)(y.off_uh - y.off_f0) / kYcWarps / stb;
+        y.Qc = qc;
+        y.nchunks = (b + qc - 1) / qc;
         y.off_g1 = pb;
-        y.stage_bytes = pb * NPL;
-        y.nstages = (int)std::min<size_t>(kYcMaxStages, ring_max / y.stage_bytes);
-        y.smem = off + (size_t)y.nstages * y.stage_bytes;
+        y.stage_bytes = stb;
+        y.nfix = (int)nfix;
+        y.nstages = (int)std::min<size_t>(kYcMaxStages, nfix + per_f);
+        y.smem = off + (size_t)kYcWarps * nfix * stb;
         return true;
     }
     return false;
+}
+
+// The kernel instance for the plan's block size: rows per lane R = ceil(b/32) up to 4; four columns per
+// launch only with R <= 2 (at most eight accumulators per lane).
+using YcKernel = void (*)(YcArgs);
+template <class A, int KC>
+static YcKernel yc_kernel(int b) {
+    const int R = (b + 31) / 32;
+    if (R <= 1) return ycontract_kernel<A, KC, 1, false>;
+    if (R == 2) return b % 2 == 0 ? ycontract_kernel<A, KC, 2, true> : ycontract_kernel<A, KC, 2, false>;
+    if constexpr (KC == 1) {
+        if (R == 3) return ycontract_kernel<A, 1, 3, false>;
+        if (R == 4) return ycontract_kernel<A, 1, 4, false>;
+    }
+    return nullptr;
 }
 
 template <class A, int KC>
@@ -345,8 +374,9 @@ static cudaError_t yc_config(const Plan *p, const YcShape &y, cudaLaunchConfig_t
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     (void)ncols_groups;
-    return cudaFuncSetAttribute(ycontract_kernel<A, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)p->smem_optin);
+    const YcKernel kern = yc_kernel<A, KC>(p->b);
+    if (!kern) return cudaErrorInvalidConfiguration;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
 }
 
 // Largest cluster size whose mx clusters are all resident at once (the occupancy API decides), so that
@@ -365,7 +395,7 @@ static bool yc_choose(Plan *p, int kc, YcShape &out) {
             continue;
         }
         int nclus = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclus, ycontract_kernel<A, KC>, &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(&nclus, yc_kernel<A, KC>(p->b), &cfg) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -403,18 +433,16 @@ static int yc_launch(Plan *p, const void *U, void *V, int kc, const int *active,
     a.Q = y.Q;
     a.pshare = y.pshare;
     a.kshare = y.kshare;
-    a.RH = y.RH;
-    a.G = y.G;
     a.Qc = y.Qc;
     a.nchunks = y.nchunks;
     a.nstages = y.nstages;
+    a.nfix = y.nfix;
     a.stage_bytes = y.stage_bytes;
     a.off_g1 = y.off_g1;
     a.off_tw = y.off_tw;
     a.off_f0 = y.off_f0;
     a.off_f1 = y.off_f1;
     a.off_uh = y.off_uh;
-    a.off_red = y.off_red;
     a.off_ring = y.off_ring;
     const FftPlan &fy = p->fy.M == p->my ? p->fy : p->fx;
     Fft2Side sd;
@@ -447,7 +475,7 @@ static int yc_launch(Plan *p, const void *U, void *V, int kc, const int *active,
     cudaError_t e = yc_config<A, KC>(p, y, cfg, attr, 1);
     if (e != cudaSuccess) return check_cuda(p, e, "fused y-level product smem attribute");
     const int tok = prof_begin(p, BTTB_K_BLOCK_PRODUCT_PREC + (A::kind == 0 ? BTTB_MV_FP64 : BTTB_MV_FP32));
-    e = cudaLaunchKernelEx(&cfg, ycontract_kernel<A, KC>, a);
+    e = cudaLaunchKernelEx(&cfg, yc_kernel<A, KC>(p->b), a);
     count_launch(p);
     if (e != cudaSuccess) return check_cuda(p, e, "fused y-level product launch");
     // algorithmic bytes: the spectrum planes once, U in and V out (the intermediates stay on chip)
@@ -485,7 +513,7 @@ static int yc_probe(Plan *p, int k, int Q) {
         return -2;
     }
     int nclus = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclus, ycontract_kernel<A, KC>, &cfg);
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclus, yc_kernel<A, KC>(p->b), &cfg);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return -1000 - (int)e;
@@ -501,7 +529,7 @@ int ycontract_probe(Plan *p, int prec, int k, int Q) {
 }
 
 bool ycontract_fits(Plan *p, int prec, int k) {
-    if (k < 1 || k > 4 || p->b > 256) return false;
+    if (k < 1 || k > 4 || p->b > 128 || (k > 1 && p->b > 64)) return false;
     if (prec == PREC_DF64) return (k == 1 ? yc_shape<DF64, 1>(p, k) : yc_shape<DF64, 4>(p, k)).ok == 1;
     if (prec == PREC_F32) return (k == 1 ? yc_shape<F32, 1>(p, k) : yc_shape<F32, 4>(p, k)).ok == 1;
     return false;

@@ -432,6 +432,7 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter, int total) {
 // hco = h and adds h to hacc.
 constexpr int kDotNE = 256;
 constexpr int kDotIW = 8;
+constexpr int kDotVB = 8;        // vector-major reduction: vectors per shared-memory round
 constexpr int kDotPL = kDotNE / 32;         // entries per lane
 
 struct StepArgs {
@@ -1026,71 +1027,80 @@ __global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArg
     } else {
         // vector-major: CTA (group vg of a.vgrp vectors, group cb of kDotIW chunks); warp w takes chunk
         // cb*kDotIW + w of each vector of its group in turn, so u and x come from L1 after the first one and
-        // the grid stays within about one wave.  The CTAs of one chunk group are adjacent (vg fastest).
+        // the grid stays within about one wave.  The CTAs of one chunk group are adjacent (vg fastest).  The
+        // warps' sums of up to kDotVB vectors wait in shared memory for one barrier, after which the CTA's
+        // partials of those vectors are formed (warp order) together.
         const int ngrp = (j + 1 + a.vgrp - 1) / a.vgrp;
         const int cb = blockIdx.x / ngrp, vg = blockIdx.x - cb * ngrp;
         const int blk = cb * kDotIW + warp;
-        __shared__ dacc cred[kDotIW][4];
-        for (int i = vg * a.vgrp; i < min(j + 1, (vg + 1) * a.vgrp); ++i) {
-        dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
-        if (i <= j && blk < a.nblk_dot) {
-            // i < j: (q_i, u) and (q_i, x); i == j: (u, u) and (u, x)
-            const float4 *uv = a.U + (long)c * a.n;
-            const float4 *xv = a.X + (long)c * a.n;
-            const float4 *qv = i < j ? a.Vb + (long)i * a.bs_i + (long)c * a.bs_c : uv;
-            for (int sc = 0; sc < a.dot_sub; ++sc) {
-                const long n0 = ((long)blk * a.dot_sub + sc) * kDotNE;
-                const int len = (int)max(0L, min((long)kDotNE, a.n - n0));
-                float4 q[kDotPL], u[kDotPL], x[kDotPL];
-    #pragma unroll
-                for (int r = 0; r < kDotPL; ++r) {
-                    const int e = lane + 32 * r;
-                    const bool in = e < len;
-                    q[r] = in ? qv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    u[r] = in ? uv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    x[r] = in && has_x ? xv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int ilo = vg * a.vgrp, ihi = min(j + 1, (vg + 1) * a.vgrp);
+        __shared__ dacc cred[kDotVB][4][kDotIW];
+        for (int i0 = ilo; i0 < ihi; i0 += kDotVB) {
+            const int nb = min(kDotVB, ihi - i0);
+            for (int i = i0; i < i0 + nb; ++i) {
+                dacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
+                if (blk < a.nblk_dot) {
+                    // i < j: (q_i, u) and (q_i, x); i == j: (u, u) and (u, x)
+                    const float4 *uv = a.U + (long)c * a.n;
+                    const float4 *xv = a.X + (long)c * a.n;
+                    const float4 *qv = i < j ? a.Vb + (long)i * a.bs_i + (long)c * a.bs_c : uv;
+                    for (int sc = 0; sc < a.dot_sub; ++sc) {
+                        const long n0 = ((long)blk * a.dot_sub + sc) * kDotNE;
+                        const int len = (int)max(0L, min((long)kDotNE, a.n - n0));
+                        float4 q[kDotPL], u[kDotPL], x[kDotPL];
+#pragma unroll
+                        for (int r = 0; r < kDotPL; ++r) {
+                            const int e = lane + 32 * r;
+                            const bool in = e < len;
+                            q[r] = in ? qv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            u[r] = in ? uv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            x[r] = in && has_x ? xv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                        float ftr = 0.f, fti = 0.f;
+#pragma unroll
+                        for (int r = 0; r < kDotPL; ++r) {
+                            // conj(q) u compensated; conj(q) x (first-pass coefficients t) in binary32
+                            dacc_mac(sr, q[r].x, q[r].z, u[r].x, u[r].z);
+                            dacc_mac(sr, q[r].y, q[r].w, u[r].y, u[r].w);
+                            dacc_mac(si, q[r].x, q[r].z, u[r].y, u[r].w);
+                            dacc_mac(si, -q[r].y, -q[r].w, u[r].x, u[r].z);
+                            ftr = fmaf(q[r].x, x[r].x, ftr);
+                            ftr = fmaf(q[r].y, x[r].y, ftr);
+                            fti = fmaf(q[r].x, x[r].y, fti);
+                            fti = fmaf(-q[r].y, x[r].x, fti);
+                        }
+                        dacc_add(tr, dacc{ftr, 0.f});
+                        dacc_add(ti, dacc{fti, 0.f});
+                    }
+                    warp_reduce_dacc(sr);
+                    warp_reduce_dacc(si);
+                    warp_reduce_dacc(tr);
+                    warp_reduce_dacc(ti);
                 }
-                float ftr = 0.f, fti = 0.f;
-    #pragma unroll
-                for (int r = 0; r < kDotPL; ++r) {
-                    // conj(q) u compensated; conj(q) x (first-pass coefficients t) in binary32
-                    dacc_mac(sr, q[r].x, q[r].z, u[r].x, u[r].z);
-                    dacc_mac(sr, q[r].y, q[r].w, u[r].y, u[r].w);
-                    dacc_mac(si, q[r].x, q[r].z, u[r].y, u[r].w);
-                    dacc_mac(si, -q[r].y, -q[r].w, u[r].x, u[r].z);
-                    ftr = fmaf(q[r].x, x[r].x, ftr);
-                    ftr = fmaf(q[r].y, x[r].y, ftr);
-                    fti = fmaf(q[r].x, x[r].y, fti);
-                    fti = fmaf(-q[r].y, x[r].x, fti);
+                if (lane == 0) {
+                    cred[i - i0][0][warp] = sr;
+                    cred[i - i0][1][warp] = si;
+                    cred[i - i0][2][warp] = tr;
+                    cred[i - i0][3][warp] = ti;
                 }
-                dacc_add(tr, dacc{ftr, 0.f});
-                dacc_add(ti, dacc{fti, 0.f});
             }
-            warp_reduce_dacc(sr);
-            warp_reduce_dacc(si);
-            warp_reduce_dacc(tr);
-            warp_reduce_dacc(ti);
-        }
-        // the CTA's warps are summed in warp order into one partial per quantity
-        if (lane == 0) {
-            cred[warp][0] = sr;
-            cred[warp][1] = si;
-            cred[warp][2] = tr;
-            cred[warp][3] = ti;
-        }
-        __syncthreads();
-        if (threadIdx.x < 4 && i <= j) {
-            dacc acc = cred[0][threadIdx.x];
-            for (int w = 1; w < kDotIW; ++w) dacc_add(acc, cred[w][threadIdx.x]);
-            const df r = dacc_result(acc);
-            cred[0][threadIdx.x] = dacc{r.hi, r.lo};
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && i <= j) {
-            part[(long)i * cpv + cb] = make_float4(cred[0][0].S, cred[0][1].S, cred[0][0].s, cred[0][1].s);
-            part[(long)(a.m + 1 + i) * cpv + cb] = make_float4(cred[0][2].S, cred[0][3].S, cred[0][2].s, cred[0][3].s);
-        }
-        __syncthreads();                                  // cred is reused by the group's next vector
+            __syncthreads();
+            // lane (vector v, quantity qn) of warp 0 sums the warps in warp order; the lanes of Re s and Re t
+            // write the partials with their neighbours' Im s and Im t
+            static_assert(4 * kDotVB == 32, "one warp forms the partials of a round");
+            if (warp == 0) {
+                const int v = lane >> 2, qn = lane & 3;
+                dacc acc = cred[v][qn][0];                // rows v >= nb hold stale sums, never stored
+                for (int w = 1; w < kDotIW; ++w) dacc_add(acc, cred[v][qn][w]);
+                const df r = dacc_result(acc);
+                const float rh = __shfl_sync(0xffffffffu, r.hi, lane ^ 1);
+                const float rl = __shfl_sync(0xffffffffu, r.lo, lane ^ 1);
+                if (v < nb && (qn == 0 || qn == 2)) {
+                    const int i = i0 + v;
+                    part[(long)(qn == 0 ? i : a.m + 1 + i) * cpv + cb] = make_float4(r.hi, rh, r.lo, rl);
+                }
+            }
+            __syncthreads();                              // cred is reused by the group's next vectors
         }
     }
     pdl_trigger();
@@ -1550,13 +1560,13 @@ static int arnoldi_step_dcgs(Plan *p, GmresWork *g, int inner, int j) {
     const size_t smem = (size_t)(a.fused ? a.dsm_last : std::max(2 * g->m + 2, 4 * g->m + 4)) * sizeof(float4);
     const dim3 vgrid(a.nblk_vec + (a.fused ? 2 : 1), g->k);   // + the Givens CTA (+ the Hessenberg CTA)
     const bool wide = !p->in_batch && (long)a.nblk_vec * g->k < 4L * p->nsm;
-    rc = wide ? dcgs_smem_optin(p, dcgs_update_kernel<16>, smem, "delayed CGS2 update shared memory")
+    rc = wide ? dcgs_smem_optin(p, dcgs_update_kernel<8>, smem, "delayed CGS2 update shared memory")
               : dcgs_smem_optin(p, dcgs_update_kernel<4>, smem, "delayed CGS2 update shared memory");
     if (rc != BTTB_OK) return rc;
     const int tok = prof_begin(p, 4);
     cudaError_t e;
     if (wide)
-        e = launch_pdl(dcgs_update_kernel<16>, vgrid, dim3(kStepNB), smem, st, a, j);
+        e = launch_pdl(dcgs_update_kernel<8>, vgrid, dim3(kStepNB), smem, st, a, j);
     else
         e = launch_pdl(dcgs_update_kernel<4>, vgrid, dim3(kStepNB), smem, st, a, j);
     prof_end(p, tok, 0.0);

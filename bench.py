@@ -58,6 +58,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # the autotuner times the product forms; under a profiler that serialises launches its choice differs
+    # from the unprofiled one, so a profiling run can pin the form it wants to see (1..4, as
+    # BTTB_DEBUG_PRODUCT_ROUTE; 0: the tuned choice)
+    ap.add_argument("--product-form", type=int, choices=[0, 1, 2, 3, 4], default=0)
     return ap.parse_args()
 
 
@@ -457,6 +461,8 @@ def run_ours(args):
     plan = bt.Plan(nx, ny, b, max_rhs=1, prec_mask=all_prec, stream=stream)
     plan.set_generators(gen)
     fft_width = plan.autotune(1, 10)          # product form and FFT batch-chunk width for one-column products
+    if args.product_form:
+        bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, args.product_form)
     n, mx, my = plan.n, plan.mx, plan.my
     v_host = arrays.centre_excitation(nx, ny, b)[None, :].copy()
     V = torch.from_numpy(v_host).to(dev)
@@ -594,6 +600,8 @@ def run_ours(args):
                 entry.setdefault("by_route", {})[route_names[route]] = rec
         mv[name] = entry
     plan.autotune(1, 10)                      # the sweep forced each form: restore the tuned ones
+    if args.product_form:
+        bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, args.product_form)
     ir_route = route_names[bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_ROUTE_TAKEN, (bt.BTTB_MV_FP32 << 8) | 1)]
     df_route = route_names[bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_ROUTE_TAKEN, (bt.BTTB_MV_FP64 << 8) | 1)]
 

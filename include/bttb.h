@@ -416,6 +416,28 @@ enum { BTTB_DEBUG_WAIT_LIMIT_NS = 1, BTTB_DEBUG_WITHHOLD_ARRIVAL = 2, BTTB_DEBUG
        BTTB_DEBUG_ROUTE_TAKEN = 4, BTTB_DEBUG_FUSED_SHAPE = 5, BTTB_DEBUG_FUSED_CLUSTER = 6 };
 int bttb_plan_debug(bttb_plan plan, int what, long long value);
 
+/*
+ * Bounds-checked build (libbttb_checked.so, compiled with -DBTTB_CHECKED=1;
+ * the paper has no counterpart).  Its kernels check the global accesses of
+ * the vector loads and stores, the bulk and asynchronous copies, the Arnoldi,
+ * Givens and GEMM-epilogue accesses against the device buffers the library
+ * allocated or was handed in its calls, the FFT stages' shared-memory
+ * accesses against the CTA's shared memory, and the exchanges between the
+ * CTAs of a cluster against their buffers' lengths; a failed check is
+ * counted, its address recorded, and the access skipped (no fault).
+ * bttb_check_report: returns 1 in the checked build with *hits (HOST, may be
+ * NULL) the number of failed checks since load and *first_addr (HOST, may be
+ * NULL) the first bad address (a shared-memory offset carries 0x5 in the top
+ * four bits, an out-of-range index 0x6); returns 0 in the normal build (both
+ * 0).  Synchronises the device.
+ * bttb_check_probe: checked build only; reads one element past the end of a
+ * buffer of its own through a checked load (the check skips it) and returns
+ * BTTB_OK with *hits_added (HOST) the failed checks that read counted (1);
+ * BTTB_ERR_INVALID_ARG in the normal build, where it launches nothing.
+ */
+int bttb_check_report(unsigned long long *hits, unsigned long long *first_addr);
+int bttb_check_probe(unsigned long long *hits_added);
+
 /* Bytes of device memory the plan holds (spectrum copies and workspace). */
 size_t bttb_plan_workspace_bytes(bttb_plan plan);
 

@@ -16,7 +16,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libbttb.so")
+# BTTB_LIB_CHECKED=1 in the environment loads the bounds-checked build instead (tests of the checks).
+LIB_PATH = os.path.join(HERE, "libbttb_checked.so" if os.environ.get("BTTB_LIB_CHECKED") == "1" else "libbttb.so")
 
 BTTB_C64, BTTB_C128 = 0, 1
 BTTB_MV_FP64, BTTB_MV_FP32, BTTB_MV_FP64_NATIVE, BTTB_MV_TC_3XTF32, BTTB_MV_TC_BF16X3 = 0, 1, 2, 3, 4
@@ -38,7 +39,7 @@ EXPORTS = ("bttb_plan_create", "bttb_plan_grid", "bttb_set_generators", "bttb_ma
            "bttb_learned_create", "bttb_learned_param_count", "bttb_learned_params", "bttb_learned_apply",
            "bttb_learned_gradients", "bttb_learned_train_step", "bttb_plan_set_learned", "bttb_learned_destroy",
            "bttb_plan_autotune", "bttb_plan_debug", "bttb_plan_workspace_bytes", "bttb_plan_destroy",
-           "bttb_last_error")
+           "bttb_last_error", "bttb_check_report", "bttb_check_probe")
 
 
 class BttbError(RuntimeError):
@@ -104,6 +105,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bttb_learned_destroy.argtypes = [vp]
     lib.bttb_plan_autotune.argtypes = [vp, ci, ci, pi]
     lib.bttb_plan_debug.argtypes = [vp, ci, ctypes.c_longlong]
+    lib.bttb_check_report.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.bttb_check_probe.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
     lib.bttb_plan_workspace_bytes.argtypes = [vp]
     lib.bttb_plan_workspace_bytes.restype = ctypes.c_size_t
     lib.bttb_plan_destroy.argtypes = [vp]
@@ -302,6 +305,23 @@ def bttb_plan_autotune(plan, nrhs: int = 1, reps: int = 5) -> int:
 def bttb_plan_debug(plan, what: int, value: int) -> int:
     """Test hooks: BTTB_DEBUG_WAIT_LIMIT_NS, _WITHHOLD_ARRIVAL, _PRODUCT_ROUTE, _ROUTE_TAKEN (returns the route)."""
     return _check(load_library().bttb_plan_debug(plan, what, value), plan, soft_ok=True)
+
+
+def bttb_check_report():
+    """(checked, hits, first_bad_address): checked is False for the normal build (hits 0)."""
+    h, f = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+    rc = load_library().bttb_check_report(ctypes.byref(h), ctypes.byref(f))
+    if rc < 0:
+        _check(rc)
+    return rc == 1, int(h.value), int(f.value)
+
+
+def bttb_check_probe() -> int:
+    """Checked build only: the failed checks counted by one deliberate read one element past a buffer
+    (the check skips the read)."""
+    h = ctypes.c_ulonglong(0)
+    _check(load_library().bttb_check_probe(ctypes.byref(h)))
+    return int(h.value)
 
 
 def bttb_plan_workspace_bytes(plan) -> int:

@@ -9,6 +9,7 @@
 //   DF64 : double-float complex (cdf = float4), on the binary32 pipes
 //   F32  : IEEE binary32 (float2)
 #pragma once
+#include "check.cuh"
 #include <cuda_runtime.h>
 #include "df64.cuh"
 
@@ -110,16 +111,16 @@ template <class A> constexpr int native_fmt = A::kind == 2 ? FMT_C128 : (A::kind
 
 template <class A, int FMT>
 __device__ __forceinline__ typename A::C load_vec(const void *base, long idx) {
-    if constexpr (FMT == FMT_C128) return A::from_c128(reinterpret_cast<const double2 *>(base)[idx]);
-    else if constexpr (FMT == FMT_C64) return A::from_c64(reinterpret_cast<const float2 *>(base)[idx]);
-    else return A::from_cdf(reinterpret_cast<const float4 *>(base)[idx]);
+    if constexpr (FMT == FMT_C128) return A::from_c128(gld(reinterpret_cast<const double2 *>(base) + idx));
+    else if constexpr (FMT == FMT_C64) return A::from_c64(gld(reinterpret_cast<const float2 *>(base) + idx));
+    else return A::from_cdf(gld(reinterpret_cast<const float4 *>(base) + idx));
 }
 
 template <class A, int FMT>
 __device__ __forceinline__ void store_vec(void *base, long idx, typename A::C v) {
-    if constexpr (FMT == FMT_C128) reinterpret_cast<double2 *>(base)[idx] = A::to_c128(v);
-    else if constexpr (FMT == FMT_C64) reinterpret_cast<float2 *>(base)[idx] = A::to_c64(v);
-    else reinterpret_cast<float4 *>(base)[idx] = A::to_cdf(v);
+    if constexpr (FMT == FMT_C128) gst(reinterpret_cast<double2 *>(base) + idx, A::to_c128(v));
+    else if constexpr (FMT == FMT_C64) gst(reinterpret_cast<float2 *>(base) + idx, A::to_c64(v));
+    else gst(reinterpret_cast<float4 *>(base) + idx, A::to_cdf(v));
 }
 
 }  // namespace bttb

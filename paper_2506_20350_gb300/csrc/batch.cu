@@ -103,8 +103,8 @@ static int autotune_plan(Plan &p, int nrhs, int reps) {
     const int widths[6] = {2, 4, 8, 16, 32, 64};
     void *x = nullptr, *y = nullptr;
     const size_t bytes = (size_t)nrhs * p.n * sizeof(double2);
-    cudaError_t e = cudaMalloc(&x, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&y, bytes);
+    cudaError_t e = dev_malloc((void **)&x, bytes);
+    if (e == cudaSuccess) e = dev_malloc((void **)&y, bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, bytes, p.stream);
     if (e != cudaSuccess) {
         cudaFree(x);

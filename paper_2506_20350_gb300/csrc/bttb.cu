@@ -152,7 +152,7 @@ int bttb_plan_create(bttb_plan *out, int nx, int ny, int b, int max_rhs, unsigne
     p.gbs = ((long)b * b + 1) / 2 * 2;
     const size_t gplane = (size_t)p.bins * p.gbs;
     auto alloc = [&](void **ptr, size_t bytes, const char *what) -> int {
-        cudaError_t ee = cudaMalloc(ptr, bytes);
+        cudaError_t ee = dev_malloc(ptr, bytes);
         if (ee != cudaSuccess) return check_cuda(&p, ee, what);
         p.bytes_held += bytes;
         return BTTB_OK;
@@ -192,6 +192,8 @@ int bttb_set_generators(bttb_plan plan, const void *gen, bttb_dtype dtype, int g
         cudaError_t e0 = cudaDeviceSynchronize();
         if (e0 != cudaSuccess) return check_cuda(&p, e0, "set_generators: device synchronise");
     }
+    if (!gen_is_host)
+        check_track(gen, (size_t)(2 * p.nx - 1) * (2 * p.ny - 1) * p.b * p.b * (dtype == BTTB_C128 ? 16 : 8));
     cudaMemsetAsync(p.d_err, 0, sizeof(int), p.stream);
     int rc = spectrum_compute(&p, gen, dtype, gen_is_host);
     if (rc != BTTB_OK) return rc;
@@ -235,6 +237,8 @@ int bttb_matvec(bttb_plan plan, const void *x, void *y, int nrhs, long ld, bttb_
     if (dtype != BTTB_C64 && dtype != BTTB_C128) return set_error(&p, BTTB_ERR_INVALID_ARG, "bad dtype");
     if (!prec_enabled(p, prec)) return set_error(&p, BTTB_ERR_INVALID_ARG, "precision not enabled in this plan");
     const int fmt = dtype == BTTB_C128 ? FMT_C128 : FMT_C64;
+    check_track_cols(x, nrhs, ld, p.n, dtype == BTTB_C128 ? 16 : 8);
+    check_track_cols(y, nrhs, ld, p.n, dtype == BTTB_C128 ? 16 : 8);
     return matvec_run(&p, x, fmt, ld, y, fmt, ld, nrhs, (int)prec);
 }
 
@@ -247,6 +251,8 @@ int bttb_block_jacobi_apply(bttb_plan plan, const void *x, void *z, int nrhs, lo
         return set_error(&p, BTTB_ERR_INVALID_ARG, "bad nrhs, ld or pointer");
     if (nrhs == 0) return BTTB_OK;
     const int fmt = dtype == BTTB_C128 ? FMT_C128 : FMT_C64;
+    check_track_cols(x, nrhs, ld, p.n, dtype == BTTB_C128 ? 16 : 8);
+    check_track_cols(z, nrhs, ld, p.n, dtype == BTTB_C128 ? 16 : 8);
     return block_jacobi_run(&p, x, fmt, ld, z, fmt, ld, nrhs);
 }
 
@@ -269,6 +275,10 @@ int bttb_gmres_solve(bttb_plan plan, const void *V, void *I, int nrhs, long ld, 
     if (!prec_enabled(p, opts->inner)) return set_error(&p, BTTB_ERR_INVALID_ARG, "inner precision not enabled");
     if (!prec_enabled(p, BTTB_MV_FP64))
         return set_error(&p, BTTB_ERR_INVALID_ARG, "GMRES needs the FP64 (double-float) spectrum for its residuals");
+    if (!opts->host_io) {
+        check_track_cols(V, nrhs, ld, p.n, 16);
+        check_track_cols(I, nrhs, ld, p.n, 16);
+    }
     cudaMemsetAsync(p.d_err, 0, sizeof(int), p.stream);
     return gmres_solve(&p, V, I, nrhs, ld, opts, out_host);
 }

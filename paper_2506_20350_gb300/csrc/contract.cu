@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(256) contract_multi_kernel(const float2 *g0, l
         }
 #pragma unroll
         for (int j = 0; j < CPG; ++j)
-            if (cbase + j < nc) v[(long)bin * ubs + (long)(c0 + cbase + j) * b + p] = acc[j];
+            if (cbase + j < nc) gst(v + (long)bin * ubs + (long)(c0 + cbase + j) * b + p, acc[j]);
     }
     pdl_trigger();
 }
@@ -972,7 +972,7 @@ __global__ void __launch_bounds__(256) contract_multi44_kernel(const float2 *g0,
             if (cc < nc)
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
-                    if (prow[r] < b) v[(long)bin * ubs + (long)(c0 + cc) * b + prow[r]] = acc[r][j];
+                    if (prow[r] < b) gst(v + (long)bin * ubs + (long)(c0 + cc) * b + prow[r], acc[r][j]);
         }
     }
     pdl_trigger();

@@ -78,9 +78,9 @@ int fft_plan_init(Plan *p, FftPlan &f, int M) {
         t32[t] = make_float2(rh, ih);
     }
     cudaError_t e;
-    if ((e = cudaMalloc(&f.tw_f64, ntab * sizeof(double2))) != cudaSuccess) return check_cuda(p, e, "twiddles");
-    if ((e = cudaMalloc(&f.tw_df, ntab * sizeof(float4))) != cudaSuccess) return check_cuda(p, e, "twiddles");
-    if ((e = cudaMalloc(&f.tw_f32, ntab * sizeof(float2))) != cudaSuccess) return check_cuda(p, e, "twiddles");
+    if ((e = dev_malloc((void **)&f.tw_f64, ntab * sizeof(double2))) != cudaSuccess) return check_cuda(p, e, "twiddles");
+    if ((e = dev_malloc((void **)&f.tw_df, ntab * sizeof(float4))) != cudaSuccess) return check_cuda(p, e, "twiddles");
+    if ((e = dev_malloc((void **)&f.tw_f32, ntab * sizeof(float2))) != cudaSuccess) return check_cuda(p, e, "twiddles");
     cudaMemcpy(f.tw_f64, t64.data(), ntab * sizeof(double2), cudaMemcpyHostToDevice);
     cudaMemcpy(f.tw_df, tdf.data(), ntab * sizeof(float4), cudaMemcpyHostToDevice);
     e = cudaMemcpy(f.tw_f32, t32.data(), ntab * sizeof(float2), cudaMemcpyHostToDevice);
@@ -372,7 +372,8 @@ __global__ void __launch_bounds__(kFft2Threads) fft2_fused_kernel(const Fft2Args
             const int kx = idx / nrow, il = idx - kx * nrow;
             const int q = ((kx + 1) * Q - 1) / mx;                                  // owner of column kx
             C *dst = cl.map_shared_rank(Y0, q);
-            dst[(kx - q * mx / Q) * ms + rlo + il] = R1[kx * xs + il];
+            const long di = (long)(kx - q * mx / Q) * ms + rlo + il;
+            if (BTTB_ICHK(di, (long)a.ncmax * ms)) dst[di] = R1[kx * xs + il];
         }
         cl.sync();
         const C *R2 = fft2_level<A, false>(Y0, Y1, twy, a.sy, 1, ncol, ms);       // along iy, own columns
@@ -396,7 +397,8 @@ __global__ void __launch_bounds__(kFft2Threads) fft2_fused_kernel(const Fft2Args
             const int kl = idx / ny, iy = idx - kl * ny;
             const int q = ((iy + 1) * Q - 1) / ny;                                  // owner of row iy
             C *dst = cl.map_shared_rank(X0, q);
-            dst[(clo + kl) * xs + iy - q * ny / Q] = R1[kl * ms + iy];
+            const long di = (long)(clo + kl) * xs + iy - q * ny / Q;
+            if (BTTB_ICHK(di, (long)mx * xs)) dst[di] = R1[kl * ms + iy];
         }
         cl.sync();
         const C *R2 = fft2_level<A, true>(X0, X1, twx, a.sx, xs, nrow, 1);        // along kx, own rows
@@ -584,9 +586,9 @@ int spectrum_compute(Plan *p, const void *gen, bttb_dtype dtype, int gen_is_host
         rc = check_cuda(p, ee, what);
         return rc;
     };
-    if ((e = cudaMalloc(&g64, ngen * sizeof(double2))) != cudaSuccess) { fail(e, "generator buffer"); goto done; }
-    if ((e = cudaMalloc(&w1, nw * sizeof(double2))) != cudaSuccess) { fail(e, "spectrum workspace"); goto done; }
-    if ((e = cudaMalloc(&w2, nw * sizeof(double2))) != cudaSuccess) { fail(e, "spectrum workspace"); goto done; }
+    if ((e = dev_malloc((void **)&g64, ngen * sizeof(double2))) != cudaSuccess) { fail(e, "generator buffer"); goto done; }
+    if ((e = dev_malloc((void **)&w1, nw * sizeof(double2))) != cudaSuccess) { fail(e, "spectrum workspace"); goto done; }
+    if ((e = dev_malloc((void **)&w2, nw * sizeof(double2))) != cudaSuccess) { fail(e, "spectrum workspace"); goto done; }
     if (dtype == BTTB_C128) {
         e = cudaMemcpyAsync(g64, gen, ngen * sizeof(double2),
                             gen_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, p->stream);
@@ -594,7 +596,7 @@ int spectrum_compute(Plan *p, const void *gen, bttb_dtype dtype, int gen_is_host
     } else {
         const void *src = gen;
         if (gen_is_host) {
-            if ((e = cudaMalloc(&gtmp, ngen * sizeof(float2))) != cudaSuccess) { fail(e, "generator copy"); goto done; }
+            if ((e = dev_malloc((void **)&gtmp, ngen * sizeof(float2))) != cudaSuccess) { fail(e, "generator copy"); goto done; }
             e = cudaMemcpyAsync(gtmp, gen, ngen * sizeof(float2), cudaMemcpyHostToDevice, p->stream);
             if (e != cudaSuccess) { fail(e, "generator copy"); goto done; }
             src = gtmp;

@@ -101,7 +101,7 @@ __device__ __forceinline__ void fft2_stage(const typename A::C *__restrict__ src
         const int k = j - q * Ns;
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[(j + r * m) * es + off];
+        for (int r = 0; r < R; ++r) v[r] = sld(src + (j + r * m) * es + off);
         if (k != 0) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = A::cmul(v[r], tw[r * k * tstep], INV);
@@ -112,7 +112,7 @@ __device__ __forceinline__ void fft2_stage(const typename A::C *__restrict__ src
         else Butterfly<A>::r5(v, sg, c1, c2, s1, s2);
         const int dbase = q * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[(dbase + r * Ns) * es + off] = v[r];
+        for (int r = 0; r < R; ++r) sst(dst + (dbase + r * Ns) * es + off, v[r]);
     }
 }
 
@@ -166,7 +166,7 @@ __device__ __forceinline__ void fft_stage(const typename A::C *__restrict__ src,
         const int k = j - q * Ns;
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[((j + r * m) << lP) + pp];
+        for (int r = 0; r < R; ++r) v[r] = sld(src + ((j + r * m) << lP) + pp);
         if (k != 0) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = A::cmul(v[r], tw[r * k * tstep], INV);
@@ -177,7 +177,7 @@ __device__ __forceinline__ void fft_stage(const typename A::C *__restrict__ src,
         else Butterfly<A>::r5(v, sg, c1, c2, s1, s2);
         const int dbase = q * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[((dbase + r * Ns) << lP) + pp] = v[r];
+        for (int r = 0; r < R; ++r) sst(dst + ((dbase + r * Ns) << lP) + pp, v[r]);
     }
 }
 

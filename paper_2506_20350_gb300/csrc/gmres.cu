@@ -145,7 +145,7 @@ __device__ __forceinline__ void warp_sum_partials(const float4 *pp, int n, dacc 
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int e = e0 + 32 * u;
-            v[u] = e < n ? __ldcg(pp + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[u] = e < n ? gldcg(pp + e) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kVecThreads) norm_partial_kernel(const float4 
         dacc t = red[0];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) dacc_add(t, red[w]);
         const df r = dacc_result(t);
-        part[(long)c * pstride + blk] = make_float4(r.hi, 0.f, r.lo, 0.f);
+        gst(part + (long)c * pstride + blk, make_float4(r.hi, 0.f, r.lo, 0.f));
     }
 }
 
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(const float4 *basis
         const float4 x = w[(long)c * n + e];
         dacc re{x.x, x.z}, im{x.y, x.w};
         for (int i = 0; i < cnt; ++i) {
-            const float4 v = basis[(long)i * bs_i + (long)c * bs_c + e];
+            const float4 v = gld(basis + (long)i * bs_i + (long)c * bs_c + e);
             const float4 h = csm[i];
             // v h = (vr hr - vi hi) + i (vr hi + vi hr)
             dacc_mac(re, v.x, v.z, h.x, h.z);
@@ -301,13 +301,13 @@ __device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const 
     float4 *Hc = H + (long)c * (m + 1) * m;
     float zn2 = 0.f;
     for (int i = lane; i <= j; i += 32) {
-        const float4 h = ha[i];
+        const float4 h = gld(ha + i);
         hcol[i] = h;
         zn2 += h.x * h.x + h.y * h.y;
     }
     for (int i = lane; i < j; i += 32) {
-        snw[i] = sn[(long)c * m + i];
-        csw[i] = cs[(long)c * m + i];
+        snw[i] = gld(sn + (long)c * m + i);
+        csw[i] = gld(cs + (long)c * m + i);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) zn2 += __shfl_xor_sync(0xffffffffu, zn2, off);
@@ -374,16 +374,16 @@ __device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const 
                 c_ = df_mul(aa, inv_rho);
                 s_ = dfc_scale(a, df_mul(df_mul(beta, inv_rho), df_recip(aa)));   // (a/|a|) beta/rho
             }
-            cs[(long)c * m + j] = make_float2(c_.hi, c_.lo);
-            *reinterpret_cast<cdf *>(&sn[(long)c * m + j]) = dfc_store(s_);
+            gst(cs + (long)c * m + j, make_float2(c_.hi, c_.lo));
+            gst(reinterpret_cast<cdf *>(sn + (long)c * m + j), dfc_store(s_));
             // new diagonal c a + s beta
             const dfc hj = dfc_add(dfc_scale(a, c_), dfc_scale(s_, beta));
             *reinterpret_cast<cdf *>(&hcol[j]) = dfc_store(hj);
             float4 *g = gv + (long)c * (m + 1);
-            const dfc gj = dfc_load(*reinterpret_cast<const cdf *>(&g[j]));
+            const dfc gj = dfc_load(gld(reinterpret_cast<const cdf *>(g + j)));
             const dfc gj1 = dfc_neg(dfc_mul(dfc_conj(s_), gj));         // g[j+1] = -conj(s) g[j]
-            *reinterpret_cast<cdf *>(&g[j + 1]) = dfc_store(gj1);
-            *reinterpret_cast<cdf *>(&g[j]) = dfc_store(dfc_scale(gj, c_));
+            gst(reinterpret_cast<cdf *>(g + j + 1), dfc_store(gj1));
+            gst(reinterpret_cast<cdf *>(g + j), dfc_store(dfc_scale(gj, c_)));
             steps[c] = j + 1;
             const bool bd = !(beta.hi > 1e-14f * zn);
             if (bd) bdown[c] = 1;
@@ -398,7 +398,7 @@ __device__ int givens_column(int c, int j, int m, float4 *wsm, float4 *H, const 
         }
     }
     __syncwarp();
-    for (int i = lane; i <= j; i += 32) Hc[i + (long)j * (m + 1)] = hcol[i];
+    for (int i = lane; i <= j; i += 32) gst(Hc + i + (long)j * (m + 1), hcol[i]);
     return __shfl_sync(0xffffffffu, cont, 0);
 }
 
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kDotIW * 32) step_dots_kernel(const StepArgs a
                 re += __shfl_xor_sync(0xffffffffu, re, off);
                 im += __shfl_xor_sync(0xffffffffu, im, off);
             }
-            if (lane == 0) part[(long)i * a.nblk_dot + blk] = make_float4(re, im, 0.f, 0.f);
+            if (lane == 0) gst(part + (long)i * a.nblk_dot + blk, make_float4(re, im, 0.f, 0.f));
         } else {
             dacc_add(re0, dre1);
             dacc_add(im0, dim1);
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kDotIW * 32) step_dots_kernel(const StepArgs a
             warp_reduce_dacc(im0);
             if (lane == 0) {
                 const df r = dacc_result(re0), q = dacc_result(im0);
-                part[(long)i * a.nblk_dot + blk] = make_float4(r.hi, q.hi, r.lo, q.lo);
+                gst(part + (long)i * a.nblk_dot + blk, make_float4(r.hi, q.hi, r.lo, q.lo));
             }
         }
     }
@@ -561,7 +561,7 @@ __device__ __forceinline__ float4 cta_update_entry(const float4 *basis, long bs_
         float4 v[UB];
 #pragma unroll
         for (int u = 0; u < UB; ++u)
-            if (i0 + u < cnt) v[u] = basis[(long)(i0 + u) * bs_i + boff];
+            if (i0 + u < cnt) v[u] = gld(basis + (long)(i0 + u) * bs_i + boff);
 #pragma unroll
         for (int u = 0; u < UB; ++u) {
             if (i0 + u < cnt) {
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kStepNB) step_update_kernel(const StepArgs a, 
         dacc t = red[0];
         for (int w = 1; w < kStepNB / 32; ++w) dacc_add(t, red[w]);
         const df r = dacc_result(t);
-        part[blk] = make_float4(r.hi, 0.f, r.lo, 0.f);
+        gst(part + blk, make_float4(r.hi, 0.f, r.lo, 0.f));
     }
     if (!arrive_last(a.cnt_c + c, a.nblk_vec)) return;
     if (warp == 0) {
@@ -635,10 +635,10 @@ __global__ void __launch_bounds__(kStepNB) step_scale_kernel(const StepArgs a, i
         const df s = df_from_double(a.inv_beta[c]);
         const long e = (long)blk * kStepNB + threadIdx.x;
         if (e < a.n) {
-            const float4 x = a.W[(long)c * a.n + e];
+            const float4 x = gld(a.W + (long)c * a.n + e);
             const df r = df_mul(df{x.x, x.z}, s), q = df_mul(df{x.y, x.w}, s);
-            const_cast<float4 *>(a.Vb)[(long)(j + 1) * a.bs_i + (long)c * a.bs_c + e] =
-                make_float4(r.hi, q.hi, r.lo, q.lo);
+            gst(const_cast<float4 *>(a.Vb) + (long)(j + 1) * a.bs_i + (long)c * a.bs_c + e,
+                make_float4(r.hi, q.hi, r.lo, q.lo));
         }
     }
     pdl_trigger();
@@ -758,7 +758,7 @@ __device__ void dcgs_tail(const DcgsArgs &a, int c, int j, int has_x, int npart,
                     float4 v[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
-                        v[u] = e + u * T < npart ? __ldcg(pp + e + u * T) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[u] = e + u * T < npart ? gldcg(pp + e + u * T) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         dacc_add(re, dacc{v[u].x, v[u].z});
@@ -829,7 +829,7 @@ __device__ void dcgs_tail(const DcgsArgs &a, int c, int j, int has_x, int npart,
         if (j >= 1) {
             float4 *fc = hs;
             for (int q = threadIdx.x; q < j; q += blockDim.x) {
-                const cdf st = dfc_store(dfc_add(dfc_load(*reinterpret_cast<const cdf *>(&hp[q])),
+                const cdf st = dfc_store(dfc_add(dfc_load(gld(reinterpret_cast<const cdf *>(hp + q))),
                                                  dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
                 fc[q] = make_float4(st.rh, st.ih, st.rl, st.il);
             }
@@ -856,10 +856,10 @@ __device__ void dcgs_tail(const DcgsArgs &a, int c, int j, int has_x, int npart,
             dfc acc{df{0.f, 0.f}, df{0.f, 0.f}};
 #pragma unroll 4
             for (int q = max(r - 1, 0) + ((gq - max(r - 1, 0) % G) % G + G) % G; q < j; q += G)
-                acc = dfc_add(acc, dfc_mul(dfc_load(*reinterpret_cast<const cdf *>(&Hoc[(long)q * (m + 1) + r])),
+                acc = dfc_add(acc, dfc_mul(dfc_load(gld(reinterpret_cast<const cdf *>(Hoc + (long)q * (m + 1) + r))),
                                            dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
             const cdf st = dfc_store(acc);
-            hpart[gq * R + r] = make_float4(st.rh, st.ih, st.rl, st.il);
+            sst(hpart + gq * R + r, make_float4(st.rh, st.ih, st.rl, st.il));
         }
         if (threadIdx.x == 0) put_cj();
     };
@@ -867,12 +867,12 @@ __device__ void dcgs_tail(const DcgsArgs &a, int c, int j, int has_x, int npart,
         // close column j-1: entries hpre + s (rows 0..j-1), subdiagonal nu
         float4 *fc = hs;                                  // the closed column, rows 0..j-1
         for (int q = threadIdx.x; q < j; q += blockDim.x) {
-            const cdf st = dfc_store(dfc_add(dfc_load(*reinterpret_cast<const cdf *>(&hp[q])),
+            const cdf st = dfc_store(dfc_add(dfc_load(gld(reinterpret_cast<const cdf *>(hp + q))),
                                              dfc_load(*reinterpret_cast<const cdf *>(&ssm[q]))));
             fc[q] = make_float4(st.rh, st.ih, st.rl, st.il);
-            Hoc[(long)(j - 1) * (m + 1) + q] = fc[q];
+            gst(Hoc + (long)(j - 1) * (m + 1) + q, fc[q]);
         }
-        if (threadIdx.x == 0) Hoc[(long)(j - 1) * (m + 1) + j] = make_float4(nu.hi, 0.f, nu.lo, 0.f);
+        if (threadIdx.x == 0) gst(Hoc + (long)(j - 1) * (m + 1) + j, make_float4(nu.hi, 0.f, nu.lo, 0.f));
         if (!has_x) {
             // the cycle's last close (role TAIL_LAST): its Givens step here
             __syncthreads();
@@ -886,7 +886,7 @@ __device__ void dcgs_tail(const DcgsArgs &a, int c, int j, int has_x, int npart,
         if (role == TAIL_LAST) {
             // the Givens step of column j-1 runs in the update kernel's extra CTA, beside the update
             float4 *hc = a.hcol + (long)c * (m + 1);
-            for (int q = threadIdx.x; q < j; q += blockDim.x) hc[q] = fc[q];
+            for (int q = threadIdx.x; q < j; q += blockDim.x) gst(hc + q, fc[q]);
             if (threadIdx.x == 0) {
                 a.nu2[c] = df_to_double(df_mul(nu, nu));
                 a.inv_beta[c] = df_to_double(inu);
@@ -911,13 +911,13 @@ __device__ void dcgs_tail(const DcgsArgs &a, int c, int j, int has_x, int npart,
     for (int r = threadIdx.x; r <= j; r += blockDim.x) {
         const long o = (long)c * (m + 1) + r;
         if (role == TAIL_LAST) {
-            if (r < j) a.sco[o] = ssm[r];
-            a.cco[o] = tsm[r];
+            if (r < j) gst(a.sco + o, ssm[r]);
+            gst(a.cco + o, tsm[r]);
         }
         const dfc hpj = dfc_scale(dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&tsm[r])),
                                           dfc_load(*reinterpret_cast<const cdf *>(&hs[r]))), inu);
         const cdf st = dfc_store(hpj);
-        hw[r] = make_float4(st.rh, st.ih, st.rl, st.il);
+        gst(hw + r, make_float4(st.rh, st.ih, st.rl, st.il));
     }
 }
 
@@ -966,8 +966,8 @@ __global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArg
             for (int r = 0; r < kDotPL; ++r) {
                 const int e = lane + 32 * r;
                 const bool in = e < len;
-                u[r] = in ? uv[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                x[r] = in && has_x ? xv[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                u[r] = in ? gld(uv + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                x[r] = in && has_x ? gld(xv + e) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
             bool failed = false;
             int issued = j > 0 ? 0 : -1, waited = -1;     // lane 0's view of the copies
@@ -1018,7 +1018,7 @@ __global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArg
                 const dacc oth{__shfl_down_sync(0xffffffffu, tot.S, 8), __shfl_down_sync(0xffffffffu, tot.s, 8)};
                 if ((lane & 15) == 0) {
                     const df re = dacc_result(tot), im = dacc_result(oth);
-                    part[(long)(lane == 0 ? i : a.m + 1 + i) * npart + blk] = make_float4(re.hi, im.hi, re.lo, im.lo);
+                    gst(part + (long)(lane == 0 ? i : a.m + 1 + i) * npart + blk, make_float4(re.hi, im.hi, re.lo, im.lo));
                 }
             }
             if (lane == 0)                                 // copies still in flight after a failed wait
@@ -1052,9 +1052,9 @@ __global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArg
                         for (int r = 0; r < kDotPL; ++r) {
                             const int e = lane + 32 * r;
                             const bool in = e < len;
-                            q[r] = in ? qv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                            u[r] = in ? uv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                            x[r] = in && has_x ? xv[n0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            q[r] = in ? gld(qv + n0 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            u[r] = in ? gld(uv + n0 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            x[r] = in && has_x ? gld(xv + n0 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
                         float ftr = 0.f, fti = 0.f;
 #pragma unroll
@@ -1097,7 +1097,7 @@ __global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArg
                 const float rl = __shfl_sync(0xffffffffu, r.lo, lane ^ 1);
                 if (v < nb && (qn == 0 || qn == 2)) {
                     const int i = i0 + v;
-                    part[(long)(qn == 0 ? i : a.m + 1 + i) * cpv + cb] = make_float4(r.hi, rh, r.lo, rl);
+                    gst(part + (long)(qn == 0 ? i : a.m + 1 + i) * cpv + cb, make_float4(r.hi, rh, r.lo, rl));
                 }
             }
             __syncthreads();                              // cred is reused by the group's next vectors
@@ -1157,24 +1157,24 @@ __global__ void __launch_bounds__(kStepNB, 2) dcgs_update_kernel(const DcgsArgs 
         for (int q = threadIdx.x; q <= j; q += blockDim.x) {
             const long o = (long)c * (a.m + 1) + q;
             if (q < j) {
-                const float4 v = a.sco[o];
+                const float4 v = gld(a.sco + o);
                 sn_[q] = make_float4(-v.x, -v.y, -v.z, -v.w);
             }
-            const float4 w = a.cco[o];
+            const float4 w = gld(a.cco + o);
             cn_[q] = make_float4(-w.x, -w.y, -w.z, -w.w);
         }
         __syncthreads();
     }
     const long e = (long)blk * kStepNB + threadIdx.x;
     if (e < a.n) {
-        const float4 u = a.U[(long)c * a.n + e], x = a.X[(long)c * a.n + e];
+        const float4 u = gld(a.U + (long)c * a.n + e), x = gld(a.X + (long)c * a.n + e);
         dacc qr{u.x, u.z}, qi{u.y, u.w}, xr{x.x, x.z}, xi{x.y, x.w};
         const float4 *basis = a.Vb + (long)c * a.bs_c + e;
         for (int i0 = 0; i0 < j; i0 += UB) {
             float4 v[UB];
 #pragma unroll
             for (int r = 0; r < UB; ++r)
-                if (i0 + r < j) v[r] = basis[(long)(i0 + r) * a.bs_i];
+                if (i0 + r < j) v[r] = gld(basis + (long)(i0 + r) * a.bs_i);
 #pragma unroll
             for (int r = 0; r < UB; ++r) {
                 if (i0 + r < j) {
@@ -1198,8 +1198,8 @@ __global__ void __launch_bounds__(kStepNB, 2) dcgs_update_kernel(const DcgsArgs 
         dacc_mac(xi, q0.hi, q0.lo, g.y, g.w);
         dacc_mac(xi, q1.hi, q1.lo, g.x, g.z);
         const df x0 = df_mul(dacc_result(xr), inu), x1 = df_mul(dacc_result(xi), inu);
-        const_cast<float4 *>(a.Vb)[(long)j * a.bs_i + (long)c * a.bs_c + e] = make_float4(q0.hi, q1.hi, q0.lo, q1.lo);
-        a.U[(long)c * a.n + e] = make_float4(x0.hi, x1.hi, x0.lo, x1.lo);
+        gst(const_cast<float4 *>(a.Vb) + (long)j * a.bs_i + (long)c * a.bs_c + e, make_float4(q0.hi, q1.hi, q0.lo, q1.lo));
+        gst(a.U + (long)c * a.n + e, make_float4(x0.hi, x1.hi, x0.lo, x1.lo));
     }
     pdl_trigger();
 }
@@ -1223,19 +1223,19 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const float4 *H,
     __syncthreads();
     for (int i = kk - 1; i >= 0; --i) {
         if (threadIdx.x == 0) {
-            const dfc d = dfc_load(*reinterpret_cast<const cdf *>(&Hc[i + (long)i * (m + 1)]));
+            const dfc d = dfc_load(gld(reinterpret_cast<const cdf *>(Hc + i + (long)i * (m + 1))));
             const dfc sv = dfc_load(*reinterpret_cast<const cdf *>(&rhs[i]));
             const df dd = dfc_abs2(d);
             dfc yi{df{0.f, 0.f}, df{0.f, 0.f}};
             if (dd.hi > 0.f) yi = dfc_scale(dfc_mul(sv, dfc_conj(d)), df_recip(dd));
             const cdf yc = dfc_store(yi);
             ysh = make_float4(yc.rh, yc.ih, yc.rl, yc.il);
-            ycoef[(long)c * (m + 1) + i] = ysh;
+            gst(ycoef + (long)c * (m + 1) + i, ysh);
         }
         __syncthreads();
         const dfc yi = dfc_load(*reinterpret_cast<const cdf *>(&ysh));
         for (int l = threadIdx.x; l < i; l += blockDim.x) {
-            const dfc t = dfc_mul(dfc_load(*reinterpret_cast<const cdf *>(&Hc[l + (long)i * (m + 1)])), yi);
+            const dfc t = dfc_mul(dfc_load(gld(reinterpret_cast<const cdf *>(Hc + l + (long)i * (m + 1)))), yi);
             const dfc r = dfc_sub(dfc_load(*reinterpret_cast<const cdf *>(&rhs[l])), t);
             *reinterpret_cast<cdf *>(&rhs[l]) = dfc_store(r);
         }
@@ -1305,7 +1305,7 @@ static int ensure_work(Plan *p, int m, int k, long nv, int kp, bool flex, bool h
     bool ok = true;
     auto alloc = [&](auto **ptr, size_t bytes) {
         if (!ok) return;
-        if (cudaMalloc((void **)ptr, bytes) != cudaSuccess) ok = false;
+        if (dev_malloc((void **)ptr, bytes) != cudaSuccess) ok = false;
         total += bytes;
     };
     alloc(&g->X, sizeof(float4) * k * n);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "bttb.h"
+#include "check.cuh"
 
 namespace bttb {
 

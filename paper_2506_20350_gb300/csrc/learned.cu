@@ -825,7 +825,7 @@ int bttb_learned_create(bttb_learned *out, bttb_plan plan, int rank, int channel
     bool ok = true;
     auto alloc = [&](auto **ptr, size_t bytes) {
         if (!ok) return;
-        if (cudaMalloc((void **)ptr, bytes) != cudaSuccess) ok = false;
+        if (dev_malloc((void **)ptr, bytes) != cudaSuccess) ok = false;
         L->bytes += bytes;
     };
     alloc(&L->master, sizeof(float) * o);
@@ -913,6 +913,8 @@ int bttb_learned_apply(bttb_learned l, const void *r, void *z, int ncols, long l
     Learned *saved = p->learned;
     p->learned = L;
     const int fmt = dtype == BTTB_C128 ? FMT_C128 : FMT_C64;
+    check_track_cols(r, ncols, ld, L->n, dtype == BTTB_C128 ? 16 : 8);
+    check_track_cols(z, ncols, ld, L->n, dtype == BTTB_C128 ? 16 : 8);
     const int rc = learned_apply_run(p, r, fmt, ld, z, fmt, ld, ncols);
     p->learned = saved;
     return rc;
@@ -924,6 +926,8 @@ int bttb_learned_gradients(bttb_learned l, const void *r, const void *e, int nco
     Learned *L = l->L;
     if (ncols < 1 || ncols > L->maxcols || ld < L->n) return set_error(L->p, BTTB_ERR_INVALID_ARG, "bad ncols or ld");
     if (!L->p->bj_ready) return set_error(L->p, BTTB_ERR_SINGULAR, "block-Jacobi part unavailable (singular T[0,0])");
+    check_track_cols(r, ncols, ld, L->n, 8);
+    check_track_cols(e, ncols, ld, L->n, 8);
     int rc = learned_backward(L, r, e, ld, ncols, loss_host);
     if (rc != BTTB_OK) return rc;
     if (grad_host) {

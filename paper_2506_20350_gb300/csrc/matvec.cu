@@ -309,7 +309,7 @@ int block_jacobi_setup(Plan *p, const double2 *t00) {
         for (int i = 0; i < b; ++i) inv[(long)e * bq + i] = make_float2((float)col[2 * i], (float)col[2 * i + 1]);
     }
     if (!p->bj_inv) {
-        cudaError_t e = cudaMalloc(&p->bj_inv, (size_t)b * bq * sizeof(float2));
+        cudaError_t e = dev_malloc((void **)&p->bj_inv, (size_t)b * bq * sizeof(float2));
         if (e != cudaSuccess) return check_cuda(p, e, "block-Jacobi buffer");
         p->bytes_held += (size_t)b * bq * sizeof(float2);
     }

@@ -174,6 +174,10 @@ extern "C" int bttb_matvec_noalloc(int nx, int ny, int b, const void *gen, const
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p.dev);
     p.smem_optin = (size_t)optin;
 
+    check_track(base, kNoAllocScratchBytes);
+    check_track(gen, (size_t)(2 * nx - 1) * (2 * ny - 1) * b * b * 16);
+    check_track_cols(x, nrhs, ld, p.n, 16);
+    check_track_cols(y, nrhs, ld, p.n, 16);
     unsigned char *cur = static_cast<unsigned char *>(base);
     p.d_err = reinterpret_cast<int *>(cur);
     p.d_gbar = reinterpret_cast<unsigned long long *>(cur + 16);   // monotonic: never cleared

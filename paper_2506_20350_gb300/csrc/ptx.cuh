@@ -3,6 +3,7 @@
 // Every wait is bounded by the global nanosecond timer so that a kernel can
 // report a stuck pipeline instead of spinning forever.
 #pragma once
+#include "check.cuh"
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -100,6 +101,7 @@ __device__ __forceinline__ uint64_t l2_policy_evict_last() {
 // transaction bytes on `bar`.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
                                          uint64_t policy) {
+    if (!BTTB_GCHK(src, bytes) || !BTTB_SCHK(dst, bytes)) return;   // (the stage's wait then runs out)
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
         " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
@@ -112,10 +114,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 // no-ops for a kernel launched without the programmatic attribute).
 // 16-byte asynchronous global -> shared copy (L2 only), commit and wait.
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    if (!BTTB_GCHK(src, 16) || !BTTB_SCHK(dst, 16)) return;
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 // 8-byte asynchronous global -> shared copy (through L1).
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    if (!BTTB_GCHK(src, 8) || !BTTB_SCHK(dst, 8)) return;
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }

@@ -207,10 +207,10 @@ __global__ void __launch_bounds__(kTgThreads, 1) tcgemm_kernel(const __grid_cons
                 float *dst = a.v + (long)binof(j) * 2 * a.ubs + r;
 #pragma unroll
                 for (int c = 0; c < 16; ++c)
-                    if (t * kTgN + c < a.k) dst[(long)(t * kTgN + c) * twob] = v0[c];
+                    if (t * kTgN + c < a.k) gst(dst + (long)(t * kTgN + c) * twob, v0[c]);
 #pragma unroll
                 for (int c = 0; c < 16; ++c)
-                    if (t * kTgN + 16 + c < a.k) dst[(long)(t * kTgN + 16 + c) * twob] = v1[c];
+                    if (t * kTgN + 16 + c < a.k) gst(dst + (long)(t * kTgN + 16 + c) * twob, v1[c]);
             }
         };
         auto build_a = [&](int bin) {
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kTgThreads, 1) tcgemm_kernel(const __grid_cons
                     for (int e = 0; e < EC; e += 2) {
                         const int q = (kb * EB + j * EC + e) >> 1;
                         float2 gq = make_float2(0.f, 0.f);
-                        if (m < twob && q < b) gq = __ldg(g + (long)q * b);
+                        if (m < twob && q < b && BTTB_GCHK(g + (long)q * b, sizeof(float2))) gq = __ldg(g + (long)q * b);
                         x[e] = odd ? gq.y : gq.x;
                         x[e + 1] = odd ? gq.x : -gq.y;
                     }

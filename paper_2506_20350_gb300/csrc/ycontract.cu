@@ -160,7 +160,8 @@ __global__ void __launch_bounds__(kYcThreads, 2) ycontract_kernel(const YcArgs a
             const int c = t / np, pl = t - c * np;
             const int o = ky / a.kshare;
             C *dst = cl.map_shared_rank(Uh, o);
-            dst[(long)(ky - k_lo(o)) * kc * b + c * b + plo + pl] = R1[idx];
+            const long di = (long)(ky - k_lo(o)) * kc * b + c * b + plo + pl;
+            if (BTTB_ICHK(di, (long)a.kshare * kc * b)) dst[di] = R1[idx];
         }
         // the y-transform buffers take bulk copies from here on (async proxy after these generic accesses)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -192,7 +193,9 @@ __global__ void __launch_bounds__(kYcThreads, 2) ycontract_kernel(const YcArgs a
                 const GT *gs0 = reinterpret_cast<const GT *>(st) + p0;
                 const GT *gs1 = reinterpret_cast<const GT *>(st + a.off_g1) + p0;
                 const C *us = Uh + (long)kl * kc * b + q0;
-                if (p0 < b) {
+                const bool us_ok = BTTB_ICHK((long)kl * kc * b + q0 + (long)(kc - 1) * b + (qn - 1),
+                                             (long)a.kshare * kc * b);
+                if (p0 < b && us_ok) {
 #pragma unroll 2
                     for (int q = 0; q < qn; ++q) {
                         if constexpr (R == 2 && VEC) {
@@ -257,7 +260,8 @@ __global__ void __launch_bounds__(kYcThreads, 2) ycontract_kernel(const YcArgs a
             const int o = pr / a.pshare;
             const int npo = p_n(o);
             C *dst = cl.map_shared_rank(F0, o);
-            dst[(long)(klo + kl) * (kc * npo) + c * npo + (pr - p_lo(o))] = Uh[idx];
+            const long di = (long)(klo + kl) * (kc * npo) + c * npo + (pr - p_lo(o));
+            if (BTTB_ICHK(di, (long)my * kc * a.pshare)) dst[di] = Uh[idx];
         }
         cl.sync();
         // ---- 5. inverse transform along ky, crop to ny rows

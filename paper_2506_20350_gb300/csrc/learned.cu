@@ -322,21 +322,35 @@ __global__ void __launch_bounds__(256, 1) lp_conv_kernel(const float *X, int Ci,
 // per CTA row (blockIdx.y):
 //   wpart[chunk][co][ci*9 + tap] = sum_{n in chunk} dA[n][co] * in(nb(n, tap))[ci]
 //   wpart[chunk][co][Ci*9]       = sum_{n in chunk} dA[n][co]        (bias, tap 0 only)
-// in = relu(X) when relu_in.  Ci*Co/16 threads, each owning 4 output x 4 input
-// channels; tiles of kWgTile positions (input rows of the tap and dA rows) are
-// copied in with cp.async, double-buffered.
+// in = relu(X) when relu_in.  A GEMM per CTA, M = Co, N = Ci, K = the chunk's
+// positions, on the tensor cores (mma.sync m16n8k16, bfloat16 inputs, binary32
+// accumulation): tiles of kWgTile positions (input rows of the tap and dA rows)
+// are copied in with cp.async, double-buffered; each binary32 operand enters as
+// two bfloat16 terms, x = hi + lo, and the product as hi*hi + hi*lo + lo*hi (the
+// dropped lo*lo and the remainders are below 2^-16 relative per product).  Warp w
+// owns the 16 x 8 output tiles w, w + 8, ... (one row block of Co, so its A
+// fragment is loaded once per step).
 constexpr int kWgTile = 64;
 constexpr int kWgChunks = 96;       // position chunks (x 9 taps) of a weight-gradient launch
+constexpr int kWgThreads = 256;
 
-__global__ void __launch_bounds__(256) lp_wgrad_kernel(const float *X, int Ci, int relu_in, const float *dA, int Co,
-                                                       long npos, long chunk_len, int my, int mx, long bins,
-                                                       float *wpart) {
+// x = hi + lo with two bfloat16 terms, for a pair of values (packed low half first).
+__device__ __forceinline__ void split2_bf16x2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+__global__ void __launch_bounds__(kWgThreads) lp_wgrad_kernel(const float *X, int Ci, int relu_in, const float *dA,
+                                                              int Co, long npos, long chunk_len, int my, int mx,
+                                                              long bins, float *wpart) {
     extern __shared__ __align__(16) float gsm[];
     const int xs_stride = Ci + 4, ds_stride = Co + 4;
     const int buf_floats = kWgTile * (xs_stride + ds_stride);
     const int chunk = blockIdx.x, tap = blockIdx.y;
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    const int cig = threadIdx.x % (Ci / 4), cog = threadIdx.x / (Ci / 4);
     const long n0 = (long)chunk * chunk_len;
     const long n1 = min(npos, n0 + chunk_len);
     const int xch = Ci / 4, dch = Co / 4;
@@ -366,13 +380,19 @@ __global__ void __launch_bounds__(256) lp_wgrad_kernel(const float *X, int Ci, i
         }
         cp_async_commit();
     };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int MT = Co / 16, NTt = Ci / 8, T = MT * NTt;       // MT divides 8: a warp keeps one row block
+    const int mt = warp % MT;
+    int ntile = 0, nts[4];
+    for (int t = warp; t < T && ntile < 4; t += kWgThreads / 32) nts[ntile++] = t / MT;
     float acc[4][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[a][k] = 0.f;
-    float bacc[4] = {0.f, 0.f, 0.f, 0.f};
-    const bool do_bias = tap == 0 && cig == 0;
+        for (int e = 0; e < 4; ++e) acc[i][e] = 0.f;
+    float bacc = 0.f;
+    const bool do_bias = tap == 0 && (int)threadIdx.x < Co;
     int buf = 0;
     if (n0 < n1) stage(n0, gsm);
     for (long nb = n0; nb < n1; nb += kWgTile) {
@@ -382,39 +402,55 @@ __global__ void __launch_bounds__(256) lp_wgrad_kernel(const float *X, int Ci, i
         __syncthreads();
         const float *xs = gsm + buf * buf_floats;
         const float *ds = xs + kWgTile * xs_stride;
-#pragma unroll 4
-        for (int pl = 0; pl < kWgTile; ++pl) {
-            float4 xv = *reinterpret_cast<const float4 *>(xs + pl * xs_stride + cig * 4);
-            const float4 dv = *reinterpret_cast<const float4 *>(ds + pl * ds_stride + cog * 4);
-            if (relu_in) {
-                xv.x = fmaxf(xv.x, 0.f);
-                xv.y = fmaxf(xv.y, 0.f);
-                xv.z = fmaxf(xv.z, 0.f);
-                xv.w = fmaxf(xv.w, 0.f);
-            }
-            const float d4[4] = {dv.x, dv.y, dv.z, dv.w};
-            const float x4[4] = {xv.x, xv.y, xv.z, xv.w};
+        if (ntile > 0) {
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int k0 = 0; k0 < kWgTile; k0 += 16) {
+                // A (Co x K): rows co = 16 mt + gid (+8), columns k = k0 + 2 tig (+1, +8, +9)
+                const float *dr = ds + (k0 + 2 * tig) * ds_stride + mt * 16 + gid;
+                uint32_t ah[4], al[4];
+                split2_bf16x2(dr[0], dr[ds_stride], ah[0], al[0]);
+                split2_bf16x2(dr[8], dr[ds_stride + 8], ah[1], al[1]);
+                split2_bf16x2(dr[8 * ds_stride], dr[9 * ds_stride], ah[2], al[2]);
+                split2_bf16x2(dr[8 * ds_stride + 8], dr[9 * ds_stride + 8], ah[3], al[3]);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) acc[a][k] = fmaf(d4[a], x4[k], acc[a][k]);
-            if (do_bias) {
-#pragma unroll
-                for (int a = 0; a < 4; ++a) bacc[a] += d4[a];
+                for (int i = 0; i < 4; ++i) {
+                    if (i < ntile) {
+                        // B (K x Ci): rows k = k0 + 2 tig (+1, +8, +9), column ci = 8 nt + gid
+                        const float *xr = xs + (k0 + 2 * tig) * xs_stride + nts[i] * 8 + gid;
+                        float v0 = xr[0], v1 = xr[xs_stride], v2 = xr[8 * xs_stride], v3 = xr[9 * xs_stride];
+                        if (relu_in) {
+                            v0 = fmaxf(v0, 0.f);
+                            v1 = fmaxf(v1, 0.f);
+                            v2 = fmaxf(v2, 0.f);
+                            v3 = fmaxf(v3, 0.f);
+                        }
+                        uint32_t bh0, bl0, bh1, bl1;
+                        split2_bf16x2(v0, v1, bh0, bl0);
+                        split2_bf16x2(v2, v3, bh1, bl1);
+                        mma_bf16(acc[i], al, bh0, bh1);           // smallest terms first
+                        mma_bf16(acc[i], ah, bl0, bl1);
+                        mma_bf16(acc[i], ah, bh0, bh1);
+                    }
+                }
             }
         }
+        if (do_bias)
+            for (int pl = 0; pl < kWgTile; ++pl) bacc += ds[pl * ds_stride + threadIdx.x];
         __syncthreads();
         buf ^= 1;
     }
     cp_async_wait<0>();
     const int K = Ci * 9 + 1;
+    for (int i = 0; i < ntile; ++i) {
+        const int ci = nts[i] * 8 + 2 * tig;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        float *row = wpart + ((long)chunk * Co + cog * 4 + a) * K;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) row[(cig * 4 + k) * 9 + tap] = acc[a][k];
-        if (do_bias) row[Ci * 9] = bacc[a];
+        for (int half = 0; half < 2; ++half) {
+            float *row = wpart + ((long)chunk * Co + mt * 16 + gid + 8 * half) * K;
+            row[ci * 9 + tap] = acc[i][2 * half];
+            row[(ci + 1) * 9 + tap] = acc[i][2 * half + 1];
+        }
     }
+    if (do_bias) wpart[((long)chunk * Co + threadIdx.x) * K + Ci * 9] = bacc;
 }
 
 // grad[oW + co*Ci*9 + k] = sum_chunks wpart (k < Ci*9); grad[oc + co] = bias column
@@ -673,7 +709,7 @@ static int wgrad_launch(Plan *p, Learned *L, const float *X, int Ci, int relu_in
     const int nch = (int)((npos + chunk_len - 1) / chunk_len);
     const size_t smem = 2 * (size_t)kWgTile * (Ci + Co + 8) * sizeof(float);
     cudaFuncSetAttribute(lp_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
-    lp_wgrad_kernel<<<dim3(nch, 9), Ci * Co / 16, smem, p->stream>>>(X, Ci, relu_in, dA, Co, npos, chunk_len, L->my,
+    lp_wgrad_kernel<<<dim3(nch, 9), kWgThreads, smem, p->stream>>>(X, Ci, relu_in, dA, Co, npos, chunk_len, L->my,
                                                                       L->mx, L->bins, L->wpart);
     const int K = Ci * 9 + 1;
     lp_wgrad_reduce_kernel<<<(Co * K + 255) / 256, 256, 0, p->stream>>>(L->wpart, nch, Co, Ci, gW, gc);

@@ -1114,7 +1114,11 @@ __global__ void __launch_bounds__(kDotIW * 32, 2) dcgs_dots_kernel(const DcgsArg
 // q_j = (u_j - Q s)/nu and u_{j+1} = (x - Q t - q_j c_j)/nu, one entry per thread, the basis
 // entries loaded UB at a time and shared by both sums.
 static_assert(kStepNB == kDotIW * 32, "the update kernel's CTAs run the reduction tail with its warp count");
-template <int UB>
+// T32: the products of this solve are binary32 (the inner solve of GMRES-IR), so the first-pass part
+// u_{j+1} = (x - Q t - q_j c_j)/nu is formed in binary32 FMAs: x itself carries binary32 errors, t is a
+// binary32 first-pass coefficient, and the next step's reorthogonalisation (s = Q^H u_{j+1}, compensated
+// double-float) removes what this pass leaves in span(Q).  q_j stays double-float.
+template <int UB, bool T32>
 __global__ void __launch_bounds__(kStepNB, 2) dcgs_update_kernel(const DcgsArgs a, int j) {
     extern __shared__ __align__(16) float4 csm[];        // -s: j entries, -c: j+1 entries; Givens scratch
     const int c = blockIdx.y, blk = blockIdx.x;
@@ -1169,6 +1173,7 @@ __global__ void __launch_bounds__(kStepNB, 2) dcgs_update_kernel(const DcgsArgs 
     if (e < a.n) {
         const float4 u = gld(a.U + (long)c * a.n + e), x = gld(a.X + (long)c * a.n + e);
         dacc qr{u.x, u.z}, qi{u.y, u.w}, xr{x.x, x.z}, xi{x.y, x.w};
+        float fr = __fadd_rn(x.x, x.z), fi = __fadd_rn(x.y, x.w);       // T32: x in binary32
         const float4 *basis = a.Vb + (long)c * a.bs_c + e;
         for (int i0 = 0; i0 < j; i0 += UB) {
             float4 v[UB];
@@ -1183,23 +1188,40 @@ __global__ void __launch_bounds__(kStepNB, 2) dcgs_update_kernel(const DcgsArgs 
                     dacc_mac(qr, -v[r].y, -v[r].w, h.y, h.w);
                     dacc_mac(qi, v[r].x, v[r].z, h.y, h.w);
                     dacc_mac(qi, v[r].y, v[r].w, h.x, h.z);
-                    dacc_mac(xr, v[r].x, v[r].z, g.x, g.z);
-                    dacc_mac(xr, -v[r].y, -v[r].w, g.y, g.w);
-                    dacc_mac(xi, v[r].x, v[r].z, g.y, g.w);
-                    dacc_mac(xi, v[r].y, v[r].w, g.x, g.z);
+                    if constexpr (T32) {
+                        fr = fmaf(v[r].x, g.x, fr);
+                        fr = fmaf(-v[r].y, g.y, fr);
+                        fi = fmaf(v[r].x, g.y, fi);
+                        fi = fmaf(v[r].y, g.x, fi);
+                    } else {
+                        dacc_mac(xr, v[r].x, v[r].z, g.x, g.z);
+                        dacc_mac(xr, -v[r].y, -v[r].w, g.y, g.w);
+                        dacc_mac(xi, v[r].x, v[r].z, g.y, g.w);
+                        dacc_mac(xi, v[r].y, v[r].w, g.x, g.z);
+                    }
                 }
             }
         }
         const df inu = a.fused ? inu_f : df_from_double(a.inv_beta[c]);
         const df q0 = df_mul(dacc_result(qr), inu), q1 = df_mul(dacc_result(qi), inu);
         const float4 g = cn_[j];
-        dacc_mac(xr, q0.hi, q0.lo, g.x, g.z);
-        dacc_mac(xr, -q1.hi, -q1.lo, g.y, g.w);
-        dacc_mac(xi, q0.hi, q0.lo, g.y, g.w);
-        dacc_mac(xi, q1.hi, q1.lo, g.x, g.z);
-        const df x0 = df_mul(dacc_result(xr), inu), x1 = df_mul(dacc_result(xi), inu);
+        float4 un;
+        if constexpr (T32) {
+            fr = fmaf(q0.hi, g.x, fr);
+            fr = fmaf(-q1.hi, g.y, fr);
+            fi = fmaf(q0.hi, g.y, fi);
+            fi = fmaf(q1.hi, g.x, fi);
+            un = make_float4(__fmul_rn(fr, inu.hi), __fmul_rn(fi, inu.hi), 0.f, 0.f);
+        } else {
+            dacc_mac(xr, q0.hi, q0.lo, g.x, g.z);
+            dacc_mac(xr, -q1.hi, -q1.lo, g.y, g.w);
+            dacc_mac(xi, q0.hi, q0.lo, g.y, g.w);
+            dacc_mac(xi, q1.hi, q1.lo, g.x, g.z);
+            const df x0 = df_mul(dacc_result(xr), inu), x1 = df_mul(dacc_result(xi), inu);
+            un = make_float4(x0.hi, x1.hi, x0.lo, x1.lo);
+        }
         gst(const_cast<float4 *>(a.Vb) + (long)j * a.bs_i + (long)c * a.bs_c + e, make_float4(q0.hi, q1.hi, q0.lo, q1.lo));
-        gst(a.U + (long)c * a.n + e, make_float4(x0.hi, x1.hi, x0.lo, x1.lo));
+        gst(a.U + (long)c * a.n + e, un);
     }
     pdl_trigger();
 }
@@ -1560,15 +1582,12 @@ static int arnoldi_step_dcgs(Plan *p, GmresWork *g, int inner, int j) {
     const size_t smem = (size_t)(a.fused ? a.dsm_last : std::max(2 * g->m + 2, 4 * g->m + 4)) * sizeof(float4);
     const dim3 vgrid(a.nblk_vec + (a.fused ? 2 : 1), g->k);   // + the Givens CTA (+ the Hessenberg CTA)
     const bool wide = !p->in_batch && (long)a.nblk_vec * g->k < 4L * p->nsm;
-    rc = wide ? dcgs_smem_optin(p, dcgs_update_kernel<8>, smem, "delayed CGS2 update shared memory")
-              : dcgs_smem_optin(p, dcgs_update_kernel<4>, smem, "delayed CGS2 update shared memory");
-    if (rc != BTTB_OK) return rc;
+    const bool t32 = fft_prec_of(inner) == PREC_F32;          // binary32 products: binary32 first pass
+    auto kern = wide ? (t32 ? dcgs_update_kernel<8, true> : dcgs_update_kernel<8, false>)
+                     : (t32 ? dcgs_update_kernel<4, true> : dcgs_update_kernel<4, false>);
+    if ((rc = dcgs_smem_optin(p, kern, smem, "delayed CGS2 update shared memory")) != BTTB_OK) return rc;
     const int tok = prof_begin(p, 4);
-    cudaError_t e;
-    if (wide)
-        e = launch_pdl(dcgs_update_kernel<8>, vgrid, dim3(kStepNB), smem, st, a, j);
-    else
-        e = launch_pdl(dcgs_update_kernel<4>, vgrid, dim3(kStepNB), smem, st, a, j);
+    cudaError_t e = launch_pdl(kern, vgrid, dim3(kStepNB), smem, st, a, j);
     prof_end(p, tok, 0.0);
     count_launch(p);
     if (e != cudaSuccess) return check_cuda(p, e, "delayed CGS2 update launch");

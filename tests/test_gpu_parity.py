@@ -368,6 +368,27 @@ def test_full_size_product_routes(bt, precision_case, route):
         bt.bttb_plan_debug(plan.handle, bt.BTTB_DEBUG_PRODUCT_ROUTE, 0)
 
 
+@pytest.mark.parametrize("prec_name", ["BTTB_MV_TC_3XTF32", "BTTB_MV_TC_BF16X3"])
+def test_full_size_tensor_core_product(bt, prec_name):
+    """The tcgen05 per-bin GEMM at full size: the 30x30, b=60 array (3600 bins) times 128 columns (four tiles
+    of 32), columns at the tile edges and in between checked on 300 sampled rows each against the oracle's
+    O(N) row sums, to the tensor-core tolerance relative to the column's largest entry."""
+    c = arrays.CONFIGS["precision"]
+    gen = arrays.generator_blocks(c["nx"], c["ny"], c["b"], c["seed"])
+    prec = getattr(bt, prec_name)
+    plan = bt.Plan(c["nx"], c["ny"], c["b"], max_rhs=128, prec_mask=(1 << bt.BTTB_MV_FP64) | (1 << prec))
+    plan.set_generators(gen)
+    x = _rand(np.random.default_rng(12), 128, plan.n)
+    y = plan.matvec(_dev(x.astype(np.complex64)), prec=prec).cpu().numpy()
+    rows = np.unique(np.concatenate([np.arange(0, 60), plan.n - 1 - np.arange(60),
+                                     np.random.default_rng(13).integers(0, plan.n, 180)]))
+    for col in (0, 31, 32, 77, 127):
+        ref = oracle.matvec_rows(gen, x[col].astype(np.complex64), rows)
+        scale = np.abs(y[col]).max()
+        assert np.abs(y[col][rows] - ref).max() <= 4 * BF16X3_TOL * scale, (prec_name, col)
+    plan.close()
+
+
 def test_full_size_sampled_rows(bt, precision_case):
     c, gen, plan, x, ref = precision_case
     y = plan.matvec(_dev(x)).cpu().numpy()[0]

@@ -1581,7 +1581,10 @@ static int arnoldi_step_dcgs(Plan *p, GmresWork *g, int inner, int j) {
     // coefficients / Givens scratch; with the fused close, the reduction tail's scratch
     const size_t smem = (size_t)(a.fused ? a.dsm_last : std::max(2 * g->m + 2, 4 * g->m + 4)) * sizeof(float4);
     const dim3 vgrid(a.nblk_vec + (a.fused ? 2 : 1), g->k);   // + the Givens CTA (+ the Hessenberg CTA)
-    const bool wide = !p->in_batch && (long)a.nblk_vec * g->k < 4L * p->nsm;
+    // basis entries loaded eight at a time for a lone plan (the few-column grid is latency-bound, the
+    // many-column one streams the basis from HBM: both want the loads in flight), four in a batch, whose
+    // arrays' kernels share the SMs
+    const bool wide = !p->in_batch;
     const bool t32 = fft_prec_of(inner) == PREC_F32;          // binary32 products: binary32 first pass
     auto kern = wide ? (t32 ? dcgs_update_kernel<8, true> : dcgs_update_kernel<8, false>)
                      : (t32 ? dcgs_update_kernel<4, true> : dcgs_update_kernel<4, false>);

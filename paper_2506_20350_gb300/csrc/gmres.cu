@@ -553,10 +553,13 @@ __global__ void __launch_bounds__(kDotIW * 32) step_dots_kernel(const StepArgs a
 // new value.  The basis entries are loaded UB at a time, all loads of a batch
 // issued before its accumulations: a deep batch when few columns leave the GPU
 // short of warps, a shallow one (fewer registers, more warps) otherwise.
-template <int UB>
+// T32: binary32 FMAs (the first CGS pass of a solve with binary32 products; the second pass, compensated
+// double-float, removes what it leaves in span(V), as in the delayed-CGS2 update).
+template <int UB, bool T32 = false>
 __device__ __forceinline__ float4 cta_update_entry(const float4 *basis, long bs_i, long boff, const float4 *hs,
                                                    int cnt, float4 x) {
     dacc re{x.x, x.z}, im{x.y, x.w};
+    float fr = __fadd_rn(x.x, x.z), fi = __fadd_rn(x.y, x.w);
     for (int i0 = 0; i0 < cnt; i0 += UB) {
         float4 v[UB];
 #pragma unroll
@@ -566,20 +569,28 @@ __device__ __forceinline__ float4 cta_update_entry(const float4 *basis, long bs_
         for (int u = 0; u < UB; ++u) {
             if (i0 + u < cnt) {
                 const float4 h = hs[i0 + u];              // already negated
-                dacc_mac(re, v[u].x, v[u].z, h.x, h.z);
-                dacc_mac(re, -v[u].y, -v[u].w, h.y, h.w);
-                dacc_mac(im, v[u].x, v[u].z, h.y, h.w);
-                dacc_mac(im, v[u].y, v[u].w, h.x, h.z);
+                if constexpr (T32) {
+                    fr = fmaf(v[u].x, h.x, fr);
+                    fr = fmaf(-v[u].y, h.y, fr);
+                    fi = fmaf(v[u].x, h.y, fi);
+                    fi = fmaf(v[u].y, h.x, fi);
+                } else {
+                    dacc_mac(re, v[u].x, v[u].z, h.x, h.z);
+                    dacc_mac(re, -v[u].y, -v[u].w, h.y, h.w);
+                    dacc_mac(im, v[u].x, v[u].z, h.y, h.w);
+                    dacc_mac(im, v[u].y, v[u].w, h.x, h.z);
+                }
             }
         }
     }
+    if constexpr (T32) return make_float4(fr, fi, 0.f, 0.f);
     const df r = dacc_result(re), q = dacc_result(im);
     return make_float4(r.hi, q.hi, r.lo, q.lo);
 }
 
 // w -= V h (one entry per thread).  With `last` set (second pass) the kernel
 // also forms ||w||^2 and the last CTA of the column runs its Givens step.
-template <int UB>
+template <int UB, bool T32>
 __global__ void __launch_bounds__(kStepNB) step_update_kernel(const StepArgs a, int last, int j) {
     extern __shared__ __align__(16) float4 dyn[];          // hs: m+1, then Givens scratch 4m+4
     __shared__ dacc red[kStepNB / 32];
@@ -597,7 +608,7 @@ __global__ void __launch_bounds__(kStepNB) step_update_kernel(const StepArgs a, 
     dacc nrm{0.f, 0.f};
     if (e < a.n) {
         float4 &wv = a.W[(long)c * a.n + e];
-        const float4 x = cta_update_entry<UB>(a.Vb, a.bs_i, (long)c * a.bs_c + e, hs, cnt, wv);
+        const float4 x = cta_update_entry<UB, T32>(a.Vb, a.bs_i, (long)c * a.bs_c + e, hs, cnt, wv);
         wv = x;
         dacc_mac(nrm, x.x, x.z, x.x, x.z);
         dacc_mac(nrm, x.y, x.w, x.y, x.w);
@@ -1454,10 +1465,12 @@ static int arnoldi_step(Plan *p, GmresWork *g, int inner, int j) {
         launch_pdl(step_dots_kernel, dgrid, dim3(kDotIW * 32), 0, st, a, pass, pass == 0 ? a.cnt_a : a.cnt_b, j);
         prof_end(p, tok, 0.0);
         tok = prof_begin(p, pass == 0 ? 4 : 5);
-        if (!p->in_batch && (long)a.nblk_vec * k < 4L * p->nsm)
-            launch_pdl(step_update_kernel<16>, vgrid, dim3(kStepNB), upd_smem, st, a, pass, j);
-        else
-            launch_pdl(step_update_kernel<4>, vgrid, dim3(kStepNB), upd_smem, st, a, pass, j);
+        // the first pass in binary32 FMAs when the products are binary32 (the second pass corrects it)
+        const bool t32 = pass == 0 && fft_prec_of(inner) == PREC_F32;
+        const bool deep = !p->in_batch && (long)a.nblk_vec * k < 4L * p->nsm;
+        auto ukern = deep ? (t32 ? step_update_kernel<16, true> : step_update_kernel<16, false>)
+                          : (t32 ? step_update_kernel<4, true> : step_update_kernel<4, false>);
+        launch_pdl(ukern, vgrid, dim3(kStepNB), upd_smem, st, a, pass, j);
         prof_end(p, tok, 0.0);
     }
     tok = prof_begin(p, 6);

@@ -93,3 +93,16 @@ def test_excitations():
     assert v.shape == (192, 1) and v[(1 * 4 + 1) * 12, 0] == 1 and np.count_nonzero(v) == 1
     c = arrays.centre_excitation(30, 30, 60)
     assert c[(15 * 30 + 15) * 60] == 1 and np.count_nonzero(c) == 1
+
+
+def test_bounds_check_entry_points_in_the_normal_build(lib):
+    """The normal library reports that it is not the bounds-checked build (no hits, no device call) and
+    refuses the probe without launching anything."""
+    import paper_2506_20350_gb300 as bt
+    h, f = ctypes.c_ulonglong(7), ctypes.c_ulonglong(7)
+    assert lib.bttb_check_report(ctypes.byref(h), ctypes.byref(f)) == 0
+    assert h.value == 0 and f.value == 0
+    assert lib.bttb_check_report(None, None) == 0
+    n = ctypes.c_ulonglong(7)
+    assert lib.bttb_check_probe(ctypes.byref(n)) == bt.BTTB_ERR_INVALID_ARG
+    assert n.value == 0 and "checked" in bt.bttb_last_error()

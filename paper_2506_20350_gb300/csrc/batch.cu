@@ -97,8 +97,9 @@ static float time_products(Plan &p, void *x, void *y, int nrhs, int prec, int re
 // Autotuner: for products of `nrhs` columns, times every form of the product that applies to the plan (all
 // of them give the strided passes' bits): the strided passes and the fused level-2 kernel, whose x passes
 // are strided, with each FFT batch-chunk width in {2, 4, ..., 64}; the fused two-level FFT; the persistent
-// kernel; in binary32, and keeps the fastest form and width; then times those forms of the double-float
-// product (FP64 plans) with that width and keeps the fastest.  Returns the width (or a negative status).
+// kernel; in binary32, and keeps the fastest form and width (a form other than the strided passes only if
+// it beats them by 2%); then times those forms of the double-float product (FP64 plans) with that width and
+// keeps the fastest the same way.  Returns the width (or a negative status).
 static int autotune_plan(Plan &p, int nrhs, int reps) {
     const int widths[6] = {2, 4, 8, 16, 32, 64};
     void *x = nullptr, *y = nullptr;
@@ -124,7 +125,9 @@ static int autotune_plan(Plan &p, int nrhs, int reps) {
             if (!uses_width && w != widths[0]) break;
             p.fft_pmax = w;
             const float ms = time_products(p, x, y, nrhs, PREC_F32, reps, e0, e1);
-            if (ms < best_ms) {
+            // another form than the strided passes has to be faster by 2%, so that timing noise does not
+            // flip the choice between forms that tie
+            if (ms < best_ms * (route == ROUTE_PASSES || best_r != ROUTE_PASSES ? 1.f : 0.98f)) {
                 best_ms = ms;
                 best_w = w;
                 best_r = route;
@@ -140,7 +143,7 @@ static int autotune_plan(Plan &p, int nrhs, int reps) {
             p.route_df = route;
             if (product_route(&p, nrhs, PREC_DF64) != route) continue;
             const float ms = time_products(p, x, y, nrhs, PREC_DF64, reps, e0, e1);
-            if (ms < best_df) {
+            if (ms < best_df * (route == ROUTE_PASSES || best_rd != ROUTE_PASSES ? 1.f : 0.98f)) {
                 best_df = ms;
                 best_rd = route;
             }
